@@ -1,0 +1,330 @@
+"""Benchmark of the fused explicit phase-field PVD step (cell-updates per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--workload NAME]
+
+One bench step is one whole run of the workload: the default ``paper512`` is
+the paper-scale plain DNS, a 512 x 512 FP32 grid advanced 50,000 explicit
+midpoint steps from a seeded film, with mass/free-energy diagnostics every
+1,000 steps, launched as CUDA-graph replays of 1,000 fused step kernels.
+Every run restarts from the same initial state (reset outside the timed
+events); L2 is flushed between runs.  Under torchrun each rank runs its own
+replica (independent deposition runs: weak scaling, no collective on the data
+path) and rank 0 prints one JSON line with the max time over ranks.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(a bounded sample of the same workload), rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_05410_gb300 import inputs as I  # noqa: E402
+
+METRIC = "DNS cell-updates/s (%HBM peak)"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL_UPDATE = 24  # read phi, c, rho + write phi, c, rho, FP32
+
+WORKLOADS = {
+    "paper512": dict(spec=I.PAPER_512["spec"], params=I.PAPER_512["params"], steps=50000,
+                     desc="plain DNS 512x512, 50000 steps, diagnostics every 1000"),
+    "small64": dict(spec=I.SMALL_64["spec"], params=dict(I.SMALL_64["params"], diag_every=1000), steps=2000,
+                    desc="plain DNS 64x64, 2000 steps"),
+    "large4096": dict(spec=I.FilmSpec(4096, 4096, 16.0, seed=1), params=dict(v_mag=0.3, diag_every=1000),
+                      steps=2000, desc="plain DNS 4096x4096, 2000 steps, diagnostics every 1000"),
+    "large8192": dict(spec=I.FilmSpec(8192, 8192, 16.0, seed=1), params=dict(v_mag=0.3, diag_every=1000),
+                      steps=1000, desc="plain DNS 8192x8192, 1000 steps, diagnostics every 1000"),
+}
+
+# DRAM bytes per step-kernel launch from an ncu capture, keyed by workload, with the
+# hash of the kernel source it was taken on (reported as null once the source changes).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_2312_05410_gb300", "csrc", "pf_step.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d["hbm_gbs"], source="measured")
+    return dict(hbm_gbs=6800.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = sorted({n for r in self.rows for n, v in zip(self.NAMES, r[2:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_native(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2312_05410_gb300 import build as B
+
+    B.build()
+    from paper_2312_05410_gb300 import pf
+
+    W = WORKLOADS[args.workload]
+    spec, nsteps = W["spec"], W["steps"]
+    p = I.default_params(**W["params"])
+    p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
+    state = I.film_state(spec, p)
+    sim = pf.Sim(p, *state, history_rows=nsteps // max(1, p["diag_every"]) + 2)
+    stream = sim.stream
+    init = [t.clone() for t in sim.fields]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    cells = spec.nx * spec.ny
+
+    def reset():
+        for t, s in zip(sim.fields, init):
+            t.copy_(s)
+        sim.set_step(0)
+        flush.zero_()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        reset()
+        sim.step(nsteps)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K whole runs, each bracketed by events on the launch stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for a, b in evs:
+            reset()
+            a.record(stream)
+            sim.step(nsteps)
+            b.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+    run_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(run_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    final_diag = sim.diag()
+
+    # ---- end to end through the public API with host buffers (pinned H2D + D2H inside)
+    host_in = [torch.from_numpy(np.ascontiguousarray(t.cpu().numpy())).pin_memory() for t in init]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for a, b in e2e_ev:
+        sim.set_step(0)
+        flush.zero_()
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            for t, h in zip(sim.fields, host_in):
+                t.copy_(h, non_blocking=True)
+        sim.step(nsteps)
+        with torch.cuda.stream(stream):
+            for t, h in zip(sim.fields, host_out):
+                h.copy_(t, non_blocking=True)
+        b.record(stream)
+    barrier()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    io_bytes = sum(h.numel() * h.element_size() for h in host_in)
+    sim.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    updates = cells * nsteps * args.steps * ws
+    value = updates / total_s
+    launches_per_run = nsteps + 2 * ((nsteps + p["diag_every"] - 1) // p["diag_every"] if p["diag_every"] else 0)
+    peaks = measured_peaks()
+    # Dominant kernel: the fused step. Its average launch duration is bounded above by
+    # the timed region per step launch (it also covers the diagnostic kernels and gaps).
+    per_launch_s = total_s / (nsteps * args.steps)
+    achieved = BYTES_PER_CELL_UPDATE * cells / per_launch_s / 1e9
+    tr = NCU_TRAFFIC.get(args.workload)
+    traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": W["desc"], "nx": spec.nx, "ny": spec.ny, "timesteps_per_run": nsteps,
+                   "diag_every": p["diag_every"], "dt": p["dt"], "per_rank": "independent replica",
+                   "l2": "flushed between timed runs (256 MB write)",
+                   "launch": "CUDA graph replays of fused step kernels"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_source": peaks["source"], "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
+        "gpu_launches": launches_per_run * args.steps,
+        "e2e": {"value": cells * nsteps * args.steps * ws / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "clocks": clk.summary(),
+        "wall_s": wall,
+        "final_diag": [float(x) for x in final_diag],
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(workload: str, budget_s: float = 15.0, steps: int | None = None) -> dict:
+    """Time the FP64 oracle (single thread, as it stands) on a bounded sample of the workload."""
+    import oracle as O
+
+    W = WORKLOADS[workload]
+    spec = W["spec"]
+    p = O.with_dt(I.default_params(**W["params"]))
+    state = I.film_state(spec, p)
+    O.step(p, *state, 1)  # load and warm the library
+    if steps is None:
+        t = time.perf_counter()
+        O.step(p, *state, 5)
+        per = (time.perf_counter() - t) / 5
+        steps = max(1, min(W["steps"], int(budget_s / per)))
+    t = time.perf_counter()
+    O.step(p, *state, steps)
+    dt = time.perf_counter() - t
+    return {"value": spec.nx * spec.ny * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{spec.nx}x{spec.ny} grid, first {steps} of the {W['steps']} steps, FP64, single thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload]
+    spec = W["spec"]
+    import oracle as O
+
+    p = O.with_dt(I.default_params(**W["params"]))
+    state = I.film_state(spec, p)
+    # size one sample step so that warmup + timed steps take about a minute in total
+    t = time.perf_counter()
+    O.step(p, *state, 3)
+    per = (time.perf_counter() - t) / 3
+    k = max(1, int(60.0 / (args.steps + args.warmup) / per))
+    k = min(k, W["steps"])
+    for _ in range(args.warmup):
+        O.step(p, *state, k)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.step(p, *state, k)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = spec.nx * spec.ny * k * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W["desc"], "nx": spec.nx, "ny": spec.ny, "timesteps_per_sample_step": k},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{spec.nx}x{spec.ny} grid, {k} of the {W['steps']} steps per bench step, "
+                                   "FP64 single-thread oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="paper512")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * pf.h - C ABI of the GB300 (sm_103a) explicit phase-field PVD time step.
+ *
+ * The method (arXiv 2312.05410, Materials and Methods, "Phase-field modeling of
+ * physical vapor deposition" and "Dataset"): three fields on a uniform 2D mesh,
+ *   phi  order parameter, solid +1 / vapor -1,
+ *   c    concentration of one species (conserved, Cahn-Hilliard),
+ *   rho  vapor density (convection-diffusion with a deposition sink),
+ * advanced by second-order central differences in space and the explicit
+ * midpoint (two-stage Runge-Kutta) method in time.  Closures the paper defers to
+ * another reference (free energy, switching function h, boundary conditions) are
+ * fixed as documented on pf_params below.
+ *
+ * Memory: every field is a caller-owned FP32 device array of ny rows of nx
+ * values, x fastest, with a row pitch of `pitch` floats (pitch >= nx, pitch a
+ * multiple of 4, base address 16-byte aligned).  The library never allocates
+ * device memory: scratch comes from a caller-owned workspace of
+ * pf_workspace_size() bytes.  All launches go to the caller's CUDA stream; only
+ * pf_diag() and pf_diag_history() synchronise it.
+ *
+ * Errors: every int-returning call returns PF_OK (0) or a negative PF_ERR_*
+ * code; pf_last_error() gives a message for the calling thread.  No call
+ * throws across the ABI.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_OK             0
+#define PF_ERR_ARG       -1  /* bad argument (null pointer, size, mode)            */
+#define PF_ERR_LAYOUT    -2  /* pitch / alignment / workspace too small            */
+#define PF_ERR_UNSTABLE  -3  /* dt above the explicit stability limit              */
+#define PF_ERR_NONFINITE -4  /* NaN or Inf seen in a field by a diagnostic pass    */
+#define PF_ERR_TIMEOUT   -5  /* a bounded device wait ran out                      */
+#define PF_ERR_CUDA      -6  /* a CUDA runtime call failed                         */
+
+/*
+ * Model parameters (host, FP64; the device computes in FP32).
+ *
+ *  dx, dt            mesh spacing and time step; dt must not exceed pf_dt_limit().
+ *  W_c, W_phi        well heights of the bulk free energy
+ *                    f(phi,c) = W_phi/4 (1-phi^2)^2 + p(phi) W_c c^2 (1-c)^2,
+ *                    p(phi) = 1/4 (2-phi)(1+phi)^2 (the paper's M^Bulk prefactor).
+ *  kappa_c, kappa_phi  gradient-energy coefficients (kappa/2 |grad u|^2).
+ *  MA_bulk, MB_bulk, MA_surf, MB_surf, sigma_surf
+ *                    composition mobility M_c = p(phi)(h MA_b + (1-h) MB_b)
+ *                      + exp(-(phi/sigma)^2)(h MA_s + (1-h) MB_s), h = c^2 (3-2c)
+ *                    (the paper's M^Bulk and M^Surf; its self-referencing
+ *                    "- M^Surf" term is dropped).
+ *  M_phi             constant mobility of the conserved phi equation (phi_mode 0).
+ *  L_phi             relaxation rate of the Allen-Cahn variant (phi_mode 1).
+ *  D_rho             vapor diffusivity.
+ *  v_mag, v_angle_deg  incident vapor velocity v = v_mag (cos a, -sin a), angle a
+ *                    from the substrate (90 = normal incidence).
+ *  rho_top           vapor reservoir value held in the ghost row above the top.
+ *  phi_mode          0: dphi/dt = div(M_phi grad dF/dphi) + S (the paper's
+ *                    Cahn-Hilliard form with source); 1: dphi/dt = -L_phi dF/dphi + S.
+ *  deposition        0 switches the incident flux off (v = 0, S = 0).
+ *  diag_every        0: no periodic diagnostics; k > 0: pf_step records
+ *                    {sum c, sum phi, sum rho, F_h} of every state whose step
+ *                    index is a multiple of k (step 0 included).
+ * Boundaries: x periodic; bottom row mirror for all fields; top row mirror for
+ * phi and c (and both chemical potentials), reservoir value rho_top for rho.
+ */
+typedef struct pf_params {
+    double dx, dt;
+    double W_c, W_phi, kappa_c, kappa_phi;
+    double MA_bulk, MB_bulk, MA_surf, MB_surf, sigma_surf;
+    double M_phi, L_phi, D_rho, v_mag, v_angle_deg, rho_top;
+    int phi_mode, deposition, diag_every;
+} pf_params;
+
+typedef struct pf_handle pf_handle;
+
+/*
+ * Explicit stability limit of the midpoint method for these parameters
+ * ("Dataset": explicit midpoint integration).  out[0] = min(out[1..3]);
+ * out[1] composition, out[2] order parameter, out[3] vapor (largest dt with
+ * |1 + z + z^2/2| <= 1 over a fixed 513 x 257 lattice of wave numbers).
+ * Host only; returns PF_ERR_ARG on a null pointer or non-positive dx.
+ */
+int pf_dt_limit(const pf_params* p, double out[4]);
+
+/* Bytes of caller-owned device workspace pf_init() needs for an nx x ny grid
+ * with the given row pitch (ping-pong state, reduction partials, diagnostic
+ * history of `history_rows` records, error word). 0 on bad sizes. */
+size_t pf_workspace_size(int nx, int ny, int pitch, int history_rows);
+
+/*
+ * Bind a simulation to caller-owned device fields and workspace.
+ *  phi, c, rho   device FP32 fields (state at step 0), ny rows, row pitch `pitch`.
+ *  work          device workspace of at least pf_workspace_size(nx, ny, pitch,
+ *                history_rows) bytes, 256-byte aligned; contents undefined on entry.
+ *  stream        cudaStream_t (NULL = legacy default stream) for every launch.
+ * Validates the parameters (PF_ERR_ARG), the layout (PF_ERR_LAYOUT) and
+ * dt <= pf_dt_limit() (PF_ERR_UNSTABLE).  No kernel runs and nothing is copied.
+ * The caller keeps ownership of every buffer; the handle holds pointers only.
+ */
+int pf_init(const pf_params* p, int nx, int ny, int pitch,
+            float* phi, float* c, float* rho,
+            void* work, size_t work_bytes, int history_rows,
+            void* stream, pf_handle** out);
+
+/*
+ * Advance n >= 0 explicit midpoint steps (all rows of the method: Laplacians,
+ * chemical potentials, mobility, conserved flux divergences, Allen-Cahn
+ * variant, deposition source, vapor transport, two RK stages) with one fused
+ * kernel launch per step.  Asynchronous on the bound stream; when the stream
+ * reaches the end of the call, phi, c and rho hold the state at step
+ * (step0 + n).  Long runs replay a captured CUDA graph of whole step blocks.
+ */
+int pf_step(pf_handle* h, long n);
+
+/* Diagnostics of the current state: out = {dx^2 sum c, dx^2 sum phi,
+ * dx^2 sum rho, F_h} with the discrete free energy F_h = dx^2 sum f +
+ * kappa_phi/2 sum_faces (dphi)^2 + kappa_c/2 sum_faces (dc)^2.  Per-cell terms
+ * in FP32, accumulation in FP64 in a fixed order (deterministic).  Synchronises
+ * the stream.  Returns PF_ERR_NONFINITE if any diagnostic pass so far saw a
+ * NaN or Inf (the error word is sticky until pf_clear_error). */
+int pf_diag(pf_handle* h, double out[4]);
+
+/* Copy up to max_rows recorded diagnostic records (step, sum c, sum phi,
+ * sum rho, F_h as 5 doubles each, oldest first) to host memory `out`;
+ * *rows receives the count.  Synchronises the stream. */
+int pf_diag_history(pf_handle* h, double* out, int max_rows, int* rows);
+
+/* Step counter of the bound state (starts at 0; pf_set_step is for resuming
+ * from a checkpoint, so that periodic diagnostics keep their phase). */
+long pf_get_step(const pf_handle* h);
+int pf_set_step(pf_handle* h, long step);
+
+/* Clear the sticky device error word (async). */
+int pf_clear_error(pf_handle* h);
+
+/* Release the handle (no device memory is freed: the caller owns it).
+ * Synchronises the stream first. */
+int pf_destroy(pf_handle* h);
+
+/*
+ * Diagnostics of arbitrary fields without a handle: writes the 4 doubles of
+ * pf_diag() to the DEVICE pointer out_dev (8-byte aligned), asynchronously on
+ * `stream`.  work: device scratch of pf_diag_workspace_size(nx, ny) bytes
+ * (per-block FP64 partials and the error word), caller-owned.  A NaN or Inf in
+ * any field sets bit 0 of the int at work + pf_diag_error_offset(nx, ny).
+ */
+size_t pf_diag_workspace_size(int nx, int ny);
+size_t pf_diag_error_offset(int nx, int ny);
+int pf_diagnostics(const pf_params* p, int nx, int ny, int pitch,
+                   const float* phi, const float* c, const float* rho,
+                   void* work, size_t work_bytes, double* out_dev, void* stream);
+
+/* Text for an error code, and the last error message of the calling thread. */
+const char* pf_strerror(int code);
+const char* pf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

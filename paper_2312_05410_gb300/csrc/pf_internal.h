@@ -1,0 +1,57 @@
+// Internal declarations shared by the kernels and the C-ABI layer (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pf {
+
+// FP32 constants of one explicit midpoint step, folded from pf_params on the host.
+struct StepConst {
+    int nx, ny, pitch;
+    float Wc;          // W_c
+    float Wf;          // W_phi
+    float kc;          // kappa_c / dx^2
+    float kf;          // kappa_phi / dx^2
+    float MBb, dMb;    // bulk mobility MB_bulk and MA_bulk - MB_bulk
+    float MBs, dMs;    // surface mobility MB_surf and MA_surf - MB_surf
+    float nisig2;      // -log2(e) / sigma_surf^2 (exp(-(phi/sigma)^2) = 2^(nisig2 phi^2))
+    float cR;          // 1 / (2 dx^2): face mean 1/2 (M + M_nb) and the 1/dx^2 of the divergence
+    float cF;          // phi_mode 0: M_phi / dx^2; phi_mode 1: -L_phi
+    float ax, ay;      // v_x / (2 dx), v_y / (2 dx)
+    float cD;          // D_rho / dx^2
+    float rho_top;     // reservoir ghost value above the top row
+    float dt;          // time step
+};
+
+enum MobKind { MOB_UNIFORM = 0, MOB_BULK = 1, MOB_SURF = 2 };
+
+// Output tile of the fused step kernel (4-cell halo staged around it):
+// TILE_SMALL 32 x 16 cells (many CTAs for small grids), TILE_LARGE 64 x 32.
+enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1 };
+int choose_tile(int nx, int ny);
+
+// Launch one fused step: (phi0, c0, rho0) -> (phi1, c1, rho1) with programmatic
+// dependent launch enabled (the kernel waits for the previous grid before reading).
+cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob,
+                        const float* phi0, const float* c0, const float* rho0,
+                        float* phi1, float* c1, float* rho1, cudaStream_t s);
+size_t step_smem_bytes(int tile);
+
+// Diagnostics: per-block FP64 partials then a fixed-order final reduction.
+struct DiagConst {
+    int nx, ny, pitch;
+    float Wc, Wf;
+    double area;       // dx^2
+    double hkf, hkc;   // kappa_phi / 2, kappa_c / 2
+};
+int diag_blocks(int nx, int ny);
+// hist (may be NULL): {count, next record step, capacity} then capacity records of
+// {step, sum c, sum phi, sum rho, F_h}; each call appends one record and advances
+// the next-record step by step_stride.
+cudaError_t launch_diag(const DiagConst& d, const float* phi, const float* c, const float* rho,
+                        double* partials, int* err, double* out, long long* hist, long long step_stride,
+                        cudaStream_t s);
+// Reset the history bookkeeping and the error word of a workspace.
+cudaError_t launch_reset(long long* hist, long long capacity, long long next_step, int* err, cudaStream_t s);
+
+}  // namespace pf

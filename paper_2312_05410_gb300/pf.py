@@ -1,0 +1,232 @@
+"""Python binding of libpf.so (include/pf.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; PyTorch provides device
+memory and the CUDA stream.  Importing this module loads the in-tree
+``_build/libpf.so`` and raises if it is missing (build it with
+``python -m paper_2312_05410_gb300.build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+PF_OK = 0
+PF_ERR_ARG = -1
+PF_ERR_LAYOUT = -2
+PF_ERR_UNSTABLE = -3
+PF_ERR_NONFINITE = -4
+PF_ERR_TIMEOUT = -5
+PF_ERR_CUDA = -6
+
+
+class PFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Params(C.Structure):
+    """Mirror of struct pf_params."""
+    _fields_ = [(n, C.c_double) for n in (
+        "dx", "dt", "W_c", "W_phi", "kappa_c", "kappa_phi",
+        "MA_bulk", "MB_bulk", "MA_surf", "MB_surf", "sigma_surf",
+        "M_phi", "L_phi", "D_rho", "v_mag", "v_angle_deg", "rho_top")] + [
+        ("phi_mode", C.c_int), ("deposition", C.c_int), ("diag_every", C.c_int)]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Params":
+        p = cls()
+        for name, _ in cls._fields_:
+            setattr(p, name, d[name])
+        return p
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libpf.so not built ({_LIB_PATH}); run python -m paper_2312_05410_gb300.build")
+    L = C.CDLL(_LIB_PATH)
+    P = C.POINTER(Params)
+    vp, sz = C.c_void_p, C.c_size_t
+    L.pf_dt_limit.argtypes, L.pf_dt_limit.restype = [P, C.POINTER(C.c_double)], C.c_int
+    L.pf_workspace_size.argtypes, L.pf_workspace_size.restype = [C.c_int, C.c_int, C.c_int, C.c_int], sz
+    L.pf_init.argtypes = [P, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, sz, C.c_int, vp, C.POINTER(vp)]
+    L.pf_init.restype = C.c_int
+    L.pf_step.argtypes, L.pf_step.restype = [vp, C.c_long], C.c_int
+    L.pf_diag.argtypes, L.pf_diag.restype = [vp, C.POINTER(C.c_double)], C.c_int
+    L.pf_diag_history.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
+    L.pf_diag_history.restype = C.c_int
+    L.pf_get_step.argtypes, L.pf_get_step.restype = [vp], C.c_long
+    L.pf_set_step.argtypes, L.pf_set_step.restype = [vp, C.c_long], C.c_int
+    L.pf_clear_error.argtypes, L.pf_clear_error.restype = [vp], C.c_int
+    L.pf_destroy.argtypes, L.pf_destroy.restype = [vp], C.c_int
+    L.pf_diag_workspace_size.argtypes, L.pf_diag_workspace_size.restype = [C.c_int, C.c_int], sz
+    L.pf_diag_error_offset.argtypes, L.pf_diag_error_offset.restype = [C.c_int, C.c_int], sz
+    L.pf_diagnostics.argtypes = [P, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, sz, vp, vp]
+    L.pf_diagnostics.restype = C.c_int
+    L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
+    L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(rc: int) -> int:
+    if rc != PF_OK:
+        raise PFError(rc, f"{lib.pf_strerror(rc).decode()}: {lib.pf_last_error().decode()}")
+    return rc
+
+
+def strerror(code: int) -> str:
+    return lib.pf_strerror(code).decode()
+
+
+def last_error() -> str:
+    return lib.pf_last_error().decode()
+
+
+# ---------------------------------------------------------------- thin wrappers
+def pf_dt_limit(params: dict) -> np.ndarray:
+    out = (C.c_double * 4)()
+    _check(lib.pf_dt_limit(C.byref(Params.from_dict(params)), out))
+    return np.array(out[:])
+
+
+def pf_workspace_size(nx: int, ny: int, pitch: int, history_rows: int) -> int:
+    return int(lib.pf_workspace_size(nx, ny, pitch, history_rows))
+
+
+def pf_init(params: dict, nx: int, ny: int, pitch: int, phi_ptr: int, c_ptr: int, rho_ptr: int,
+            work_ptr: int, work_bytes: int, history_rows: int, stream: int) -> int:
+    """Returns the raw return code and handle (no exception), for error-path tests."""
+    h = C.c_void_p()
+    rc = lib.pf_init(C.byref(Params.from_dict(params)), nx, ny, pitch, phi_ptr, c_ptr, rho_ptr, work_ptr,
+                     work_bytes, history_rows, stream, C.byref(h))
+    return rc, h
+
+
+def pf_step(h, n: int) -> int:
+    return lib.pf_step(h, n)
+
+
+def pf_diag(h):
+    out = (C.c_double * 4)()
+    rc = lib.pf_diag(h, out)
+    return rc, np.array(out[:])
+
+
+def pf_diag_history(h, max_rows: int = 4096):
+    buf = (C.c_double * (5 * max(1, max_rows)))()
+    rows = C.c_int(0)
+    _check(lib.pf_diag_history(h, buf, max_rows, C.byref(rows)))
+    return np.array(buf[: 5 * rows.value]).reshape(rows.value, 5)
+
+
+def pf_get_step(h) -> int:
+    return int(lib.pf_get_step(h))
+
+
+def pf_set_step(h, step: int) -> int:
+    return lib.pf_set_step(h, step)
+
+
+def pf_clear_error(h) -> int:
+    return lib.pf_clear_error(h)
+
+
+def pf_destroy(h) -> int:
+    return lib.pf_destroy(h)
+
+
+def pf_diag_workspace_size(nx: int, ny: int) -> int:
+    return int(lib.pf_diag_workspace_size(nx, ny))
+
+
+def pf_diag_error_offset(nx: int, ny: int) -> int:
+    return int(lib.pf_diag_error_offset(nx, ny))
+
+
+def pf_diagnostics(params: dict, nx: int, ny: int, pitch: int, phi_ptr: int, c_ptr: int, rho_ptr: int,
+                   work_ptr: int, work_bytes: int, out_dev_ptr: int, stream: int) -> int:
+    return lib.pf_diagnostics(C.byref(Params.from_dict(params)), nx, ny, pitch, phi_ptr, c_ptr, rho_ptr,
+                              work_ptr, work_bytes, out_dev_ptr, stream)
+
+
+# ---------------------------------------------------------------- torch-backed simulation
+def padded_pitch(nx: int) -> int:
+    """Row pitch in floats: nx rounded up to 32 (128-byte rows)."""
+    return (nx + 31) // 32 * 32
+
+
+class Sim:
+    """One simulation bound to torch-owned device fields and workspace.
+
+    ``phi``, ``c``, ``rho`` are (ny, pitch) float32 CUDA tensors; the model
+    state is their first nx columns.  All launches go to ``stream`` (default:
+    torch's current stream).
+    """
+
+    def __init__(self, params: dict, phi, c, rho, history_rows: int = 256, stream=None, device="cuda"):
+        import torch
+
+        phi, c, rho = (np.asarray(a, dtype=np.float32) for a in (phi, c, rho))
+        ny, nx = phi.shape
+        self.nx, self.ny, self.pitch = nx, ny, padded_pitch(nx)
+        self.params = dict(params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.fields = []
+        for a in (phi, c, rho):
+            t = torch.zeros((ny, self.pitch), dtype=torch.float32, device=device)
+            t[:, :nx] = torch.from_numpy(a).to(device)
+            self.fields.append(t)
+        self.phi, self.c, self.rho = self.fields
+        nbytes = pf_workspace_size(nx, ny, self.pitch, history_rows)
+        if nbytes == 0:
+            raise PFError(PF_ERR_ARG, "bad grid size")
+        self.work = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.work.data_ptr()
+        self._work_ptr = (base + 255) // 256 * 256
+        self._work_bytes = nbytes
+        torch.cuda.synchronize()
+        rc, h = pf_init(self.params, nx, ny, self.pitch, self.phi.data_ptr(), self.c.data_ptr(),
+                        self.rho.data_ptr(), self._work_ptr, nbytes, history_rows, self.stream.cuda_stream)
+        _check(rc)
+        self.h = h
+
+    def step(self, n: int):
+        _check(pf_step(self.h, int(n)))
+
+    def diag(self) -> np.ndarray:
+        rc, out = pf_diag(self.h)
+        _check(rc)
+        return out
+
+    def history(self) -> np.ndarray:
+        return pf_diag_history(self.h)
+
+    @property
+    def step_index(self) -> int:
+        return pf_get_step(self.h)
+
+    def set_step(self, step: int):
+        _check(pf_set_step(self.h, step))
+
+    def numpy(self):
+        """(phi, c, rho) of the current state as float32 numpy arrays (synchronises)."""
+        self.stream.synchronize()
+        return tuple(t[:, : self.nx].cpu().numpy() for t in self.fields)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            _check(pf_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

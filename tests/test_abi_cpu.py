@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: exported symbols, the host-side stability
+limit against the oracle's, and every argument/layout/stability error path of
+pf_init and pf_diagnostics (they return before any CUDA call)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_05410_gb300 import build as B
+from paper_2312_05410_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def pf():
+    B.build()
+    from paper_2312_05410_gb300 import pf as mod
+    return mod
+
+
+def declared_symbols():
+    text = open(os.path.join(B.INCLUDE, "pf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pf_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(pf):
+    names = declared_symbols()
+    assert len(names) >= 15, names
+    for n in names:
+        assert hasattr(pf.lib, n), n
+
+
+def test_strerror(pf):
+    assert pf.strerror(0) == "ok"
+    assert "stability" in pf.strerror(pf.PF_ERR_UNSTABLE)
+    assert pf.strerror(-99) == "unknown error"
+
+
+@pytest.mark.parametrize("over", [
+    {}, dict(phi_mode=1), dict(v_angle_deg=55.0, v_mag=0.9, D_rho=0.3), dict(MA_surf=10.0, MB_surf=3.0, MA_bulk=2.0),
+    dict(deposition=0, dx=0.5), dict(D_rho=0.05, v_mag=1.0, v_angle_deg=50.0), dict(kappa_c=8.0, W_c=3.0),
+])
+def test_dt_limit_matches_oracle(pf, over):
+    p = I.default_params(**over)
+    got = pf.pf_dt_limit(p)
+    ref = O.dt_limit(p)
+    np.testing.assert_allclose(got, [ref["dt_lim"], ref["dt_c"], ref["dt_phi"], ref["dt_rho"]], rtol=1e-12)
+
+
+FAKE = 1 << 20  # aligned non-null address; never dereferenced on these paths
+
+
+def _init(pf, p, nx=64, ny=64, pitch=64, ptrs=(FAKE, FAKE, FAKE), work=FAKE, work_bytes=None, hist=4):
+    if work_bytes is None:
+        work_bytes = pf.pf_workspace_size(nx, ny, max(pitch, 1), hist) or 1 << 30
+    rc, h = pf.pf_init(p, nx, ny, pitch, *ptrs, work, work_bytes, hist, 0)
+    return rc
+
+
+def test_init_error_paths(pf):
+    good = O.with_dt(I.default_params())
+    assert _init(pf, good, nx=0) == pf.PF_ERR_ARG
+    assert _init(pf, good, ny=0) == pf.PF_ERR_ARG
+    assert _init(pf, good, pitch=66) == pf.PF_ERR_LAYOUT
+    assert _init(pf, good, pitch=60) == pf.PF_ERR_LAYOUT
+    assert _init(pf, good, ptrs=(FAKE + 4, FAKE, FAKE)) == pf.PF_ERR_LAYOUT
+    assert _init(pf, good, ptrs=(0, FAKE, FAKE)) == pf.PF_ERR_ARG
+    assert _init(pf, good, work=FAKE + 64) == pf.PF_ERR_LAYOUT
+    assert _init(pf, good, work_bytes=1024) == pf.PF_ERR_LAYOUT
+    assert _init(pf, dict(good, phi_mode=2)) == pf.PF_ERR_ARG
+    assert _init(pf, dict(good, dt=0.0)) == pf.PF_ERR_ARG
+    assert _init(pf, dict(good, W_c=float("nan"))) == pf.PF_ERR_ARG
+    assert _init(pf, dict(good, MA_surf=1.0, sigma_surf=0.0)) == pf.PF_ERR_ARG
+    assert _init(pf, good, hist=-1) == pf.PF_ERR_ARG
+    lim = pf.pf_dt_limit(good)[0]
+    rc = _init(pf, dict(good, dt=1.01 * lim))
+    assert rc == pf.PF_ERR_UNSTABLE
+    assert "stability limit" in pf.last_error()
+
+
+def test_workspace_size(pf):
+    assert pf.pf_workspace_size(0, 4, 32, 1) == 0
+    assert pf.pf_workspace_size(40, 4, 32, 1) == 0  # pitch < nx
+    s1 = pf.pf_workspace_size(512, 512, 512, 64)
+    assert s1 >= 3 * 512 * 512 * 4
+    assert pf.pf_workspace_size(512, 512, 512, 128) > s1
+    assert s1 % 256 == 0
+
+
+def test_diagnostics_error_paths(pf):
+    p = I.default_params()
+    need = pf.pf_diag_workspace_size(64, 64)
+    assert need > 0 and pf.pf_diag_error_offset(64, 64) < need
+    assert pf.pf_diagnostics(p, 64, 64, 64, FAKE, FAKE, FAKE, FAKE, need - 1, FAKE, 0) == pf.PF_ERR_LAYOUT
+    assert pf.pf_diagnostics(p, 64, 64, 64, FAKE, FAKE, 0, FAKE, need, FAKE, 0) == pf.PF_ERR_ARG
+    assert pf.pf_diagnostics(p, 0, 64, 64, FAKE, FAKE, FAKE, FAKE, need, FAKE, 0) == pf.PF_ERR_ARG
+    assert pf.pf_diagnostics(p, 64, 64, 64, FAKE, FAKE, FAKE, FAKE + 8, need, FAKE, 0) == pf.PF_ERR_LAYOUT

@@ -1,0 +1,197 @@
+"""GPU parity of the fused step against the FP64 oracle, through the C ABI.
+
+Tolerances are the project's targets: max-abs 1e-5 after 100 steps and 1e-4
+after 2000 steps on every field (FP32 state against FP64; the spinodal growth
+of the composition amplifies round-off by about e^{t/8}).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2312_05410_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf(cuda_ok):
+    from paper_2312_05410_gb300 import build as B
+    B.build()
+    from paper_2312_05410_gb300 import pf as mod
+    return mod
+
+
+def run_gpu(pf, params, state, steps, history_rows=64):
+    sim = pf.Sim(params, *state, history_rows=history_rows)
+    sim.step(steps)
+    out = sim.numpy()
+    hist = sim.history()
+    sim.close()
+    return out, hist
+
+
+def max_err(a, b):
+    return max(float(np.abs(x.astype(np.float64) - y).max()) for x, y in zip(a, b))
+
+
+def test_small_film_100_and_2000_steps(pf):
+    cfg = I.SMALL_64
+    p = O.with_dt(I.default_params(**cfg["params"]))
+    state = I.film_state(cfg["spec"], p)
+    ref100 = O.step(p, *state, 100)
+    ref2000 = O.step(p, *ref100, 1900)
+    g100, _ = run_gpu(pf, p, state, 100)
+    g2000, _ = run_gpu(pf, p, state, 2000)
+    e100, e2000 = max_err(g100, ref100), max_err(g2000, ref2000)
+    assert e100 <= 1e-5, e100
+    assert e2000 <= 1e-4, e2000
+    # the run did something: the film grew and the composition coarsened
+    assert ref2000[0].sum() > state[0].astype(np.float64).sum() + 10
+
+
+@pytest.mark.parametrize("nx,ny", [(37, 23), (65, 64), (130, 70), (64, 33), (1, 5), (3, 2), (200, 9)])
+def test_odd_and_ragged_sizes(pf, nx, ny):
+    p = O.with_dt(I.default_params(v_angle_deg=65.0))
+    state = I.film_state(I.FilmSpec(nx, ny, ny / 3.0, seed=nx * 1000 + ny), p)
+    ref = O.step(p, *state, 100)
+    got, _ = run_gpu(pf, p, state, 100)
+    assert max_err(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("over", [
+    dict(phi_mode=1),
+    dict(MA_bulk=2.0, MB_bulk=0.5),
+    dict(MA_bulk=2.0, MB_bulk=0.5, MA_surf=10.0, MB_surf=4.0, sigma_surf=0.5),
+    dict(v_angle_deg=50.0, v_mag=1.0),
+    dict(deposition=0),
+    dict(dx=0.7, kappa_c=1.5, W_c=1.2, rho_top=0.8),
+])
+def test_model_variants(pf, over):
+    p = O.with_dt(I.default_params(**over))
+    state = I.film_state(I.FilmSpec(96, 80, 20.0, seed=7), p)
+    ref = O.step(p, *state, 100)
+    got, _ = run_gpu(pf, p, state, 100)
+    assert max_err(got, ref) <= 1e-5
+
+
+def test_rough_random_fields(pf):
+    p = O.with_dt(I.default_params(v_angle_deg=70.0))
+    state = I.random_state(72, 40, seed=21)
+    ref = O.step(p, *state, 20)
+    got, _ = run_gpu(pf, p, state, 20)
+    assert max_err(got, ref) <= 1e-5
+
+
+def test_paper_scale_grid_graph_path(pf):
+    """512 x 512, the benchmark's kernel and graph replay (diagnostics every 100 steps)."""
+    cfg = I.PAPER_512
+    p = O.with_dt(I.default_params(**dict(cfg["params"], diag_every=100)))
+    state = I.film_state(cfg["spec"], p)
+    ref = O.step(p, *state, 200)
+    got, hist = run_gpu(pf, p, state, 200)
+    assert max_err(got, ref) <= 1e-5
+    # history: records of the states at steps 0 and 100
+    assert hist.shape == (2, 5)
+    assert list(hist[:, 0]) == [0.0, 100.0]
+    d0 = O.diag(p, *state)
+    d100 = O.diag(p, *O.step(p, *state, 100))
+    np.testing.assert_allclose(hist[0, 1:], d0, rtol=2e-6)
+    np.testing.assert_allclose(hist[1, 1:], d100, rtol=2e-6)
+
+
+def test_diag_matches_oracle(pf):
+    p = O.with_dt(I.default_params(kappa_c=1.7, W_phi=0.8, dx=0.9))
+    state = I.film_state(I.FilmSpec(100, 60, 15.0, seed=3), p)
+    sim = pf.Sim(p, *state)
+    got = sim.diag()
+    sim.close()
+    np.testing.assert_allclose(got, O.diag(p, *state), rtol=1e-6)
+
+
+def test_composition_conserved_long_run(pf):
+    """sum(c) has no source and no boundary flux: FP32 drift stays tiny over 20000 steps."""
+    cfg = I.PAPER_512
+    p = O.with_dt(I.default_params(**dict(cfg["params"], diag_every=1000)))
+    state = I.film_state(cfg["spec"], p)
+    sim = pf.Sim(p, *state)
+    d0 = sim.diag()
+    sim.step(20000)
+    d1 = sim.diag()
+    hist = sim.history()
+    sim.close()
+    assert abs(d1[0] - d0[0]) <= 2e-5 * abs(d0[0]), (d0, d1)
+    assert d1[1] > d0[1]  # film grew
+    assert np.all(np.isfinite(hist))
+    assert hist.shape[0] == 20
+
+
+def test_runs_are_bitwise_deterministic(pf):
+    p = O.with_dt(I.default_params())
+    state = I.film_state(I.FilmSpec(128, 96, 12.0, seed=5), p)
+    a, _ = run_gpu(pf, p, state, 300)
+    b, _ = run_gpu(pf, p, state, 300)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_resume_from_checkpoint_is_bitwise(pf):
+    p = O.with_dt(I.default_params(diag_every=100))
+    state = I.film_state(I.FilmSpec(96, 96, 12.0, seed=6), p)
+    full, hfull = run_gpu(pf, p, state, 1000)
+    sim = pf.Sim(p, *state)
+    sim.step(500)
+    ckpt = sim.numpy()
+    sim.close()
+    sim = pf.Sim(p, *ckpt)
+    sim.set_step(500)
+    sim.step(500)
+    resumed = sim.numpy()
+    hres = sim.history()
+    sim.close()
+    for x, y in zip(full, resumed):
+        assert np.array_equal(x, y)
+    np.testing.assert_array_equal(hres, hfull[5:])
+
+
+def test_step_counts_odd_and_zero(pf):
+    p = O.with_dt(I.default_params())
+    state = I.film_state(I.FilmSpec(64, 64, 8.0, seed=0), p)
+    sim = pf.Sim(p, *state)
+    sim.step(0)
+    assert all(np.array_equal(a, b) for a, b in zip(sim.numpy(), state))
+    sim.step(7)
+    sim.step(6)
+    got = sim.numpy()
+    assert sim.step_index == 13
+    sim.close()
+    assert max_err(got, O.step(p, *state, 13)) <= 1e-5
+
+
+def test_nonfinite_is_reported(pf):
+    p = O.with_dt(I.default_params())
+    phi, c, rho = I.film_state(I.FilmSpec(64, 64, 8.0, seed=0), p)
+    c = c.copy()
+    c[10, 10] = np.nan
+    sim = pf.Sim(p, phi, c, rho)
+    sim.step(3)
+    rc, _ = pf.pf_diag(sim.h)
+    assert rc == pf.PF_ERR_NONFINITE
+    assert pf.pf_clear_error(sim.h) == 0
+    sim.close()
+
+
+def test_standalone_diagnostics_entry_point(pf):
+    import torch
+
+    p = O.with_dt(I.default_params())
+    state = I.film_state(I.FilmSpec(80, 50, 10.0, seed=2), p)
+    sim = pf.Sim(p, *state)
+    ws = torch.zeros(pf.pf_diag_workspace_size(80, 50) + 256, dtype=torch.uint8, device="cuda")
+    wp = (ws.data_ptr() + 255) // 256 * 256
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    rc = pf.pf_diagnostics(p, 80, 50, sim.pitch, sim.phi.data_ptr(), sim.c.data_ptr(), sim.rho.data_ptr(), wp,
+                           pf.pf_diag_workspace_size(80, 50), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), sim.diag(), rtol=1e-12)
+    sim.close()
