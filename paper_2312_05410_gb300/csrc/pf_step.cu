@@ -12,296 +12,360 @@
 //   L3  mu_c, mu_phi, M_c        of u*
 //   L4  u^{n+1} = u^n + dt R(u*) -> global memory
 // so a step is one launch with 24 B of algorithmic HBM traffic per cell.
-// Threads work on x-adjacent cell pairs with packed FP32x2 arithmetic
-// (fma/add/mul .f32x2).  Boundary rules live in the row-neighbour offsets:
-// the bottom and top rows see themselves as their outer neighbour (mirror);
-// rho's outer neighbour above the top row is the reservoir value.
+//
+// Work layout: every thread owns one pair of x-adjacent columns and, in each
+// level, streams down a segment of rows with a three-row register window, so a
+// vertical neighbour is a register and each staged value is loaded from shared
+// memory once per level (plus the two scalar west/east neighbours).  The pair
+// is computed with packed FP32x2 arithmetic (fma/add/mul .f32x2).
+//
+// Boundary rules are applied once, where a level stores its results: the
+// bottom and top domain rows are also written into the ghost row outside them
+// (mirror), except that rho's ghost row above the top holds the reservoir
+// value; the stencils themselves have no boundary branches.  Only domain rows
+// are computed, so a ghost row has exactly one writer.
 #include "pf_internal.h"
 
 namespace pf {
 namespace {
 
+// Pair arithmetic: packed .f32x2 instructions (PF_PACKED=1) or two scalar FP32 ops.
+#ifndef PF_PACKED
+#define PF_PACKED 1
+#endif
 typedef float2 f2;
 __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+#if PF_PACKED
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
+#else
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
 
 constexpr int HALO = 4;
-constexpr int PAD = 4;  // columns of padding on each side of a staged row (keeps 16-B alignment)
+constexpr int PAD = 4;  // left padding of a staged row (keeps float4 staging 16-B aligned)
 
-template <int TX, int TY>
+template <int TX, int TY, int S>
 struct Geo {
     static constexpr int LX = TX + 2 * HALO;  // staged columns
     static constexpr int LY = TY + 2 * HALO;  // staged rows
-    static constexpr int PX = LX + 2 * PAD;   // row pitch in shared memory (floats)
+    static constexpr int PX = LX + PAD;       // row pitch in floats; the east neighbour of the last
+                                              // column reads the next row's padding (never used)
     static constexpr int PLANE = LY * PX;
-    static constexpr int NPLANES = 9;         // u^n (3), mu/M (3), u* (3)
-    static constexpr size_t BYTES = size_t(NPLANES) * PLANE * sizeof(float);
+    static constexpr int NPC = LX / 2;        // pair columns = threads per row segment
+    static constexpr int THREADS = NPC * S;   // S row segments
+    static constexpr size_t BYTES = (size_t(9) * PLANE + 8) * sizeof(float);  // + tail guard
+    static constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+    static constexpr int L1 = cdiv(LY - 2, S);  // longest segment of each level
+    static constexpr int L2 = cdiv(LY - 4, S);
+    static constexpr int L3 = cdiv(LY - 6, S);
+    static constexpr int L4 = cdiv(TY, S);
 };
 
-// Pair of cells (x, x+1) of one staged plane, with its four neighbour pairs.
-struct Nb {
-    f2 C, N, S;
-    float W, E;  // scalar west neighbour of x, east neighbour of x+1
-};
+__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
+__device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
 
-__device__ __forceinline__ Nb load_nb(const float* p, int up, int dn)
-{
-    Nb r;
-    r.C = *reinterpret_cast<const f2*>(p);
-    r.N = *reinterpret_cast<const f2*>(p + up);
-    r.S = *reinterpret_cast<const f2*>(p + dn);
-    r.W = p[-1];
-    r.E = p[2];
-    return r;
-}
-
-// Sum of the four neighbours of each cell of the pair.
-__device__ __forceinline__ f2 nb_sum(const Nb& a)
-{
-    f2 h = make_float2(a.W + a.C.y, a.C.x + a.E);
-    return add2(h, add2(a.N, a.S));
-}
+// Horizontal neighbour sum of the pair (x, x+1): (u[x-1] + u[x+1], u[x] + u[x+2]).
+__device__ __forceinline__ f2 hsum(float W, f2 C, float E) { return make_float2(W + C.y, C.x + E); }
 
 // p(phi) = 1/4 (2-phi)(1+phi)^2 = 1/2 + 3/4 phi - 1/4 phi^3
-__device__ __forceinline__ f2 p_of(f2 f, f2 f2sq)
+__device__ __forceinline__ f2 p_of(f2 f, f2 ff) { return fma2(fma2(F2(-0.25f), ff, F2(0.75f)), f, F2(0.5f)); }
+
+// Rows [lo, hi) of a level split into S near-equal segments; segment s of them.
+__device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, int& n)
 {
-    return fma2(fma2(F2(-0.25f), f2sq, F2(0.75f)), f, F2(0.5f));
+    const int H = hi > lo ? hi - lo : 0;
+    r0 = lo + (s * H) / S;
+    n = lo + ((s + 1) * H) / S - r0;
 }
 
-// L1 / L3: chemical potentials and mobility of one pair from the staged (phi, c).
-template <int MOB>
-__device__ __forceinline__ void level_mu(const StepConst& k, const float* sphi, const float* sc,
-                                         int up, int dn, float* o_muc, float* o_muf, float* o_M)
+// L1 / L3: mu_c, mu_phi and M_c of the staged (phi, c) over rows [r0, r0+n) of
+// one pair column; o is the offset of (row 0, this pair) in a plane.
+template <int L, int PX, int MOB>
+__device__ __forceinline__ void level_mu(const StepConst& k, const float* __restrict__ P,
+                                         const float* __restrict__ Cp, float* __restrict__ A0,
+                                         float* __restrict__ A1, float* __restrict__ A2, int o, int r0, int n,
+                                         int gy_r0, int ny)
 {
-    const Nb F = load_nb(sphi, up, dn);
-    const Nb Cc = load_nb(sc, up, dn);
-    const f2 f = F.C, c = Cc.C;
-    const f2 ff = mul2(f, f);
-    const f2 p = p_of(f, ff);
-    const f2 q = fma2(neg2(c), c, c);                               // c (1 - c)
-    const f2 g = mul2(q, q);                                   // g(c) = c^2 (1-c)^2
-    const f2 Wdg = mul2(q, fma2(F2(-4.f * k.Wc), c, F2(2.f * k.Wc)));  // W_c g'(c)
-    // mu_c = p W_c g' - kappa_c L(c)
-    f2 muc = fma2(F2(4.f * k.kc), c, mul2(p, Wdg));
-    muc = fma2(F2(-k.kc), nb_sum(Cc), muc);
-    // mu_phi = -W_phi phi (1 - phi^2) + p'(phi) W_c g - kappa_phi L(phi),  p' = 3/4 (1 - phi^2)
-    f2 muf = mul2(fma2(F2(k.Wf), ff, F2(-k.Wf)), f);
-    muf = fma2(fma2(F2(-0.75f * k.Wc), ff, F2(0.75f * k.Wc)), g, muf);
-    muf = fma2(F2(4.f * k.kf), f, muf);
-    muf = fma2(F2(-k.kf), nb_sum(F), muf);
-    // M_c = p (MB + h dM) [+ exp(-(phi/sigma)^2)(MBs + h dMs)],  h = c^2 (3 - 2c)
-    f2 M;
-    if (MOB == MOB_UNIFORM) {
-        M = mul2(p, F2(k.MBb));
-    } else {
-        const f2 h = mul2(mul2(c, c), fma2(F2(-2.f), c, F2(3.f)));
-        M = mul2(p, fma2(h, F2(k.dMb), F2(k.MBb)));
-        if (MOB == MOB_SURF) {
-            const f2 t = mul2(ff, F2(k.nisig2));
-            const f2 e = make_float2(exp2f(t.x), exp2f(t.y));
-            M = fma2(e, fma2(h, F2(k.dMs), F2(k.MBs)), M);
+    f2 fw[3], cw[3];
+    const int b = o + r0 * PX;
+    fw[0] = ld2(P + b - PX);
+    fw[1] = ld2(P + b);
+    cw[0] = ld2(Cp + b - PX);
+    cw[1] = ld2(Cp + b);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        if (i < n) {
+            const int iS = i % 3, iC = (i + 1) % 3, iN = (i + 2) % 3;
+            const int q = b + i * PX;
+            fw[iN] = ld2(P + q + PX);
+            cw[iN] = ld2(Cp + q + PX);
+            const f2 f = fw[iC], c = cw[iC];
+            const f2 sf = add2(hsum(P[q - 1], f, P[q + 2]), add2(fw[iN], fw[iS]));
+            const f2 sc = add2(hsum(Cp[q - 1], c, Cp[q + 2]), add2(cw[iN], cw[iS]));
+            const f2 ff = mul2(f, f);
+            const f2 p = p_of(f, ff);
+            const f2 qq = fma2(neg2(c), c, c);                                   // c (1 - c)
+            const f2 g = mul2(qq, qq);                                           // g(c)
+            const f2 Wdg = mul2(qq, fma2(F2(-4.f * k.Wc), c, F2(2.f * k.Wc)));  // W_c g'(c)
+            // mu_c = p W_c g' - kappa_c L(c)
+            f2 muc = fma2(F2(4.f * k.kc), c, mul2(p, Wdg));
+            muc = fma2(F2(-k.kc), sc, muc);
+            // mu_phi = -W_phi phi (1 - phi^2) + p'(phi) W_c g - kappa_phi L(phi),  p' = 3/4 (1 - phi^2)
+            f2 muf = mul2(fma2(F2(k.Wf), ff, F2(-k.Wf)), f);
+            muf = fma2(fma2(F2(-0.75f * k.Wc), ff, F2(0.75f * k.Wc)), g, muf);
+            muf = fma2(F2(4.f * k.kf), f, muf);
+            muf = fma2(F2(-k.kf), sf, muf);
+            // M_c = p (MB + h dM) [+ exp(-(phi/sigma)^2)(MBs + h dMs)],  h = c^2 (3 - 2c)
+            f2 M;
+            if (MOB == MOB_UNIFORM) {
+                M = mul2(p, F2(k.MBb));
+            } else {
+                const f2 h = mul2(mul2(c, c), fma2(F2(-2.f), c, F2(3.f)));
+                M = mul2(p, fma2(h, F2(k.dMb), F2(k.MBb)));
+                if (MOB == MOB_SURF) {
+                    const f2 t = mul2(ff, F2(k.nisig2));
+                    M = fma2(make_float2(exp2f(t.x), exp2f(t.y)), fma2(h, F2(k.dMs), F2(k.MBs)), M);
+                }
+            }
+            st2(A0 + q, muc);
+            st2(A1 + q, muf);
+            st2(A2 + q, M);
         }
     }
-    *reinterpret_cast<f2*>(o_muc) = muc;
-    *reinterpret_cast<f2*>(o_muf) = muf;
-    *reinterpret_cast<f2*>(o_M) = M;
-}
-
-// L2 / L4 right-hand side of one pair: R_phi, R_c, R_rho (not yet scaled by dt).
-template <int PHI_MODE>
-__device__ __forceinline__ void level_rhs(const StepConst& k, const float* smuc, const float* smuf,
-                                          const float* sM, const float* sphi, const float* srho,
-                                          int up, int dn, bool top, f2& Rf, f2& Rc, f2& Rr)
-{
-    // conserved composition flux: sum_faces (M + M_nb)(mu_nb - mu) / (2 dx^2)
-    const Nb m = load_nb(smuc, up, dn);
-    const Nb M = load_nb(sM, up, dn);
-    const float Fa = (M.W + M.C.x) * (m.C.x - m.W);      // face (x-1 | x)
-    const float Fb = (M.C.x + M.C.y) * (m.C.y - m.C.x);  // face (x | x+1)
-    const float Fc = (M.C.y + M.E) * (m.E - m.C.y);      // face (x+1 | x+2)
-    f2 rc = make_float2(Fb - Fa, Fc - Fb);
-    rc = fma2(add2(M.C, M.N), sub2(m.N, m.C), rc);
-    rc = fma2(add2(M.C, M.S), sub2(m.S, m.C), rc);
-    Rc = mul2(rc, F2(k.cR));
-
-    // deposition source S = grad(phi) . (rho v), central differences
-    const Nb F = load_nb(sphi, up, dn);
-    const Nb R = load_nb(srho, up, dn);
-    const f2 gx = make_float2(F.C.y - F.W, F.E - F.C.x);
-    const f2 gy = sub2(F.N, F.S);
-    const f2 Src = mul2(R.C, fma2(F2(k.ax), gx, mul2(F2(k.ay), gy)));
-
-    if (PHI_MODE == 0) {
-        const Nb u = load_nb(smuf, up, dn);
-        Rf = fma2(F2(k.cF), fma2(F2(-4.f), u.C, nb_sum(u)), Src);
-    } else {
-        const f2 u = *reinterpret_cast<const f2*>(smuf);
-        Rf = fma2(F2(k.cF), u, Src);
+    if (n > 0) {  // mirror ghosts outside the bottom / top domain rows (own writes: no barrier)
+        if (gy_r0 == 0) {
+            st2(A0 + b - PX, ld2(A0 + b));
+            st2(A1 + b - PX, ld2(A1 + b));
+            st2(A2 + b - PX, ld2(A2 + b));
+        }
+        const int t = b + (n - 1) * PX;
+        if (gy_r0 + n - 1 == ny - 1) {
+            st2(A0 + t + PX, ld2(A0 + t));
+            st2(A1 + t + PX, ld2(A1 + t));
+            st2(A2 + t + PX, ld2(A2 + t));
+        }
     }
-
-    // vapor: D L(rho) - div(rho v) - S, reservoir value above the top row
-    const f2 rN = top ? F2(k.rho_top) : R.N;
-    const f2 hs = make_float2(R.W + R.C.y, R.C.x + R.E);
-    const f2 lap = fma2(F2(-4.f), R.C, add2(hs, add2(rN, R.S)));
-    const f2 rx = make_float2(R.C.y - R.W, R.E - R.C.x);
-    const f2 adv = fma2(F2(k.ax), rx, mul2(F2(k.ay), sub2(rN, R.S)));
-    Rr = sub2(fma2(F2(k.cD), lap, neg2(adv)), Src);
 }
 
-template <int TX, int TY, int THREADS, int PHI_MODE, int MOB>
-__global__ void __launch_bounds__(THREADS)
+// L2 / L4: right-hand side of one pair column over rows [r0, r0+n).
+// A0..A2: mu_c, mu_phi, M; P, R: the phi and rho the source and vapor terms use;
+// Uc: the state the update starts from (phi, c, rho planes at Uc, Uc+PLANE, Uc+2 PLANE).
+// FINAL = false: u* = u^n + dt/2 R into Bout (with ghost rows); true: u^{n+1} to global.
+template <int L, int PX, int PLANE, int PHI_MODE, bool FINAL>
+__device__ __forceinline__ void level_rhs(const StepConst& k, const float* __restrict__ A0,
+                                          const float* __restrict__ A1, const float* __restrict__ A2,
+                                          const float* __restrict__ P, const float* __restrict__ R,
+                                          const float* __restrict__ Uc, float* __restrict__ Bout, int o, int r0,
+                                          int n, int gy_r0, int ny, float* __restrict__ g_phi,
+                                          float* __restrict__ g_c, float* __restrict__ g_rho, size_t g_off,
+                                          int pitch, bool store_x, bool pair_full)
+{
+    f2 mw[3], Mw[3], uw[3], fw[3], rw[3];
+    const int b = o + r0 * PX;
+    mw[0] = ld2(A0 + b - PX); mw[1] = ld2(A0 + b);
+    Mw[0] = ld2(A2 + b - PX); Mw[1] = ld2(A2 + b);
+    fw[0] = ld2(P + b - PX);  fw[1] = ld2(P + b);
+    rw[0] = ld2(R + b - PX);  rw[1] = ld2(R + b);
+    if (PHI_MODE == 0) { uw[0] = ld2(A1 + b - PX); uw[1] = ld2(A1 + b); }
+    const f2 hdt = F2(FINAL ? k.dt : 0.5f * k.dt);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        if (i < n) {
+            const int iS = i % 3, iC = (i + 1) % 3, iN = (i + 2) % 3;
+            const int q = b + i * PX;
+            mw[iN] = ld2(A0 + q + PX);
+            Mw[iN] = ld2(A2 + q + PX);
+            fw[iN] = ld2(P + q + PX);
+            rw[iN] = ld2(R + q + PX);
+            if (PHI_MODE == 0) uw[iN] = ld2(A1 + q + PX);
+
+            // conserved composition flux: sum_faces (M + M_nb)(mu_nb - mu) / (2 dx^2)
+            const f2 m = mw[iC], M = Mw[iC];
+            const float mW = A0[q - 1], mE = A0[q + 2], MW = A2[q - 1], ME = A2[q + 2];
+            const float Fa = (MW + M.x) * (m.x - mW);   // face (x-1 | x)
+            const float Fb = (M.x + M.y) * (m.y - m.x);  // face (x | x+1)
+            const float Fc = (M.y + ME) * (mE - m.y);    // face (x+1 | x+2)
+            f2 rc = make_float2(Fb - Fa, Fc - Fb);
+            rc = fma2(add2(M, Mw[iN]), sub2(mw[iN], m), rc);
+            rc = fma2(add2(M, Mw[iS]), sub2(mw[iS], m), rc);
+
+            // deposition source S = grad(phi) . (rho v), central differences
+            const f2 f = fw[iC], r = rw[iC];
+            const float fW = P[q - 1], fE = P[q + 2], rW = R[q - 1], rE = R[q + 2];
+            const f2 gx = make_float2(f.y - fW, fE - f.x);
+            const f2 Src = mul2(r, fma2(F2(k.ax), gx, mul2(F2(k.ay), sub2(fw[iN], fw[iS]))));
+
+            f2 Rf;
+            if (PHI_MODE == 0) {
+                const f2 u = uw[iC];
+                const f2 su = add2(hsum(A1[q - 1], u, A1[q + 2]), add2(uw[iN], uw[iS]));
+                Rf = fma2(F2(k.cF), fma2(F2(-4.f), u, su), Src);
+            } else {
+                Rf = fma2(F2(k.cF), ld2(A1 + q), Src);
+            }
+            // vapor: D L(rho) - div(rho v) - S (the ghost above the top row holds rho_top)
+            const f2 lap = fma2(F2(-4.f), r, add2(hsum(rW, r, rE), add2(rw[iN], rw[iS])));
+            const f2 adv = fma2(F2(k.ax), make_float2(r.y - rW, rE - r.x), mul2(F2(k.ay), sub2(rw[iN], rw[iS])));
+            const f2 Rr = sub2(fma2(F2(k.cD), lap, neg2(adv)), Src);
+
+            const f2 of = fma2(hdt, Rf, ld2(Uc + q));
+            const f2 oc = fma2(hdt, mul2(rc, F2(k.cR)), ld2(Uc + PLANE + q));
+            const f2 orr = fma2(hdt, Rr, ld2(Uc + 2 * PLANE + q));
+            if (!FINAL) {
+                st2(Bout + q, of);
+                st2(Bout + PLANE + q, oc);
+                st2(Bout + 2 * PLANE + q, orr);
+            } else if (store_x) {
+                const size_t g = g_off + size_t(i) * pitch;
+                if (pair_full) {
+                    st2(g_phi + g, of);
+                    st2(g_c + g, oc);
+                    st2(g_rho + g, orr);
+                } else {
+                    g_phi[g] = of.x;
+                    g_c[g] = oc.x;
+                    g_rho[g] = orr.x;
+                }
+            }
+        }
+    }
+    if (!FINAL && n > 0) {  // ghosts: mirror below the bottom row; above the top, mirror and rho_top
+        if (gy_r0 == 0) {
+            st2(Bout + b - PX, ld2(Bout + b));
+            st2(Bout + PLANE + b - PX, ld2(Bout + PLANE + b));
+            st2(Bout + 2 * PLANE + b - PX, ld2(Bout + 2 * PLANE + b));
+        }
+        const int t = b + (n - 1) * PX;
+        if (gy_r0 + n - 1 == ny - 1) {
+            st2(Bout + t + PX, ld2(Bout + t));
+            st2(Bout + PLANE + t + PX, ld2(Bout + PLANE + t));
+            st2(Bout + 2 * PLANE + t + PX, F2(k.rho_top));
+        }
+    }
+}
+
+template <int TX, int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TX, TY, S>::THREADS)
 step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
             const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
             float* __restrict__ rho1)
 {
-    using G = Geo<TX, TY>;
+    using G = Geo<TX, TY, S>;
+    constexpr int PX = G::PX, PLANE = G::PLANE;
     extern __shared__ __align__(16) float sm[];
-    float* const U = sm;                  // u^n: phi, c, rho
-    float* const A = sm + 3 * G::PLANE;   // mu_c, mu_phi, M
-    float* const B = sm + 6 * G::PLANE;   // u*: phi, c, rho
+    float* const U = sm;               // u^n: phi, c, rho
+    float* const A = sm + 3 * PLANE;   // mu_c, mu_phi, M
+    float* const B = sm + 6 * PLANE;   // u*: phi, c, rho
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int gx0 = x0 - HALO, gy0 = y0 - HALO;
     const int nx = k.nx, ny = k.ny, pitch = k.pitch;
 
-    // ---- stage u^n (rows outside the domain are zero and never read by domain rows)
     // Wait for the previous step's grid (programmatic dependent launch) before reading.
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    auto field = [&](int f) { return f == 0 ? phi0 : (f == 1 ? c0 : rho0); };
-    auto wrap = [&](int gx) {  // periodic x; one correction suffices when nx >= LX
-        if (nx >= G::LX) {
-            gx = gx < 0 ? gx + nx : gx;
-            return gx >= nx ? gx - nx : gx;
-        }
-        gx %= nx;
-        return gx < 0 ? gx + nx : gx;
-    };
-    if ((nx & 3) == 0) {
-        // x0 and nx are multiples of 4, so every aligned group of 4 staged columns
-        // is either wholly inside [0, nx) or wholly wrapped
-        constexpr int Q = G::LX / 4;
-        for (int idx = tid; idx < 3 * G::LY * Q; idx += THREADS) {
-            const int fld = idx / (G::LY * Q);
-            const int rem = idx - fld * (G::LY * Q);
-            const int ly = rem / Q, q = rem - ly * Q;
-            const int gy = gy0 + ly;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gy >= 0 && gy < ny)
-                v = __ldg(reinterpret_cast<const float4*>(field(fld) + (size_t)gy * pitch + wrap(gx0 + 4 * q)));
-            *reinterpret_cast<float4*>(U + fld * G::PLANE + ly * G::PX + PAD + 4 * q) = v;
-        }
-    } else {
-        for (int idx = tid; idx < 3 * G::LY * G::LX; idx += THREADS) {
-            const int fld = idx / (G::LY * G::LX);
-            const int rem = idx - fld * (G::LY * G::LX);
-            const int ly = rem / G::LX, lx = rem - ly * G::LX;
-            const int gy = gy0 + ly;
-            float v = 0.f;
-            if (gy >= 0 && gy < ny) v = __ldg(field(fld) + (size_t)gy * pitch + wrap(gx0 + lx));
-            U[fld * G::PLANE + ly * G::PX + PAD + lx] = v;
+
+    // ---- stage u^n: domain rows, plus the ghost rows -1 and ny by the boundary rules
+    // (mirror; rho above the top = rho_top); other out-of-domain rows are zero.
+    // Every 16-byte group is an asynchronous global->shared copy, all in flight at once.
+    {
+        auto field = [&](int f) { return f == 0 ? phi0 : (f == 1 ? c0 : rho0); };
+        auto wrap = [&](int gx) {  // periodic x; one correction suffices when nx >= LX
+            if (nx >= G::LX) {
+                gx = gx < 0 ? gx + nx : gx;
+                return gx >= nx ? gx - nx : gx;
+            }
+            gx %= nx;
+            return gx < 0 ? gx + nx : gx;
+        };
+        if ((nx & 3) == 0) {
+            // x0 and nx are multiples of 4: each aligned group of 4 staged columns is
+            // wholly inside [0, nx) or wholly wrapped
+            constexpr int Q = G::LX / 4;
+            for (int idx = tid; idx < 3 * G::LY * Q; idx += G::THREADS) {
+                const int fld = idx / (G::LY * Q);
+                const int rem = idx - fld * (G::LY * Q);
+                const int ly = rem / Q, q = rem - ly * Q;
+                int gy = gy0 + ly;
+                float* dst = U + fld * PLANE + ly * PX + PAD + 4 * q;
+                if ((fld == 2 && gy == ny) || gy < -1 || gy > ny) {
+                    const float v = (gy == ny) ? k.rho_top : 0.f;
+                    *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
+                } else {
+                    gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+                    const float* src = field(fld) + (size_t)gy * pitch + wrap(gx0 + 4 * q);
+                    const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(src) : "memory");
+                }
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        } else {
+            for (int idx = tid; idx < 3 * G::LY * G::LX; idx += G::THREADS) {
+                const int fld = idx / (G::LY * G::LX);
+                const int rem = idx - fld * (G::LY * G::LX);
+                const int ly = rem / G::LX, lx = rem - ly * G::LX;
+                int gy = gy0 + ly;
+                float v = 0.f;
+                if (fld == 2 && gy == ny) {
+                    v = k.rho_top;
+                } else if (gy >= -1 && gy <= ny) {
+                    gy = gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
+                    v = __ldg(field(fld) + (size_t)gy * pitch + wrap(gx0 + lx));
+                }
+                U[fld * PLANE + ly * PX + PAD + lx] = v;
+            }
         }
     }
     // Let the next step's grid begin launching; it waits for this grid to finish.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __syncthreads();
 
-    // Row-neighbour offsets with the boundary rules folded in.
-    auto offs = [&](int ly, int& up, int& dn, bool& top) {
-        const int gy = gy0 + ly;
-        top = (gy == ny - 1);
-        up = (gy >= ny - 1) ? 0 : G::PX;
-        dn = (gy <= 0) ? 0 : -G::PX;
-    };
+    const int pc = tid % G::NPC, s = tid / G::NPC;
+    const int o = PAD + 2 * pc;
+    // staged rows holding domain rows: [dlo, dhi)
+    const int dlo = -gy0 > 0 ? -gy0 : 0;
+    const int dhi = ny - gy0 < G::LY ? ny - gy0 : G::LY;
+    int r0, n;
 
-    // ---- L1: mu, M of u^n over rows [1, LY-1), all staged columns
-    {
-        constexpr int NP = G::LX / 2, NR = G::LY - 2;
-        for (int idx = tid; idx < NP * NR; idx += THREADS) {
-            const int r = idx / NP, pc = idx - r * NP;
-            const int ly = 1 + r, o = ly * G::PX + PAD + 2 * pc;
-            int up, dn; bool top;
-            offs(ly, up, dn, top);
-            level_mu<MOB>(k, U + o, U + G::PLANE + o, up, dn, A + o, A + G::PLANE + o, A + 2 * G::PLANE + o);
-        }
-    }
+    // ---- L1: mu, M of u^n on staged rows [1, LY-1)
+    segment(dlo > 1 ? dlo : 1, dhi < G::LY - 1 ? dhi : G::LY - 1, S, s, r0, n);
+    level_mu<G::L1, PX, MOB>(k, U, U + PLANE, A, A + PLANE, A + 2 * PLANE, o, r0, n, gy0 + r0, ny);
     __syncthreads();
 
-    // ---- L2: u* over rows [2, LY-2), columns [2, LX-2)
-    {
-        constexpr int NP = (G::LX - 4) / 2, NR = G::LY - 4;
-        const f2 hdt = F2(0.5f * k.dt);
-        for (int idx = tid; idx < NP * NR; idx += THREADS) {
-            const int r = idx / NP, pc = idx - r * NP;
-            const int ly = 2 + r, o = ly * G::PX + PAD + 2 + 2 * pc;
-            int up, dn; bool top;
-            offs(ly, up, dn, top);
-            f2 Rf, Rc, Rr;
-            level_rhs<PHI_MODE>(k, A + o, A + G::PLANE + o, A + 2 * G::PLANE + o, U + o, U + 2 * G::PLANE + o,
-                                up, dn, top, Rf, Rc, Rr);
-            *reinterpret_cast<f2*>(B + o) = fma2(hdt, Rf, *reinterpret_cast<const f2*>(U + o));
-            *reinterpret_cast<f2*>(B + G::PLANE + o) =
-                fma2(hdt, Rc, *reinterpret_cast<const f2*>(U + G::PLANE + o));
-            *reinterpret_cast<f2*>(B + 2 * G::PLANE + o) =
-                fma2(hdt, Rr, *reinterpret_cast<const f2*>(U + 2 * G::PLANE + o));
-        }
-    }
+    // ---- L2: u* on staged rows [2, LY-2)
+    segment(dlo > 2 ? dlo : 2, dhi < G::LY - 2 ? dhi : G::LY - 2, S, s, r0, n);
+    level_rhs<G::L2, PX, PLANE, PHI_MODE, false>(k, A, A + PLANE, A + 2 * PLANE, U, U + 2 * PLANE, U, B, o, r0, n,
+                                                 gy0 + r0, ny, nullptr, nullptr, nullptr, 0, 0, false, false);
     __syncthreads();
 
-    // ---- L3: mu, M of u* over rows [3, LY-3), columns [2, LX-2)
-    {
-        constexpr int NP = (G::LX - 4) / 2, NR = G::LY - 6;
-        for (int idx = tid; idx < NP * NR; idx += THREADS) {
-            const int r = idx / NP, pc = idx - r * NP;
-            const int ly = 3 + r, o = ly * G::PX + PAD + 2 + 2 * pc;
-            int up, dn; bool top;
-            offs(ly, up, dn, top);
-            level_mu<MOB>(k, B + o, B + G::PLANE + o, up, dn, A + o, A + G::PLANE + o, A + 2 * G::PLANE + o);
-        }
-    }
+    // ---- L3: mu, M of u* on staged rows [3, LY-3)
+    segment(dlo > 3 ? dlo : 3, dhi < G::LY - 3 ? dhi : G::LY - 3, S, s, r0, n);
+    level_mu<G::L3, PX, MOB>(k, B, B + PLANE, A, A + PLANE, A + 2 * PLANE, o, r0, n, gy0 + r0, ny);
     __syncthreads();
 
-    // ---- L4: u^{n+1} over the TX x TY output block
-    {
-        constexpr int NP = TX / 2;
-        const f2 dt = F2(k.dt);
-        for (int idx = tid; idx < NP * TY; idx += THREADS) {
-            const int r = idx / NP, pc = idx - r * NP;
-            const int ly = HALO + r, o = ly * G::PX + PAD + HALO + 2 * pc;
-            const int gy = y0 + r, gx = x0 + 2 * pc;
-            if (gy >= ny || gx >= nx) continue;
-            int up, dn; bool top;
-            offs(ly, up, dn, top);
-            f2 Rf, Rc, Rr;
-            level_rhs<PHI_MODE>(k, A + o, A + G::PLANE + o, A + 2 * G::PLANE + o, B + o, B + 2 * G::PLANE + o,
-                                up, dn, top, Rf, Rc, Rr);
-            const f2 out[3] = {fma2(dt, Rf, *reinterpret_cast<const f2*>(U + o)),
-                               fma2(dt, Rc, *reinterpret_cast<const f2*>(U + G::PLANE + o)),
-                               fma2(dt, Rr, *reinterpret_cast<const f2*>(U + 2 * G::PLANE + o))};
-            const size_t g = (size_t)gy * pitch + gx;
-            if (gx + 1 < nx) {
-                *reinterpret_cast<f2*>(phi1 + g) = out[0];
-                *reinterpret_cast<f2*>(c1 + g) = out[1];
-                *reinterpret_cast<f2*>(rho1 + g) = out[2];
-            } else {
-                phi1[g] = out[0].x;
-                c1[g] = out[1].x;
-                rho1[g] = out[2].x;
-            }
-        }
-    }
+    // ---- L4: u^{n+1} on the output rows [4, 4+TY), stored for output columns in the domain
+    segment(dlo > HALO ? dlo : HALO, dhi < HALO + TY ? dhi : HALO + TY, S, s, r0, n);
+    const int gx = gx0 + 2 * pc;  // global column of the pair's first cell
+    const bool store_x = (2 * pc >= HALO) && (2 * pc < HALO + TX) && gx < nx;
+    const bool pair_full = gx + 1 < nx;
+    const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
+    level_rhs<G::L4, PX, PLANE, PHI_MODE, true>(k, A, A + PLANE, A + 2 * PLANE, B, B + 2 * PLANE, U, nullptr, o, r0,
+                                                n, gy0 + r0, ny, phi1, c1, rho1, g_off, pitch, store_x, pair_full);
 }
 
-template <int TX, int TY, int THREADS, int PHI_MODE, int MOB>
+template <int TX, int TY, int S, int PHI_MODE, int MOB>
 cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const float* r0, float* f1,
                      float* c1, float* r1, cudaStream_t s)
 {
-    using G = Geo<TX, TY>;
-    auto kern = step_kernel<TX, TY, THREADS, PHI_MODE, MOB>;
+    using G = Geo<TX, TY, S>;
+    auto kern = step_kernel<TX, TY, S, PHI_MODE, MOB>;
     static bool configured = false;  // the attribute is per function; setting it twice is harmless
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES);
@@ -310,7 +374,7 @@ cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY);
-    cfg.blockDim = dim3(THREADS);
+    cfg.blockDim = dim3(G::THREADS);
     cfg.dynamicSmemBytes = G::BYTES;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -321,18 +385,18 @@ cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const
     return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1);
 }
 
-template <int TX, int TY, int THREADS>
+template <int TX, int TY, int S>
 cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s)
 {
     if (phi_mode == 0) {
-        if (mob == MOB_UNIFORM) return launch_t<TX, TY, THREADS, 0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
-        if (mob == MOB_BULK) return launch_t<TX, TY, THREADS, 0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
-        return launch_t<TX, TY, THREADS, 0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
+        if (mob == MOB_UNIFORM) return launch_t<TX, TY, S, 0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
+        if (mob == MOB_BULK) return launch_t<TX, TY, S, 0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
+        return launch_t<TX, TY, S, 0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
     }
-    if (mob == MOB_UNIFORM) return launch_t<TX, TY, THREADS, 1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
-    if (mob == MOB_BULK) return launch_t<TX, TY, THREADS, 1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
-    return launch_t<TX, TY, THREADS, 1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
+    if (mob == MOB_UNIFORM) return launch_t<TX, TY, S, 1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
+    if (mob == MOB_BULK) return launch_t<TX, TY, S, 1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
+    return launch_t<TX, TY, S, 1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
 }
 
 }  // namespace
@@ -343,16 +407,29 @@ int choose_tile(int nx, int ny)
     return (long long)nx * ny <= (1LL << 20) ? TILE_SMALL : TILE_LARGE;
 }
 
+#ifndef PF_SMALL_TX
+#define PF_SMALL_TX 32
+#define PF_SMALL_TY 16
+#define PF_SMALL_S 8
+#endif
+#ifndef PF_LARGE_TX
+#define PF_LARGE_TX 64
+#define PF_LARGE_TY 32
+#define PF_LARGE_S 8
+#endif
+#define PF_SMALL_TILE PF_SMALL_TX, PF_SMALL_TY, PF_SMALL_S
+#define PF_LARGE_TILE PF_LARGE_TX, PF_LARGE_TY, PF_LARGE_S
+
 size_t step_smem_bytes(int tile)
 {
-    return tile == TILE_SMALL ? Geo<32, 16>::BYTES : Geo<64, 32>::BYTES;
+    return tile == TILE_SMALL ? Geo<PF_SMALL_TILE>::BYTES : Geo<PF_LARGE_TILE>::BYTES;
 }
 
 cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob, const float* f0, const float* c0,
                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s)
 {
-    if (tile == TILE_SMALL) return launch_tile<32, 16, 256>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
-    return launch_tile<64, 32, 256>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+    if (tile == TILE_SMALL) return launch_tile<PF_SMALL_TILE>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+    return launch_tile<PF_LARGE_TILE>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
 }
 
 }  // namespace pf
