@@ -13,11 +13,12 @@
 //   L4  u^{n+1} = u^n + dt R(u*) -> global memory
 // so a step is one launch with 24 B of algorithmic HBM traffic per cell.
 //
-// Work layout: every thread owns one pair of x-adjacent columns and, in each
+// Work layout: every thread owns four x-adjacent columns (a quad) and, in each
 // level, streams down a segment of rows with a three-row register window, so a
 // vertical neighbour is a register and each staged value is loaded from shared
-// memory once per level (plus the two scalar west/east neighbours).  The pair
-// is computed with packed FP32x2 arithmetic (fma/add/mul .f32x2).
+// memory once per level as one 16-byte load (plus the two scalar west/east
+// neighbours of the quad).  Quads are computed as two pairs with packed FP32x2
+// arithmetic (fma/add/mul .f32x2).
 //
 // Boundary rules are applied once, where a level stores its results: the
 // bottom and top domain rows are also written into the ghost row outside them
@@ -29,37 +30,55 @@
 namespace pf {
 namespace {
 
-// Pair arithmetic: packed .f32x2 instructions (PF_PACKED=1) or two scalar FP32 ops.
-#ifndef PF_PACKED
-#define PF_PACKED 1
-#endif
 typedef float2 f2;
 __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
-#if PF_PACKED
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
-#else
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-#endif
-__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
+
+// Four x-adjacent cells as two packed pairs: lo = (x, x+1), hi = (x+2, x+3).
+struct q4 {
+    f2 lo, hi;
+};
+__device__ __forceinline__ q4 Q(float a) { return {F2(a), F2(a)}; }
+__device__ __forceinline__ q4 qadd(q4 a, q4 b) { return {add2(a.lo, b.lo), add2(a.hi, b.hi)}; }
+__device__ __forceinline__ q4 qmul(q4 a, q4 b) { return {mul2(a.lo, b.lo), mul2(a.hi, b.hi)}; }
+__device__ __forceinline__ q4 qfma(q4 a, q4 b, q4 c) { return {fma2(a.lo, b.lo, c.lo), fma2(a.hi, b.hi, c.hi)}; }
+__device__ __forceinline__ q4 qsub(q4 a, q4 b) { return qfma(b, Q(-1.f), a); }
+__device__ __forceinline__ q4 qneg(q4 a) { return {make_float2(-a.lo.x, -a.lo.y), make_float2(-a.hi.x, -a.hi.y)}; }
+__device__ __forceinline__ q4 ld4(const float* p)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st4(float* p, q4 v)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v.lo.x, v.lo.y, v.hi.x, v.hi.y);
+}
+// Horizontal neighbour sums u[x-1] + u[x+1] of the quad, given its west and east neighbours.
+__device__ __forceinline__ q4 hsum(float W, q4 C, float E)
+{
+    return {make_float2(W + C.lo.y, C.lo.x + C.hi.x), make_float2(C.lo.y + C.hi.y, C.hi.x + E)};
+}
+// Central differences u[x+1] - u[x-1] of the quad.
+__device__ __forceinline__ q4 hdiff(float W, q4 C, float E)
+{
+    return {make_float2(C.lo.y - W, C.hi.x - C.lo.x), make_float2(C.hi.y - C.lo.y, E - C.hi.x)};
+}
 
 constexpr int HALO = 4;
-constexpr int PAD = 4;  // left padding of a staged row (keeps float4 staging 16-B aligned)
+constexpr int PAD = 4;  // left padding of a staged row (keeps 16-B alignment)
 
 template <int TX, int TY, int S>
 struct Geo {
+    static_assert(TX % 4 == 0, "tile width must be a multiple of 4");
     static constexpr int LX = TX + 2 * HALO;  // staged columns
     static constexpr int LY = TY + 2 * HALO;  // staged rows
     static constexpr int PX = LX + PAD;       // row pitch in floats; the east neighbour of the last
                                               // column reads the next row's padding (never used)
     static constexpr int PLANE = LY * PX;
-    static constexpr int NPC = LX / 2;        // pair columns = threads per row segment
-    static constexpr int THREADS = NPC * S;   // S row segments
+    static constexpr int NQC = LX / 4;        // quad columns = threads per row segment
+    static constexpr int THREADS = NQC * S;   // S row segments
     static constexpr size_t BYTES = (size_t(9) * PLANE + 8) * sizeof(float);  // + tail guard
     static constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
     static constexpr int L1 = cdiv(LY - 2, S);  // longest segment of each level
@@ -68,14 +87,8 @@ struct Geo {
     static constexpr int L4 = cdiv(TY, S);
 };
 
-__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
-__device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
-
-// Horizontal neighbour sum of the pair (x, x+1): (u[x-1] + u[x+1], u[x] + u[x+2]).
-__device__ __forceinline__ f2 hsum(float W, f2 C, float E) { return make_float2(W + C.y, C.x + E); }
-
 // p(phi) = 1/4 (2-phi)(1+phi)^2 = 1/2 + 3/4 phi - 1/4 phi^3
-__device__ __forceinline__ f2 p_of(f2 f, f2 ff) { return fma2(fma2(F2(-0.25f), ff, F2(0.75f)), f, F2(0.5f)); }
+__device__ __forceinline__ q4 p_of(q4 f, q4 ff) { return qfma(qfma(Q(-0.25f), ff, Q(0.75f)), f, Q(0.5f)); }
 
 // Rows [lo, hi) of a level split into S near-equal segments; segment s of them.
 __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, int& n)
@@ -85,76 +98,77 @@ __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, i
     n = lo + ((s + 1) * H) / S - r0;
 }
 
-// L1 / L3: mu_c, mu_phi and M_c of the staged (phi, c) over rows [r0, r0+n) of
-// one pair column; o is the offset of (row 0, this pair) in a plane.
+// L1 / L3: mu_c, mu_phi and M_c of the staged (phi, c) over rows [r0, r0+n) of one
+// quad column; o is the offset of (row 0, this quad) in a plane.
 template <int L, int PX, int MOB>
 __device__ __forceinline__ void level_mu(const StepConst& k, const float* __restrict__ P,
                                          const float* __restrict__ Cp, float* __restrict__ A0,
                                          float* __restrict__ A1, float* __restrict__ A2, int o, int r0, int n,
                                          int gy_r0, int ny)
 {
-    f2 fw[3], cw[3];
+    q4 fw[3], cw[3];
     const int b = o + r0 * PX;
-    fw[0] = ld2(P + b - PX);
-    fw[1] = ld2(P + b);
-    cw[0] = ld2(Cp + b - PX);
-    cw[1] = ld2(Cp + b);
+    fw[0] = ld4(P + b - PX);
+    fw[1] = ld4(P + b);
+    cw[0] = ld4(Cp + b - PX);
+    cw[1] = ld4(Cp + b);
 #pragma unroll
     for (int i = 0; i < L; ++i) {
         if (i < n) {
             const int iS = i % 3, iC = (i + 1) % 3, iN = (i + 2) % 3;
             const int q = b + i * PX;
-            fw[iN] = ld2(P + q + PX);
-            cw[iN] = ld2(Cp + q + PX);
-            const f2 f = fw[iC], c = cw[iC];
-            const f2 sf = add2(hsum(P[q - 1], f, P[q + 2]), add2(fw[iN], fw[iS]));
-            const f2 sc = add2(hsum(Cp[q - 1], c, Cp[q + 2]), add2(cw[iN], cw[iS]));
-            const f2 ff = mul2(f, f);
-            const f2 p = p_of(f, ff);
-            const f2 qq = fma2(neg2(c), c, c);                                   // c (1 - c)
-            const f2 g = mul2(qq, qq);                                           // g(c)
-            const f2 Wdg = mul2(qq, fma2(F2(-4.f * k.Wc), c, F2(2.f * k.Wc)));  // W_c g'(c)
+            fw[iN] = ld4(P + q + PX);
+            cw[iN] = ld4(Cp + q + PX);
+            const q4 f = fw[iC], c = cw[iC];
+            const q4 sf = qadd(hsum(P[q - 1], f, P[q + 4]), qadd(fw[iN], fw[iS]));
+            const q4 sc = qadd(hsum(Cp[q - 1], c, Cp[q + 4]), qadd(cw[iN], cw[iS]));
+            const q4 ff = qmul(f, f);
+            const q4 p = p_of(f, ff);
+            const q4 qq = qfma(qneg(c), c, c);                                  // c (1 - c)
+            const q4 g = qmul(qq, qq);                                          // g(c)
+            const q4 Wdg = qmul(qq, qfma(Q(-4.f * k.Wc), c, Q(2.f * k.Wc)));  // W_c g'(c)
             // mu_c = p W_c g' - kappa_c L(c)
-            f2 muc = fma2(F2(4.f * k.kc), c, mul2(p, Wdg));
-            muc = fma2(F2(-k.kc), sc, muc);
+            q4 muc = qfma(Q(4.f * k.kc), c, qmul(p, Wdg));
+            muc = qfma(Q(-k.kc), sc, muc);
             // mu_phi = -W_phi phi (1 - phi^2) + p'(phi) W_c g - kappa_phi L(phi),  p' = 3/4 (1 - phi^2)
-            f2 muf = mul2(fma2(F2(k.Wf), ff, F2(-k.Wf)), f);
-            muf = fma2(fma2(F2(-0.75f * k.Wc), ff, F2(0.75f * k.Wc)), g, muf);
-            muf = fma2(F2(4.f * k.kf), f, muf);
-            muf = fma2(F2(-k.kf), sf, muf);
+            q4 muf = qmul(qfma(Q(k.Wf), ff, Q(-k.Wf)), f);
+            muf = qfma(qfma(Q(-0.75f * k.Wc), ff, Q(0.75f * k.Wc)), g, muf);
+            muf = qfma(Q(4.f * k.kf), f, muf);
+            muf = qfma(Q(-k.kf), sf, muf);
             // M_c = p (MB + h dM) [+ exp(-(phi/sigma)^2)(MBs + h dMs)],  h = c^2 (3 - 2c)
-            f2 M;
+            q4 M;
             if (MOB == MOB_UNIFORM) {
-                M = mul2(p, F2(k.MBb));
+                M = qmul(p, Q(k.MBb));
             } else {
-                const f2 h = mul2(mul2(c, c), fma2(F2(-2.f), c, F2(3.f)));
-                M = mul2(p, fma2(h, F2(k.dMb), F2(k.MBb)));
+                const q4 h = qmul(qmul(c, c), qfma(Q(-2.f), c, Q(3.f)));
+                M = qmul(p, qfma(h, Q(k.dMb), Q(k.MBb)));
                 if (MOB == MOB_SURF) {
-                    const f2 t = mul2(ff, F2(k.nisig2));
-                    M = fma2(make_float2(exp2f(t.x), exp2f(t.y)), fma2(h, F2(k.dMs), F2(k.MBs)), M);
+                    const q4 t = qmul(ff, Q(k.nisig2));
+                    const q4 e = {make_float2(exp2f(t.lo.x), exp2f(t.lo.y)), make_float2(exp2f(t.hi.x), exp2f(t.hi.y))};
+                    M = qfma(e, qfma(h, Q(k.dMs), Q(k.MBs)), M);
                 }
             }
-            st2(A0 + q, muc);
-            st2(A1 + q, muf);
-            st2(A2 + q, M);
+            st4(A0 + q, muc);
+            st4(A1 + q, muf);
+            st4(A2 + q, M);
         }
     }
     if (n > 0) {  // mirror ghosts outside the bottom / top domain rows (own writes: no barrier)
         if (gy_r0 == 0) {
-            st2(A0 + b - PX, ld2(A0 + b));
-            st2(A1 + b - PX, ld2(A1 + b));
-            st2(A2 + b - PX, ld2(A2 + b));
+            st4(A0 + b - PX, ld4(A0 + b));
+            st4(A1 + b - PX, ld4(A1 + b));
+            st4(A2 + b - PX, ld4(A2 + b));
         }
         const int t = b + (n - 1) * PX;
         if (gy_r0 + n - 1 == ny - 1) {
-            st2(A0 + t + PX, ld2(A0 + t));
-            st2(A1 + t + PX, ld2(A1 + t));
-            st2(A2 + t + PX, ld2(A2 + t));
+            st4(A0 + t + PX, ld4(A0 + t));
+            st4(A1 + t + PX, ld4(A1 + t));
+            st4(A2 + t + PX, ld4(A2 + t));
         }
     }
 }
 
-// L2 / L4: right-hand side of one pair column over rows [r0, r0+n).
+// L2 / L4: right-hand side of one quad column over rows [r0, r0+n).
 // A0..A2: mu_c, mu_phi, M; P, R: the phi and rho the source and vapor terms use;
 // Uc: the state the update starts from (phi, c, rho planes at Uc, Uc+PLANE, Uc+2 PLANE).
 // FINAL = false: u* = u^n + dt/2 R into Bout (with ghost rows); true: u^{n+1} to global.
@@ -165,88 +179,96 @@ __device__ __forceinline__ void level_rhs(const StepConst& k, const float* __res
                                           const float* __restrict__ Uc, float* __restrict__ Bout, int o, int r0,
                                           int n, int gy_r0, int ny, float* __restrict__ g_phi,
                                           float* __restrict__ g_c, float* __restrict__ g_rho, size_t g_off,
-                                          int pitch, bool store_x, bool pair_full)
+                                          int pitch, bool store_x, int valid_x)
 {
-    f2 mw[3], Mw[3], uw[3], fw[3], rw[3];
+    q4 mw[3], Mw[3], uw[3], fw[3], rw[3];
     const int b = o + r0 * PX;
-    mw[0] = ld2(A0 + b - PX); mw[1] = ld2(A0 + b);
-    Mw[0] = ld2(A2 + b - PX); Mw[1] = ld2(A2 + b);
-    fw[0] = ld2(P + b - PX);  fw[1] = ld2(P + b);
-    rw[0] = ld2(R + b - PX);  rw[1] = ld2(R + b);
-    if (PHI_MODE == 0) { uw[0] = ld2(A1 + b - PX); uw[1] = ld2(A1 + b); }
-    const f2 hdt = F2(FINAL ? k.dt : 0.5f * k.dt);
+    mw[0] = ld4(A0 + b - PX); mw[1] = ld4(A0 + b);
+    Mw[0] = ld4(A2 + b - PX); Mw[1] = ld4(A2 + b);
+    fw[0] = ld4(P + b - PX);  fw[1] = ld4(P + b);
+    rw[0] = ld4(R + b - PX);  rw[1] = ld4(R + b);
+    if (PHI_MODE == 0) { uw[0] = ld4(A1 + b - PX); uw[1] = ld4(A1 + b); }
+    const q4 hdt = Q(FINAL ? k.dt : 0.5f * k.dt);
 #pragma unroll
     for (int i = 0; i < L; ++i) {
         if (i < n) {
             const int iS = i % 3, iC = (i + 1) % 3, iN = (i + 2) % 3;
             const int q = b + i * PX;
-            mw[iN] = ld2(A0 + q + PX);
-            Mw[iN] = ld2(A2 + q + PX);
-            fw[iN] = ld2(P + q + PX);
-            rw[iN] = ld2(R + q + PX);
-            if (PHI_MODE == 0) uw[iN] = ld2(A1 + q + PX);
+            mw[iN] = ld4(A0 + q + PX);
+            Mw[iN] = ld4(A2 + q + PX);
+            fw[iN] = ld4(P + q + PX);
+            rw[iN] = ld4(R + q + PX);
+            if (PHI_MODE == 0) uw[iN] = ld4(A1 + q + PX);
 
             // conserved composition flux: sum_faces (M + M_nb)(mu_nb - mu) / (2 dx^2)
-            const f2 m = mw[iC], M = Mw[iC];
-            const float mW = A0[q - 1], mE = A0[q + 2], MW = A2[q - 1], ME = A2[q + 2];
-            const float Fa = (MW + M.x) * (m.x - mW);   // face (x-1 | x)
-            const float Fb = (M.x + M.y) * (m.y - m.x);  // face (x | x+1)
-            const float Fc = (M.y + ME) * (mE - m.y);    // face (x+1 | x+2)
-            f2 rc = make_float2(Fb - Fa, Fc - Fb);
-            rc = fma2(add2(M, Mw[iN]), sub2(mw[iN], m), rc);
-            rc = fma2(add2(M, Mw[iS]), sub2(mw[iS], m), rc);
+            const q4 m = mw[iC], M = Mw[iC];
+            const float mW = A0[q - 1], mE = A0[q + 4], MW = A2[q - 1], ME = A2[q + 4];
+            const float F0 = (MW + M.lo.x) * (m.lo.x - mW);       // face (x-1 | x)
+            const float F1 = (M.lo.x + M.lo.y) * (m.lo.y - m.lo.x);  // face (x | x+1)
+            const float F2_ = (M.lo.y + M.hi.x) * (m.hi.x - m.lo.y);
+            const float F3 = (M.hi.x + M.hi.y) * (m.hi.y - m.hi.x);
+            const float F4 = (M.hi.y + ME) * (mE - m.hi.y);         // face (x+3 | x+4)
+            q4 rc = {make_float2(F1 - F0, F2_ - F1), make_float2(F3 - F2_, F4 - F3)};
+            rc = qfma(qadd(M, Mw[iN]), qsub(mw[iN], m), rc);
+            rc = qfma(qadd(M, Mw[iS]), qsub(mw[iS], m), rc);
 
             // deposition source S = grad(phi) . (rho v), central differences
-            const f2 f = fw[iC], r = rw[iC];
-            const float fW = P[q - 1], fE = P[q + 2], rW = R[q - 1], rE = R[q + 2];
-            const f2 gx = make_float2(f.y - fW, fE - f.x);
-            const f2 Src = mul2(r, fma2(F2(k.ax), gx, mul2(F2(k.ay), sub2(fw[iN], fw[iS]))));
+            const q4 f = fw[iC], r = rw[iC];
+            const float fW = P[q - 1], fE = P[q + 4], rW = R[q - 1], rE = R[q + 4];
+            const q4 Src = qmul(r, qfma(Q(k.ax), hdiff(fW, f, fE), qmul(Q(k.ay), qsub(fw[iN], fw[iS]))));
 
-            f2 Rf;
+            q4 Rf;
             if (PHI_MODE == 0) {
-                const f2 u = uw[iC];
-                const f2 su = add2(hsum(A1[q - 1], u, A1[q + 2]), add2(uw[iN], uw[iS]));
-                Rf = fma2(F2(k.cF), fma2(F2(-4.f), u, su), Src);
+                const q4 u = uw[iC];
+                const q4 su = qadd(hsum(A1[q - 1], u, A1[q + 4]), qadd(uw[iN], uw[iS]));
+                Rf = qfma(Q(k.cF), qfma(Q(-4.f), u, su), Src);
             } else {
-                Rf = fma2(F2(k.cF), ld2(A1 + q), Src);
+                Rf = qfma(Q(k.cF), ld4(A1 + q), Src);
             }
             // vapor: D L(rho) - div(rho v) - S (the ghost above the top row holds rho_top)
-            const f2 lap = fma2(F2(-4.f), r, add2(hsum(rW, r, rE), add2(rw[iN], rw[iS])));
-            const f2 adv = fma2(F2(k.ax), make_float2(r.y - rW, rE - r.x), mul2(F2(k.ay), sub2(rw[iN], rw[iS])));
-            const f2 Rr = sub2(fma2(F2(k.cD), lap, neg2(adv)), Src);
+            const q4 lap = qfma(Q(-4.f), r, qadd(hsum(rW, r, rE), qadd(rw[iN], rw[iS])));
+            const q4 adv = qfma(Q(k.ax), hdiff(rW, r, rE), qmul(Q(k.ay), qsub(rw[iN], rw[iS])));
+            const q4 Rr = qsub(qfma(Q(k.cD), lap, qneg(adv)), Src);
 
-            const f2 of = fma2(hdt, Rf, ld2(Uc + q));
-            const f2 oc = fma2(hdt, mul2(rc, F2(k.cR)), ld2(Uc + PLANE + q));
-            const f2 orr = fma2(hdt, Rr, ld2(Uc + 2 * PLANE + q));
+            const q4 of = qfma(hdt, Rf, ld4(Uc + q));
+            const q4 oc = qfma(hdt, qmul(rc, Q(k.cR)), ld4(Uc + PLANE + q));
+            const q4 orr = qfma(hdt, Rr, ld4(Uc + 2 * PLANE + q));
             if (!FINAL) {
-                st2(Bout + q, of);
-                st2(Bout + PLANE + q, oc);
-                st2(Bout + 2 * PLANE + q, orr);
+                st4(Bout + q, of);
+                st4(Bout + PLANE + q, oc);
+                st4(Bout + 2 * PLANE + q, orr);
             } else if (store_x) {
                 const size_t g = g_off + size_t(i) * pitch;
-                if (pair_full) {
-                    st2(g_phi + g, of);
-                    st2(g_c + g, oc);
-                    st2(g_rho + g, orr);
+                if (valid_x >= 4) {
+                    st4(g_phi + g, of);
+                    st4(g_c + g, oc);
+                    st4(g_rho + g, orr);
                 } else {
-                    g_phi[g] = of.x;
-                    g_c[g] = oc.x;
-                    g_rho[g] = orr.x;
+                    const float vf[4] = {of.lo.x, of.lo.y, of.hi.x, of.hi.y};
+                    const float vc[4] = {oc.lo.x, oc.lo.y, oc.hi.x, oc.hi.y};
+                    const float vr[4] = {orr.lo.x, orr.lo.y, orr.hi.x, orr.hi.y};
+#pragma unroll
+                    for (int e = 0; e < 3; ++e)
+                        if (e < valid_x) {
+                            g_phi[g + e] = vf[e];
+                            g_c[g + e] = vc[e];
+                            g_rho[g + e] = vr[e];
+                        }
                 }
             }
         }
     }
     if (!FINAL && n > 0) {  // ghosts: mirror below the bottom row; above the top, mirror and rho_top
         if (gy_r0 == 0) {
-            st2(Bout + b - PX, ld2(Bout + b));
-            st2(Bout + PLANE + b - PX, ld2(Bout + PLANE + b));
-            st2(Bout + 2 * PLANE + b - PX, ld2(Bout + 2 * PLANE + b));
+            st4(Bout + b - PX, ld4(Bout + b));
+            st4(Bout + PLANE + b - PX, ld4(Bout + PLANE + b));
+            st4(Bout + 2 * PLANE + b - PX, ld4(Bout + 2 * PLANE + b));
         }
         const int t = b + (n - 1) * PX;
         if (gy_r0 + n - 1 == ny - 1) {
-            st2(Bout + t + PX, ld2(Bout + t));
-            st2(Bout + PLANE + t + PX, ld2(Bout + PLANE + t));
-            st2(Bout + 2 * PLANE + t + PX, F2(k.rho_top));
+            st4(Bout + t + PX, ld4(Bout + t));
+            st4(Bout + PLANE + t + PX, ld4(Bout + PLANE + t));
+            st4(Bout + 2 * PLANE + t + PX, Q(k.rho_top));
         }
     }
 }
@@ -327,8 +349,8 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __syncthreads();
 
-    const int pc = tid % G::NPC, s = tid / G::NPC;
-    const int o = PAD + 2 * pc;
+    const int qc = tid % G::NQC, s = tid / G::NQC;
+    const int o = PAD + 4 * qc;
     // staged rows holding domain rows: [dlo, dhi)
     const int dlo = -gy0 > 0 ? -gy0 : 0;
     const int dhi = ny - gy0 < G::LY ? ny - gy0 : G::LY;
@@ -352,12 +374,12 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
 
     // ---- L4: u^{n+1} on the output rows [4, 4+TY), stored for output columns in the domain
     segment(dlo > HALO ? dlo : HALO, dhi < HALO + TY ? dhi : HALO + TY, S, s, r0, n);
-    const int gx = gx0 + 2 * pc;  // global column of the pair's first cell
-    const bool store_x = (2 * pc >= HALO) && (2 * pc < HALO + TX) && gx < nx;
-    const bool pair_full = gx + 1 < nx;
+    const int gx = gx0 + 4 * qc;  // global column of the quad's first cell
+    const bool store_x = (4 * qc >= HALO) && (4 * qc < HALO + TX) && gx < nx;
+    const int valid_x = nx - gx;  // cells of the quad inside the domain (>= 4: all)
     const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
     level_rhs<G::L4, PX, PLANE, PHI_MODE, true>(k, A, A + PLANE, A + 2 * PLANE, B, B + 2 * PLANE, U, nullptr, o, r0,
-                                                n, gy0 + r0, ny, phi1, c1, rho1, g_off, pitch, store_x, pair_full);
+                                                n, gy0 + r0, ny, phi1, c1, rho1, g_off, pitch, store_x, valid_x);
 }
 
 template <int TX, int TY, int S, int PHI_MODE, int MOB>
@@ -410,12 +432,12 @@ int choose_tile(int nx, int ny)
 #ifndef PF_SMALL_TX
 #define PF_SMALL_TX 32
 #define PF_SMALL_TY 16
-#define PF_SMALL_S 8
+#define PF_SMALL_S 16
 #endif
 #ifndef PF_LARGE_TX
 #define PF_LARGE_TX 64
 #define PF_LARGE_TY 32
-#define PF_LARGE_S 8
+#define PF_LARGE_S 16
 #endif
 #define PF_SMALL_TILE PF_SMALL_TX, PF_SMALL_TY, PF_SMALL_S
 #define PF_LARGE_TILE PF_LARGE_TX, PF_LARGE_TY, PF_LARGE_S
