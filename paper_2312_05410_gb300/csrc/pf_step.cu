@@ -385,7 +385,7 @@ cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* 
 }  // namespace
 
 #ifndef PF_SMALL_TY
-#define PF_SMALL_TY 16
+#define PF_SMALL_TY 8
 #define PF_SMALL_S 4
 #endif
 #ifndef PF_LARGE_TY
