@@ -154,6 +154,29 @@ int pf_diagnostics(const pf_params* p, int nx, int ny, int pitch,
                    const float* phi, const float* c, const float* rho,
                    void* work, size_t work_bytes, double* out_dev, void* stream);
 
+/*
+ * pf_diagnostics without a workspace, for callers that must not allocate
+ * device memory themselves (for example a plug-in inside an application that
+ * owns all device memory through its own pool, or a latency-critical loop in
+ * which cudaMalloc/cudaFree would synchronise the device).  The paper has no
+ * counterpart: this is a packaging variant of the diagnostics above.
+ *
+ * Same inputs and the same 4 doubles written to out_dev (device, 8-byte
+ * aligned) as pf_diagnostics.  If err_dev (device int) is not NULL it receives
+ * 1 when a field holds a NaN or Inf, else 0.  The reduction scratch is one
+ * static device array of 1216 x 4 doubles plus an error word (about 39 KB)
+ * that every GPU loading the library keeps until the process exits; any grid
+ * the library accepts (sides up to 2^20) fits in it, other sizes are rejected
+ * with PF_ERR_ARG / PF_ERR_LAYOUT.  The first call on each device performs a
+ * one-time set-up (it looks up the array's device address), so make that first
+ * call before any stream capture.  All calls share the array: calls that can
+ * overlap on the GPU (unordered streams) race.  Nothing is allocated.
+ * Returns PF_OK or a PF_ERR_* code; asynchronous on `stream`.
+ */
+int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
+                          const float* phi, const float* c, const float* rho,
+                          double* out_dev, int* err_dev, void* stream);
+
 /* Text for an error code, and the last error message of the calling thread. */
 const char* pf_strerror(int code);
 const char* pf_last_error(void);

@@ -67,6 +67,8 @@ def _load():
     L.pf_diag_error_offset.argtypes, L.pf_diag_error_offset.restype = [C.c_int, C.c_int], sz
     L.pf_diagnostics.argtypes = [P, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, sz, vp, vp]
     L.pf_diagnostics.restype = C.c_int
+    L.pf_diagnostics_static.argtypes = [P, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+    L.pf_diagnostics_static.restype = C.c_int
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
     L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
     return L
@@ -154,6 +156,13 @@ def pf_diagnostics(params: dict, nx: int, ny: int, pitch: int, phi_ptr: int, c_p
                    work_ptr: int, work_bytes: int, out_dev_ptr: int, stream: int) -> int:
     return lib.pf_diagnostics(C.byref(Params.from_dict(params)), nx, ny, pitch, phi_ptr, c_ptr, rho_ptr,
                               work_ptr, work_bytes, out_dev_ptr, stream)
+
+
+def pf_diagnostics_static(params: dict, nx: int, ny: int, pitch: int, phi_ptr: int, c_ptr: int, rho_ptr: int,
+                          out_dev_ptr: int, err_dev_ptr, stream: int) -> int:
+    """Diagnostics with no caller workspace (for callers that cannot allocate device memory)."""
+    return lib.pf_diagnostics_static(C.byref(Params.from_dict(params)), nx, ny, pitch, phi_ptr, c_ptr, rho_ptr,
+                                     out_dev_ptr, err_dev_ptr, stream)
 
 
 # ---------------------------------------------------------------- torch-backed simulation
