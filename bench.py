@@ -46,6 +46,9 @@ WORKLOADS = {
                       steps=2000, desc="plain DNS 4096x4096, 2000 steps, diagnostics every 1000"),
     "large8192": dict(spec=I.FilmSpec(8192, 8192, 16.0, seed=1), params=dict(v_mag=0.3, diag_every=1000),
                       steps=1000, desc="plain DNS 8192x8192, 1000 steps, diagnostics every 1000"),
+    "ensemble64": dict(kind="ensemble", n_runs=64, seed=3, steps=10000,
+                       desc="batched DNS ensemble: 64 runs, sides in {128,192,256,384,512}, V~U[0.1,0.9], "
+                            "c_inc~U[0.3,0.7], 10000 steps"),
 }
 
 # DRAM bytes per step-kernel launch from an ncu capture, keyed by workload, with the
@@ -120,6 +123,71 @@ def dist_env():
     return ws, rank, local
 
 
+class SingleRun:
+    """One plain-DNS run through pf.Sim (periodic diagnostics inside the graph)."""
+
+    def __init__(self, pf, W):
+        spec = W["spec"]
+        p = I.default_params(**W["params"])
+        p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
+        self.params = p
+        self.sim = pf.Sim(p, *I.film_state(spec, p), history_rows=W["steps"] // max(1, p["diag_every"]) + 2)
+        self.stream = self.sim.stream
+        self.fields = list(self.sim.fields)
+        self.cells = spec.nx * spec.ny
+        self.nsteps = W["steps"]
+        de = p["diag_every"]
+        self.launches = self.nsteps + (2 * ((self.nsteps + de - 1) // de) if de else 0)
+        self.config = {"nx": spec.nx, "ny": spec.ny, "timesteps_per_run": self.nsteps, "diag_every": de,
+                       "dt": p["dt"], "launch": "CUDA graph replays of fused step kernels"}
+
+    def reset_counters(self):
+        self.sim.set_step(0)
+
+    def run(self):
+        self.sim.step(self.nsteps)
+
+    def final_diag(self):
+        return [float(x) for x in self.sim.diag()]
+
+    def close(self):
+        self.sim.close()
+
+
+class EnsembleRun:
+    """Independent runs of uneven sizes, one launch per step for all of them."""
+
+    def __init__(self, pf, W):
+        ms = []
+        for m in I.ensemble_members(W["n_runs"], seed=W["seed"]):
+            p = I.default_params(v_mag=m["v_mag"])
+            p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
+            ms.append((p, *I.film_state(m["spec"], p)))
+        self.ens = pf.Ensemble(ms)
+        self.stream = self.ens.stream
+        self.fields = [t for run in self.ens.fields for t in run]
+        self.cells = sum(ny * nx for ny, nx in self.ens.shapes)
+        self.nsteps = W["steps"]
+        self.chosen, self.tune = self.ens.autotune(10)
+        self.launches = self.nsteps
+        sides = sorted({nx for _, nx in self.ens.shapes})
+        self.config = {"runs": len(ms), "sides": sides, "total_cells": self.cells, "timesteps_per_run": self.nsteps,
+                       "tile_kind": self.chosen, "autotune_s_per_step": self.tune,
+                       "launch": "one fused launch per step for all runs, CUDA graph replays"}
+
+    def reset_counters(self):
+        pass
+
+    def run(self):
+        self.ens.step(self.nsteps)
+
+    def final_diag(self):
+        return [float(x) for x in self.ens.diag(0)]
+
+    def close(self):
+        self.ens.close()
+
+
 def run_native(args):
     import torch
 
@@ -136,20 +204,16 @@ def run_native(args):
     from paper_2312_05410_gb300 import pf
 
     W = WORKLOADS[args.workload]
-    spec, nsteps = W["spec"], W["steps"]
-    p = I.default_params(**W["params"])
-    p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
-    state = I.film_state(spec, p)
-    sim = pf.Sim(p, *state, history_rows=nsteps // max(1, p["diag_every"]) + 2)
-    stream = sim.stream
-    init = [t.clone() for t in sim.fields]
+    R = EnsembleRun(pf, W) if W.get("kind") == "ensemble" else SingleRun(pf, W)
+    stream = R.stream
+    init = [t.clone() for t in R.fields]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
-    cells = spec.nx * spec.ny
+    cells, nsteps = R.cells, R.nsteps
 
     def reset():
-        for t, s in zip(sim.fields, init):
+        for t, s in zip(R.fields, init):
             t.copy_(s)
-        sim.set_step(0)
+        R.reset_counters()
         flush.zero_()
 
     def barrier():
@@ -160,7 +224,7 @@ def run_native(args):
 
     for _ in range(args.warmup):
         reset()
-        sim.step(nsteps)
+        R.run()
     torch.cuda.synchronize()
 
     # ---- timed region: K whole runs, each bracketed by events on the launch stream
@@ -171,7 +235,7 @@ def run_native(args):
         for a, b in evs:
             reset()
             a.record(stream)
-            sim.step(nsteps)
+            R.run()
             b.record(stream)
         barrier()
         wall = time.perf_counter() - t0
@@ -181,7 +245,7 @@ def run_native(args):
         t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_s = float(t.item())
-    final_diag = sim.diag()
+    final_diag = R.final_diag()
 
     # ---- end to end through the public API with host buffers (pinned H2D + D2H inside)
     host_in = [torch.from_numpy(np.ascontiguousarray(t.cpu().numpy())).pin_memory() for t in init]
@@ -189,15 +253,15 @@ def run_native(args):
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     for a, b in e2e_ev:
-        sim.set_step(0)
+        R.reset_counters()
         flush.zero_()
         a.record(stream)
         with torch.cuda.stream(stream):
-            for t, h in zip(sim.fields, host_in):
+            for t, h in zip(R.fields, host_in):
                 t.copy_(h, non_blocking=True)
-        sim.step(nsteps)
+        R.run()
         with torch.cuda.stream(stream):
-            for t, h in zip(sim.fields, host_out):
+            for t, h in zip(R.fields, host_out):
                 h.copy_(t, non_blocking=True)
         b.record(stream)
     barrier()
@@ -207,15 +271,13 @@ def run_native(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     io_bytes = sum(h.numel() * h.element_size() for h in host_in)
-    sim.close()
+    R.close()
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    updates = cells * nsteps * args.steps * ws
-    value = updates / total_s
-    launches_per_run = nsteps + 2 * ((nsteps + p["diag_every"] - 1) // p["diag_every"] if p["diag_every"] else 0)
+    value = cells * nsteps * args.steps * ws / total_s
     peaks = measured_peaks()
     # Dominant kernel: the fused step. Its average launch duration is bounded above by
     # the timed region per step launch (it also covers the diagnostic kernels and gaps).
@@ -227,19 +289,17 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": W["desc"], "nx": spec.nx, "ny": spec.ny, "timesteps_per_run": nsteps,
-                   "diag_every": p["diag_every"], "dt": p["dt"], "per_rank": "independent replica",
-                   "l2": "flushed between timed runs (256 MB write)",
-                   "launch": "CUDA graph replays of fused step kernels"},
+        "config": dict({"workload": W["desc"], "per_rank": "independent replica",
+                        "l2": "flushed between timed runs (256 MB write)"}, **R.config),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peaks["source"], "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
-        "gpu_launches": launches_per_run * args.steps,
+        "gpu_launches": R.launches * args.steps,
         "e2e": {"value": cells * nsteps * args.steps * ws / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "clocks": clk.summary(),
         "wall_s": wall,
-        "final_diag": [float(x) for x in final_diag],
+        "final_diag": final_diag,
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
@@ -248,13 +308,22 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def oracle_problem(W):
+    """(spec, params, what) of the grid the CPU oracle samples for workload W."""
+    import oracle as O
+
+    if W.get("kind") == "ensemble":
+        m = I.ensemble_members(W["n_runs"], seed=W["seed"])[0]
+        return m["spec"], O.with_dt(I.default_params(v_mag=m["v_mag"])), "run 0 of the ensemble"
+    return W["spec"], O.with_dt(I.default_params(**W["params"])), "the"
+
+
 def cpu_baseline(workload: str, budget_s: float = 15.0, steps: int | None = None) -> dict:
     """Time the FP64 oracle (single thread, as it stands) on a bounded sample of the workload."""
     import oracle as O
 
     W = WORKLOADS[workload]
-    spec = W["spec"]
-    p = O.with_dt(I.default_params(**W["params"]))
+    spec, p, what = oracle_problem(W)
     state = I.film_state(spec, p)
     O.step(p, *state, 1)  # load and warm the library
     if steps is None:
@@ -266,7 +335,7 @@ def cpu_baseline(workload: str, budget_s: float = 15.0, steps: int | None = None
     O.step(p, *state, steps)
     dt = time.perf_counter() - t
     return {"value": spec.nx * spec.ny * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{spec.nx}x{spec.ny} grid, first {steps} of the {W['steps']} steps, FP64, single thread",
+            "sample": f"{what} {spec.nx}x{spec.ny} grid, first {steps} of the {W['steps']} steps, FP64, single thread",
             "seconds": dt}
 
 
@@ -275,10 +344,9 @@ def run_reference(args):
     if rank != 0:
         return
     W = WORKLOADS[args.workload]
-    spec = W["spec"]
     import oracle as O
 
-    p = O.with_dt(I.default_params(**W["params"]))
+    spec, p, _ = oracle_problem(W)
     state = I.film_state(spec, p)
     # size one sample step so that warmup + timed steps take about a minute in total
     t = time.perf_counter()

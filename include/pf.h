@@ -177,6 +177,42 @@ int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
                           const float* phi, const float* c, const float* rho,
                           double* out_dev, int* err_dev, void* stream);
 
+/*
+ * Ensemble: nruns independent runs (uneven grid sizes, per-run parameters; the
+ * paper's dataset is such a sweep over deposition rate, angle and mobilities,
+ * "Dataset") advanced in lockstep.  Every step of every run is ONE launch of
+ * the fused step kernel over a table of tiles of all runs; long stretches are
+ * replays of a captured CUDA graph.  All runs must share phi_mode and the
+ * mobility form (uniform / bulk / bulk + surface); their coefficients, dt,
+ * velocity, sizes and pitches may differ.  diag_every is ignored.
+ *
+ * pf_ens_workspace_size: bytes of caller-owned device workspace (ping-pong
+ *   partner of every run, run and tile tables, reduction scratch); 0 on bad sizes.
+ * pf_ens_init: phi[r], c[r], rho[r] are run r's caller-owned device fields
+ *   (layout as for pf_init); work is 256-byte aligned.  Errors as pf_init.
+ * pf_ens_step: advance every run n steps (async on the stream); the caller's
+ *   fields hold the new states when the stream reaches the end of the call.
+ * pf_ens_autotune: time trial_steps (even, >= 2) steps with each compiled tile
+ *   shape and keep the fastest; these are real steps of the simulation (3 x
+ *   (trial_steps + 2) in total).  chosen (may be NULL) receives the tile kind,
+ *   seconds_per_step (may be NULL, 3 doubles) the timings.  Synchronises.
+ * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x32), 2 (56x16).
+ * pf_ens_diag: pf_diag of run `run` (synchronises).
+ */
+typedef struct pf_ens pf_ens;
+size_t pf_ens_workspace_size(int nruns, const int* nx, const int* ny, const int* pitch);
+int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny, const int* pitch,
+                float* const* phi, float* const* c, float* const* rho,
+                void* work, size_t work_bytes, void* stream, pf_ens** out);
+int pf_ens_step(pf_ens* e, long n);
+int pf_ens_autotune(pf_ens* e, int trial_steps, int* chosen, double* seconds_per_step);
+int pf_ens_set_tile(pf_ens* e, int tile);
+int pf_ens_get_tile(const pf_ens* e);
+long pf_ens_get_step(const pf_ens* e);
+int pf_ens_diag(pf_ens* e, int run, double out[4]);
+int pf_ens_destroy(pf_ens* e);
+const char* pf_ens_last_error(void);
+
 /* Text for an error code, and the last error message of the calling thread. */
 const char* pf_strerror(int code);
 const char* pf_last_error(void);

@@ -25,10 +25,25 @@ struct StepConst {
 
 enum MobKind { MOB_UNIFORM = 0, MOB_BULK = 1, MOB_SURF = 2 };
 
-// Output tile of the fused step kernel (4-cell halo staged around it):
-// TILE_SMALL 32 x 16 cells (many CTAs for small grids), TILE_LARGE 64 x 32.
-enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1 };
+// Output tile of the fused step kernel (4-cell halo staged around it): 56 columns
+// by tile_height(kind) rows; TILE_SMALL gives small grids many CTAs.
+enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1, TILE_MEDIUM = 2 };
+constexpr int NUM_TILE_KINDS = 3;
 int choose_tile(int nx, int ny);
+int tile_width();
+int tile_height(int tile);
+
+// Ensemble of independent runs stepped by one launch: per-run constants and the
+// two buffers of its ping-pong pair; one table entry per output tile.
+struct EnsRun {
+    StepConst k;
+    float* f[2][3];  // [buffer][phi, c, rho]
+};
+struct EnsTile {
+    int run, x0, y0;
+};
+cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
+                            int parity, cudaStream_t s);
 
 // Launch one fused step: (phi0, c0, rho0) -> (phi1, c1, rho1) with programmatic
 // dependent launch enabled (the kernel waits for the previous grid before reading).

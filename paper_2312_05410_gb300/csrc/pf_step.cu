@@ -223,11 +223,11 @@ __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, i
     n = lo + ((s + 1) * H) / S - r0;
 }
 
+// One step of the output tile with corner (x0, y0) of one run (the whole CTA).
 template <int TY, int S, int PHI_MODE, int MOB>
-__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
-step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
-            const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
-            float* __restrict__ rho1)
+__device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, const float* __restrict__ phi0,
+                                          const float* __restrict__ c0, const float* __restrict__ rho0,
+                                          float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1)
 {
     using G = Geo<TY, S>;
     constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
@@ -236,7 +236,6 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
     float* const B = sm + 3 * PLANE;   // u*:  phi, c, rho (followed by the guard rows)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * TXO, y0 = blockIdx.y * TY;
     const int gx0 = x0 - HALO, gy0 = y0 - HALO;
     const int nx = k.nx, ny = k.ny, pitch = k.pitch;
 
@@ -343,29 +342,83 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
                                                  store_x, pair_full);
 }
 
+// One step of one run: a 2D grid of 56 x TY tiles.
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
+step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
+            const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
+            float* __restrict__ rho1)
+{
+    step_tile<TY, S, PHI_MODE, MOB>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
+}
+
+// One step of every run of an ensemble: CTA b takes tile b of the table; runs
+// step in lockstep, so one parity bit says which buffer of each run is current.
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
+ens_step_kernel(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ runs, int parity)
+{
+    const EnsTile t = tiles[blockIdx.x];
+    const EnsRun& r = runs[t.run];
+    const int a = parity, b = 1 - parity;
+    step_tile<TY, S, PHI_MODE, MOB>(r.k, t.x0, t.y0, r.f[a][0], r.f[a][1], r.f[a][2], r.f[b][0], r.f[b][1],
+                                    r.f[b][2]);
+}
+
+// Opt the kernel into its dynamic shared-memory size (once per kernel function).
+template <class Kern>
+cudaError_t configure_smem(Kern kern, bool& configured, size_t smem)
+{
+    if (!configured) {  // the attribute is per function; setting it twice is harmless
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    return cudaSuccess;
+}
+
+// Launch configuration with programmatic dependent launch enabled.
+cudaLaunchConfig_t pdl_config(dim3 grid, int threads, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 template <int TY, int S, int PHI_MODE, int MOB>
 cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const float* r0, float* f1,
                      float* c1, float* r1, cudaStream_t s)
 {
     using G = Geo<TY, S>;
     auto kern = step_kernel<TY, S, PHI_MODE, MOB>;
-    static bool configured = false;  // the attribute is per function; setting it twice is harmless
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
-    cfg.blockDim = dim3(G::THREADS);
-    cfg.dynamicSmemBytes = G::BYTES;
-    cfg.stream = s;
+    static bool configured = false;
+    const dim3 grid((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
+    cudaError_t e = configure_smem(kern, configured, G::BYTES);
+    if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::BYTES, s, attr);
     return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1);
+}
+
+template <int TY, int S, int PHI_MODE, int MOB>
+cudaError_t launch_ens_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, int parity, cudaStream_t s)
+{
+    using G = Geo<TY, S>;
+    auto kern = ens_step_kernel<TY, S, PHI_MODE, MOB>;
+    static bool configured = false;
+    const dim3 grid(ntiles);
+    cudaError_t e = configure_smem(kern, configured, G::BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::BYTES, s, attr);
+    return cudaLaunchKernelEx(&cfg, kern, tiles, runs, parity);
 }
 
 template <int TY, int S>
@@ -382,11 +435,29 @@ cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* 
     return launch_t<TY, S, 1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
 }
 
+template <int TY, int S>
+cudaError_t launch_ens_tile(int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
+                            int parity, cudaStream_t s)
+{
+    if (phi_mode == 0) {
+        if (mob == MOB_UNIFORM) return launch_ens_t<TY, S, 0, MOB_UNIFORM>(tiles, runs, ntiles, parity, s);
+        if (mob == MOB_BULK) return launch_ens_t<TY, S, 0, MOB_BULK>(tiles, runs, ntiles, parity, s);
+        return launch_ens_t<TY, S, 0, MOB_SURF>(tiles, runs, ntiles, parity, s);
+    }
+    if (mob == MOB_UNIFORM) return launch_ens_t<TY, S, 1, MOB_UNIFORM>(tiles, runs, ntiles, parity, s);
+    if (mob == MOB_BULK) return launch_ens_t<TY, S, 1, MOB_BULK>(tiles, runs, ntiles, parity, s);
+    return launch_ens_t<TY, S, 1, MOB_SURF>(tiles, runs, ntiles, parity, s);
+}
+
 }  // namespace
 
 #ifndef PF_SMALL_TY
 #define PF_SMALL_TY 8
 #define PF_SMALL_S 4
+#endif
+#ifndef PF_MEDIUM_TY
+#define PF_MEDIUM_TY 16
+#define PF_MEDIUM_S 4
 #endif
 #ifndef PF_LARGE_TY
 #define PF_LARGE_TY 32
@@ -399,9 +470,18 @@ int choose_tile(int nx, int ny)
     return (long long)nx * ny <= (1LL << 20) ? TILE_SMALL : TILE_LARGE;
 }
 
+int tile_width() { return TXO; }
+
+int tile_height(int tile)
+{
+    return tile == TILE_SMALL ? PF_SMALL_TY : (tile == TILE_MEDIUM ? PF_MEDIUM_TY : PF_LARGE_TY);
+}
+
 size_t step_smem_bytes(int tile)
 {
-    return tile == TILE_SMALL ? Geo<PF_SMALL_TY, PF_SMALL_S>::BYTES : Geo<PF_LARGE_TY, PF_LARGE_S>::BYTES;
+    if (tile == TILE_SMALL) return Geo<PF_SMALL_TY, PF_SMALL_S>::BYTES;
+    if (tile == TILE_MEDIUM) return Geo<PF_MEDIUM_TY, PF_MEDIUM_S>::BYTES;
+    return Geo<PF_LARGE_TY, PF_LARGE_S>::BYTES;
 }
 
 cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob, const float* f0, const float* c0,
@@ -409,7 +489,20 @@ cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob, con
 {
     if (tile == TILE_SMALL)
         return launch_tile<PF_SMALL_TY, PF_SMALL_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+    if (tile == TILE_MEDIUM)
+        return launch_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
     return launch_tile<PF_LARGE_TY, PF_LARGE_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+}
+
+cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
+                            int parity, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (tile == TILE_SMALL)
+        return launch_ens_tile<PF_SMALL_TY, PF_SMALL_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
+    if (tile == TILE_MEDIUM)
+        return launch_ens_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
+    return launch_ens_tile<PF_LARGE_TY, PF_LARGE_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
 }
 
 }  // namespace pf

@@ -69,6 +69,19 @@ def _load():
     L.pf_diagnostics.restype = C.c_int
     L.pf_diagnostics_static.argtypes = [P, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
     L.pf_diagnostics_static.restype = C.c_int
+    ip, pp = C.POINTER(C.c_int), C.POINTER(C.c_void_p)
+    L.pf_ens_workspace_size.argtypes, L.pf_ens_workspace_size.restype = [C.c_int, ip, ip, ip], sz
+    L.pf_ens_init.argtypes = [C.c_int, P, ip, ip, ip, pp, pp, pp, vp, sz, vp, C.POINTER(vp)]
+    L.pf_ens_init.restype = C.c_int
+    L.pf_ens_step.argtypes, L.pf_ens_step.restype = [vp, C.c_long], C.c_int
+    L.pf_ens_autotune.argtypes = [vp, C.c_int, ip, C.POINTER(C.c_double)]
+    L.pf_ens_autotune.restype = C.c_int
+    L.pf_ens_set_tile.argtypes, L.pf_ens_set_tile.restype = [vp, C.c_int], C.c_int
+    L.pf_ens_get_tile.argtypes, L.pf_ens_get_tile.restype = [vp], C.c_int
+    L.pf_ens_get_step.argtypes, L.pf_ens_get_step.restype = [vp], C.c_long
+    L.pf_ens_diag.argtypes, L.pf_ens_diag.restype = [vp, C.c_int, C.POINTER(C.c_double)], C.c_int
+    L.pf_ens_destroy.argtypes, L.pf_ens_destroy.restype = [vp], C.c_int
+    L.pf_ens_last_error.argtypes, L.pf_ens_last_error.restype = [], C.c_char_p
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
     L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
     return L
@@ -232,6 +245,96 @@ class Sim:
     def close(self):
         if getattr(self, "h", None) is not None:
             _check(pf_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Independent runs of uneven sizes stepped together by one launch per step.
+
+    members: list of (params, phi, c, rho) with numpy (ny, nx) arrays; every
+    run gets torch-owned (ny, pitch) float32 device fields.
+    """
+
+    def __init__(self, members, stream=None, device="cuda"):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.n = len(members)
+        self.fields, self.shapes, self.params = [], [], []
+        nxs, nys, pitches = [], [], []
+        for params, phi, c, rho in members:
+            ny, nx = np.asarray(phi).shape
+            pitch = padded_pitch(nx)
+            ts = []
+            for a in (phi, c, rho):
+                t = torch.zeros((ny, pitch), dtype=torch.float32, device=device)
+                t[:, :nx] = torch.from_numpy(np.asarray(a, dtype=np.float32)).to(device)
+                ts.append(t)
+            self.fields.append(ts)
+            self.shapes.append((ny, nx))
+            self.params.append(dict(params))
+            nxs.append(nx), nys.append(ny), pitches.append(pitch)
+        I = C.c_int * self.n
+        self._nx, self._ny, self._pitch = I(*nxs), I(*nys), I(*pitches)
+        nbytes = int(lib.pf_ens_workspace_size(self.n, self._nx, self._ny, self._pitch))
+        if nbytes == 0:
+            raise PFError(PF_ERR_ARG, "bad ensemble sizes")
+        self.work = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        wp = (self.work.data_ptr() + 255) // 256 * 256
+        self._params = (Params * self.n)(*[Params.from_dict(p) for p in self.params])
+        V = C.c_void_p * self.n
+        ptr = [V(*[self.fields[r][q].data_ptr() for r in range(self.n)]) for q in range(3)]
+        torch.cuda.synchronize()
+        h = C.c_void_p()
+        rc = lib.pf_ens_init(self.n, self._params, self._nx, self._ny, self._pitch, ptr[0], ptr[1], ptr[2], wp,
+                             nbytes, self.stream.cuda_stream, C.byref(h))
+        if rc != PF_OK:
+            raise PFError(rc, f"{strerror(rc)}: {lib.pf_ens_last_error().decode()}")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != PF_OK:
+            raise PFError(rc, f"{strerror(rc)}: {lib.pf_ens_last_error().decode()}")
+
+    def step(self, n: int):
+        self._check(lib.pf_ens_step(self.h, int(n)))
+
+    def autotune(self, trial_steps: int = 20):
+        chosen = C.c_int(-1)
+        secs = (C.c_double * 3)()
+        self._check(lib.pf_ens_autotune(self.h, int(trial_steps), C.byref(chosen), secs))
+        return chosen.value, list(secs)
+
+    def set_tile(self, tile: int):
+        self._check(lib.pf_ens_set_tile(self.h, int(tile)))
+
+    @property
+    def tile(self) -> int:
+        return int(lib.pf_ens_get_tile(self.h))
+
+    @property
+    def step_index(self) -> int:
+        return int(lib.pf_ens_get_step(self.h))
+
+    def diag(self, run: int) -> np.ndarray:
+        out = (C.c_double * 4)()
+        self._check(lib.pf_ens_diag(self.h, int(run), out))
+        return np.array(out[:])
+
+    def numpy(self, run: int):
+        self.stream.synchronize()
+        ny, nx = self.shapes[run]
+        return tuple(t[:, :nx].cpu().numpy() for t in self.fields[run])
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self._check(lib.pf_ens_destroy(self.h))
             self.h = None
 
     def __del__(self):

@@ -97,3 +97,33 @@ def test_diagnostics_error_paths(pf):
     assert pf.pf_diagnostics(p, 64, 64, 64, FAKE, FAKE, 0, FAKE, need, FAKE, 0) == pf.PF_ERR_ARG
     assert pf.pf_diagnostics(p, 0, 64, 64, FAKE, FAKE, FAKE, FAKE, need, FAKE, 0) == pf.PF_ERR_ARG
     assert pf.pf_diagnostics(p, 64, 64, 64, FAKE, FAKE, FAKE, FAKE + 8, need, FAKE, 0) == pf.PF_ERR_LAYOUT
+
+
+def _ens_init(pf, plist, shapes, work_bytes=None, ptr=FAKE):
+    import ctypes as C
+
+    n = len(plist)
+    I_ = C.c_int * n
+    nx = I_(*[s[0] for s in shapes])
+    ny = I_(*[s[1] for s in shapes])
+    pitch = I_(*[((s[0] + 31) // 32) * 32 for s in shapes])
+    params = (pf.Params * n)(*[pf.Params.from_dict(p) for p in plist])
+    V = C.c_void_p * n
+    f = V(*([ptr] * n))
+    if work_bytes is None:
+        work_bytes = pf.lib.pf_ens_workspace_size(n, nx, ny, pitch)
+    h = C.c_void_p()
+    return pf.lib.pf_ens_init(n, params, nx, ny, pitch, f, f, f, FAKE, work_bytes, None, C.byref(h))
+
+
+def test_ensemble_init_error_paths(pf):
+    good = O.with_dt(I.default_params())
+    shapes = [(64, 64), (37, 23)]
+    assert pf.lib.pf_ens_workspace_size(0, None, None, None) == 0
+    assert _ens_init(pf, [good, dict(good, phi_mode=1)], shapes) == pf.PF_ERR_ARG
+    assert _ens_init(pf, [good, dict(good, MA_bulk=2.0)], shapes) == pf.PF_ERR_ARG
+    lim = pf.pf_dt_limit(good)[0]
+    assert _ens_init(pf, [good, dict(good, dt=1.1 * lim)], shapes) == pf.PF_ERR_UNSTABLE
+    assert _ens_init(pf, [good, good], shapes, work_bytes=4096) == pf.PF_ERR_LAYOUT
+    assert _ens_init(pf, [good, good], [(64, 64), (0, 5)]) == pf.PF_ERR_ARG
+    assert _ens_init(pf, [good, good], shapes, ptr=FAKE + 4) == pf.PF_ERR_LAYOUT
