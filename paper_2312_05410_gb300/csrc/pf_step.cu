@@ -41,7 +41,6 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
-__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
 __device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
 
@@ -85,7 +84,7 @@ __device__ __forceinline__ void chem(const StepConst& k, f2 f, f2 c, f2 sf, f2 s
 {
     const f2 ff = mul2(f, f);
     const f2 p = fma2(fma2(F2(-0.25f), ff, F2(0.75f)), f, F2(0.5f));  // p = 1/4 (2-phi)(1+phi)^2
-    const f2 q = fma2(neg2(c), c, c);                                  // c (1 - c)
+    const f2 q = mul2(c, fma2(c, F2(-1.f), F2(1.f)));                  // c (1 - c)
     const f2 g = mul2(q, q);                                           // g(c) = c^2 (1-c)^2
     const f2 Wdg = mul2(q, fma2(F2(-4.f * k.Wc), c, F2(2.f * k.Wc)));  // W_c g'(c)
     // mu_c = p W_c g' - kappa_c L(c)
@@ -125,6 +124,7 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
     const float* Ri = I + 2 * PLANE;
     // Windows. phi and c rows are numbered t = row - (r0 - 2); rho rows t' = row - (r0 - 3).
     f2 fw[4], cw[3], rw[3], mcw[3], mfw[3], Mw[3];
+    float fWw[2], fEw[2];  // west/east neighbours of phi at the last two mu rows
     fw[0] = ld2(Fi + (r0 - 2) * PX);
     fw[1] = ld2(Fi + (r0 - 1) * PX);
     cw[0] = ld2(Ci + (r0 - 2) * PX);
@@ -140,7 +140,9 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         // mu_c, mu_phi, M at row r0 - 1 + j (phi, c rows t = j .. j + 2)
         {
             const f2 f = fw[(j + 1) % 4], c = cw[(j + 1) % 3];
-            const f2 sf = add2(hsum(west(f), f, east(f)), add2(fw[j % 4], fw[(j + 2) % 4]));
+            fWw[j % 2] = west(f);
+            fEw[j % 2] = east(f);
+            const f2 sf = add2(hsum(fWw[j % 2], f, fEw[j % 2]), add2(fw[j % 4], fw[(j + 2) % 4]));
             const f2 sc = add2(hsum(west(c), c, east(c)), add2(cw[j % 3], cw[(j + 2) % 3]));
             chem<MOB>(k, f, c, sf, sc, mcw[j % 3], mfw[j % 3], Mw[j % 3]);
         }
@@ -151,10 +153,10 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         const int iS = (j - 2) % 3, iC = (j - 1) % 3, iN = j % 3;
         // conserved composition flux: sum_faces (M + M_nb)(mu_nb - mu) / (2 dx^2)
         const f2 m = mcw[iC], M = Mw[iC];
-        const float mW = west(m), mE = east(m), MW = west(M), ME = east(M);
-        const float Fa = (MW + M.x) * (m.x - mW);   // face (x-1 | x)
+        const float mE = east(m), ME = east(M);
         const float Fb = (M.x + M.y) * (m.y - m.x);  // face (x | x+1)
         const float Fc = (M.y + ME) * (mE - m.y);    // face (x+1 | x+2)
+        const float Fa = __shfl_up_sync(FULL, Fc, 1);  // face (x-1 | x) = the west lane's east face
         f2 rc = make_float2(Fb - Fa, Fc - Fb);
         rc = fma2(add2(M, Mw[iN]), sub2(mcw[iN], m), rc);
         rc = fma2(add2(M, Mw[iS]), sub2(mcw[iS], m), rc);
@@ -163,7 +165,9 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         const f2 f = fw[j % 4], fN = fw[(j + 1) % 4], fS = fw[(j + 3) % 4];
         const f2 r = rw[(j + 1) % 3], rN = rw[(j + 2) % 3], rS = rw[j % 3];
         const float rW = west(r), rE = east(r);
-        const f2 Src = mul2(r, fma2(F2(k.ax), hdiff(west(f), f, east(f)), mul2(F2(k.ay), sub2(fN, fS))));
+        // phi at this row is the centre of the mu row computed one iteration earlier
+        const f2 Src = mul2(r, fma2(F2(k.ax), hdiff(fWw[(j + 1) % 2], f, fEw[(j + 1) % 2]),
+                                    mul2(F2(k.ay), sub2(fN, fS))));
 
         f2 Rf;
         if (PHI_MODE == 0) {
@@ -175,8 +179,8 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         }
         // vapor: D L(rho) - div(rho v) - S
         const f2 lap = fma2(F2(-4.f), r, add2(hsum(rW, r, rE), add2(rN, rS)));
-        const f2 adv = fma2(F2(k.ax), hdiff(rW, r, rE), mul2(F2(k.ay), sub2(rN, rS)));
-        const f2 Rr = sub2(fma2(F2(k.cD), lap, neg2(adv)), Src);
+        const f2 nadv = fma2(F2(-k.ax), hdiff(rW, r, rE), mul2(F2(-k.ay), sub2(rN, rS)));  // -div(rho v)
+        const f2 Rr = sub2(fma2(F2(k.cD), lap, nadv), Src);
 
         const int i = j - 2;  // output row r0 + i
         f2 bf, bc, br;
