@@ -51,9 +51,13 @@ WORKLOADS = {
                             "c_inc~U[0.3,0.7], 10000 steps"),
 }
 
-# DRAM bytes per step-kernel launch from an ncu capture, keyed by workload, with the
-# hash of the kernel source it was taken on (reported as null once the source changes).
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per step-kernel launch from one ncu capture (cold caches),
+# keyed by workload, with the hash of the kernel source it was taken on; reported as
+# null once the source changes.  Summaries: profiles/step_kernel_*_full.md.
+NCU_TRAFFIC = {
+    "paper512": {"bytes": 3169792, "src": "59d817940e9dc76c"},
+    "large4096": {"bytes": 360521216, "src": "59d817940e9dc76c"},
+}
 
 
 def kernel_source_hash() -> str:
@@ -385,9 +389,13 @@ def main():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="paper512")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--timesteps", type=int, default=0,
+                    help="override the workload's time steps per run (short runs for profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.timesteps > 0:
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], steps=args.timesteps)
     if args.impl == "reference":
         run_reference(args)
     else:
