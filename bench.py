@@ -46,6 +46,14 @@ WORKLOADS = {
                       steps=2000, desc="plain DNS 4096x4096, 2000 steps, diagnostics every 1000"),
     "large8192": dict(spec=I.FilmSpec(8192, 8192, 16.0, seed=1), params=dict(v_mag=0.3, diag_every=1000),
                       steps=1000, desc="plain DNS 8192x8192, 1000 steps, diagnostics every 1000"),
+    "paper512_surface": dict(spec=I.PAPER_512["spec"],
+                             params=dict(I.PAPER_512["params"], MA_bulk=2.0, MB_bulk=0.5, MA_surf=10.0, MB_surf=4.0,
+                                         sigma_surf=0.5),
+                             steps=50000, desc="plain DNS 512x512, 50000 steps, bulk + surface mobility (exp path)"),
+    "paper512_angle50": dict(spec=I.PAPER_512["spec"], params=dict(I.PAPER_512["params"], v_angle_deg=50.0),
+                             steps=50000, desc="plain DNS 512x512, 50000 steps, oblique incidence at 50 degrees"),
+    "paper512_ac": dict(spec=I.PAPER_512["spec"], params=dict(I.PAPER_512["params"], phi_mode=1),
+                        steps=50000, desc="plain DNS 512x512, 50000 steps, Allen-Cahn order parameter + source"),
     "ensemble64": dict(kind="ensemble", n_runs=64, seed=3, steps=10000,
                        desc="batched DNS ensemble: 64 runs, sides in {128,192,256,384,512}, V~U[0.1,0.9], "
                             "c_inc~U[0.3,0.7], 10000 steps"),

@@ -213,6 +213,31 @@ int pf_ens_diag(pf_ens* e, int run, double out[4]);
 int pf_ens_destroy(pf_ens* e);
 const char* pf_ens_last_error(void);
 
+/*
+ * Discrete adjoint of the explicit midpoint step (the paper's inverse-design
+ * motivation, Discussion: finding deposition parameters for a target
+ * microstructure).  Runs nsteps forward steps from (phi0, c0, rho0), storing a
+ * checkpoint every K steps, then the hand-written adjoint backwards through
+ * them (each segment recomputed from its checkpoint).  It returns the exact
+ * gradient of the linear functional L = sum(w_phi*phi_N + w_c*c_N + w_rho*rho_N)
+ * of the final state (w = dLoss/du_N for any loss of u_N):
+ *   g_phi0, g_c0, g_rho0  dL/d(initial fields), device, layout of the fields;
+ *   g_params (host, 3)    {dL/dv_mag, dL/ds with M_c -> s M_c at s = 1, dL/dkappa_c};
+ * dt is held fixed.  w_rho may be NULL (zero).  final_* (device, may all be
+ * NULL) receive u_N.  work: pf_adjoint_workspace_size(nx, ny, pitch, nsteps, K)
+ * bytes, 256-byte aligned (two work states, nsteps/K + 1 checkpoints, K segment
+ * states, cotangents, scratch).  Synchronises the stream.  Per-cell terms are
+ * FP32; the parameter sums are FP64 in a fixed order.
+ */
+size_t pf_adjoint_workspace_size(int nx, int ny, int pitch, long nsteps, int K);
+int pf_adjoint(const pf_params* p, int nx, int ny, int pitch,
+               const float* phi0, const float* c0, const float* rho0, long nsteps, int K,
+               const float* w_phi, const float* w_c, const float* w_rho,
+               float* g_phi0, float* g_c0, float* g_rho0, double* g_params,
+               float* final_phi, float* final_c, float* final_rho,
+               void* work, size_t work_bytes, void* stream);
+const char* pf_adjoint_last_error(void);
+
 /* Text for an error code, and the last error message of the calling thread. */
 const char* pf_strerror(int code);
 const char* pf_last_error(void);

@@ -1,0 +1,509 @@
+// Hand-written discrete adjoint of the explicit midpoint step (declarations in
+// include/pf.h: pf_adjoint).  It gives the exact gradient, through every time
+// step of the scheme the forward kernel runs (Materials and Methods equations,
+// "Dataset": central differences, explicit midpoint), of a linear functional
+// of the final state, L = sum(w . u_N), with respect to the initial fields
+// and to three parameters: the incident speed V (deposition rate), a factor on
+// the composition mobility (M_c -> s M_c, at s = 1) and kappa_c.  dt is fixed.
+//
+// For one step u' = u + dt R(u*), u* = u + dt/2 R(u), with w' the cotangent of u':
+//   w* = dt J_R(u*)^T w'
+//   w  = w' + w* + dt/2 J_R(u)^T w*
+//   theta_bar += dt (dR/dtheta)(u*)^T w' + dt/2 (dR/dtheta)(u)^T w*.
+// J_R(v)^T x is evaluated by two gather kernels.  Pass A, per cell: the
+// cotangents of the chemical potentials, of the mobility and of the source,
+//   mu_c_bar = div_M(x_c) (the flux operator is self-adjoint),
+//   M_bar = -1/(2dx^2) sum_faces (mu_nb - mu)(x_nb - x),
+//   mu_phi_bar = M_phi L(x_phi) (Allen-Cahn form: -L_phi x_phi), s_bar = x_phi - x_rho,
+// and the parameter partials.  Pass B, per cell: the cotangents of phi, c, rho
+// from the pointwise derivatives and the transposed stencils.
+// Boundary rules of the transposes (the forward copies boundary values into
+// ghost rows): operands of symmetric stencils (Laplacians, flux divergence)
+// take mirrored ghosts; weights of the central y-difference take negated
+// ghosts (mirror fields) or zero (rho's fixed reservoir value above the top);
+// rho's Laplacian takes a zero ghost above the top.
+//
+// Checkpointing: the forward stores the state every K steps; the backward
+// recomputes each segment's K states from its checkpoint with the fused step
+// kernel, then walks them in reverse.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+namespace pf {
+namespace {
+
+constexpr int ADJ_THREADS = 256;
+constexpr int ADJ_MAX_BLOCKS = 1216;
+
+struct AdjConst {
+    StepConst k;
+    float idx2;            // 1 / dx^2
+    float cx, cy;          // dR/dV scaling: (cos a, -sin a) / (2 dx), zero without deposition
+    float MAb, MBb, MAs, MBs, isig2;
+    int phi_mode;
+};
+
+// Field access with the forward's ghost rules: x periodic; phi and c reflected
+// (mirror); rho mirrored at the bottom, rho_top above the top.
+__device__ __forceinline__ int wrapx(int i, int nx)
+{
+    i %= nx;
+    return i < 0 ? i + nx : i;
+}
+__device__ __forceinline__ int refl(int j, int ny)
+{
+    for (int it = 0; it < 4 && (j < 0 || j >= ny); ++it) j = j < 0 ? -1 - j : 2 * ny - 1 - j;
+    return j < 0 ? 0 : (j >= ny ? ny - 1 : j);
+}
+__device__ __forceinline__ float mirror_at(const float* f, int j, int i, int nx, int ny, int pitch)
+{
+    return f[(size_t)refl(j, ny) * pitch + wrapx(i, nx)];
+}
+__device__ __forceinline__ float rho_at(const float* r, int j, int i, int nx, int ny, int pitch, float rho_top)
+{
+    if (j >= ny) return rho_top;
+    return r[(size_t)refl(j, ny) * pitch + wrapx(i, nx)];
+}
+
+struct Chem {
+    float muc, M;
+};
+
+// mu_c and M_c at (j, i) (ghost rows by reflection, as in the forward)
+__device__ __forceinline__ Chem chem_at(const AdjConst& a, const float* phi, const float* c, int j, int i, int nx,
+                                        int ny, int pitch)
+{
+    const float f = mirror_at(phi, j, i, nx, ny, pitch), cc = mirror_at(c, j, i, nx, ny, pitch);
+    const float sc = mirror_at(c, j, i + 1, nx, ny, pitch) + mirror_at(c, j, i - 1, nx, ny, pitch) +
+                     mirror_at(c, j + 1, i, nx, ny, pitch) + mirror_at(c, j - 1, i, nx, ny, pitch);
+    const float P = 0.25f * (2.f - f) * (1.f + f) * (1.f + f);
+    const float dg = 2.f * cc * (1.f - cc) * (1.f - 2.f * cc);
+    Chem r;
+    r.muc = P * a.k.Wc * dg - a.k.kc * (sc - 4.f * cc);
+    const float h = cc * cc * (3.f - 2.f * cc);
+    r.M = P * (h * a.MAb + (1.f - h) * a.MBb);
+    if (a.MAs != 0.f || a.MBs != 0.f) r.M += expf(-f * f * a.isig2) * (h * a.MAs + (1.f - h) * a.MBs);
+    return r;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Pass A. x: cotangent (phi, c, rho); v: state. Writes mu_c_bar, M_bar, mu_phi_bar, s_bar
+// and per-block partials {V, m_scale, kappa_c} (FP64, fixed order).
+__global__ void __launch_bounds__(ADJ_THREADS)
+vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __restrict__ vc,
+             const float* __restrict__ vrho, const float* __restrict__ xphi, const float* __restrict__ xc,
+             const float* __restrict__ xrho, float* __restrict__ muc_bar, float* __restrict__ M_bar,
+             float* __restrict__ muf_bar, float* __restrict__ s_bar, double* __restrict__ partials)
+{
+    const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
+    const long long n = (long long)nx * ny;
+    double accV = 0.0, accM = 0.0, accK = 0.0;
+    for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * ADJ_THREADS) {
+        const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
+        const size_t o = (size_t)j * pitch + i;
+        const int nj[4] = {j, j, j + 1, j - 1}, ni[4] = {i + 1, i - 1, i, i};
+        const Chem C0 = chem_at(a, vphi, vc, j, i, nx, ny, pitch);
+        const float wc = xc[o];
+        float mub = 0.f, Mb = 0.f, Rc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const Chem Cn = chem_at(a, vphi, vc, nj[q], ni[q], nx, ny, pitch);
+            const float dw = mirror_at(xc, nj[q], ni[q], nx, ny, pitch) - wc;
+            mub += (C0.M + Cn.M) * dw;
+            Mb -= (Cn.muc - C0.muc) * dw;
+            Rc += (C0.M + Cn.M) * (Cn.muc - C0.muc);
+        }
+        mub *= a.k.cR;
+        Mb *= a.k.cR;
+        Rc *= a.k.cR;
+        const float wf = xphi[o], wr = xrho[o];
+        float mfb;
+        if (a.phi_mode == 0) {
+            const float s = mirror_at(xphi, j, i + 1, nx, ny, pitch) + mirror_at(xphi, j, i - 1, nx, ny, pitch) +
+                            mirror_at(xphi, j + 1, i, nx, ny, pitch) + mirror_at(xphi, j - 1, i, nx, ny, pitch);
+            mfb = a.k.cF * (s - 4.f * wf);
+        } else {
+            mfb = a.k.cF * wf;
+        }
+        const float sb = wf - wr;
+        muc_bar[o] = mub;
+        M_bar[o] = Mb;
+        muf_bar[o] = mfb;
+        s_bar[o] = sb;
+        // parameter partials
+        const float c0 = vc[o], r0 = vrho[o];
+        const float Lc = mirror_at(vc, j, i + 1, nx, ny, pitch) + mirror_at(vc, j, i - 1, nx, ny, pitch) +
+                         mirror_at(vc, j + 1, i, nx, ny, pitch) + mirror_at(vc, j - 1, i, nx, ny, pitch) - 4.f * c0;
+        accK -= (double)mub * (double)(Lc * a.idx2);  // d mu_c / d kappa_c = -L(c)
+        accM += (double)wc * (double)Rc;
+        const float dfx = mirror_at(vphi, j, i + 1, nx, ny, pitch) - mirror_at(vphi, j, i - 1, nx, ny, pitch);
+        const float dfy = mirror_at(vphi, j + 1, i, nx, ny, pitch) - mirror_at(vphi, j - 1, i, nx, ny, pitch);
+        const float drx = rho_at(vrho, j, i + 1, nx, ny, pitch, a.k.rho_top) -
+                          rho_at(vrho, j, i - 1, nx, ny, pitch, a.k.rho_top);
+        const float dry = rho_at(vrho, j + 1, i, nx, ny, pitch, a.k.rho_top) -
+                          rho_at(vrho, j - 1, i, nx, ny, pitch, a.k.rho_top);
+        accV += (double)(sb * r0 * (a.cx * dfx + a.cy * dfy)) - (double)(wr * (a.cx * drx + a.cy * dry));
+    }
+    __shared__ double red[3][ADJ_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    accV = warp_sum(accV);
+    accM = warp_sum(accM);
+    accK = warp_sum(accK);
+    if (lane == 0) {
+        red[0][w] = accV;
+        red[1][w] = accM;
+        red[2][w] = accK;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) {
+            double s = 0.0;
+            for (int t = 0; t < ADJ_THREADS / 32; ++t) s += red[q][t];
+            partials[(size_t)q * gridDim.x + blockIdx.x] = s;
+        }
+    }
+}
+
+// acc[q] += scale * sum_b partials[q][b] (one block, fixed order).
+__global__ void __launch_bounds__(ADJ_THREADS)
+accumulate_kernel(const double* __restrict__ partials, int nblocks, double scale, double* __restrict__ acc)
+{
+    __shared__ double red[3][ADJ_THREADS / 32];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += ADJ_THREADS)
+        for (int q = 0; q < 3; ++q) s[q] += partials[(size_t)q * nblocks + b];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < 3; ++q) {
+        s[q] = warp_sum(s[q]);
+        if (lane == 0) red[q][w] = s[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) {
+            double t = 0.0;
+            for (int i = 0; i < ADJ_THREADS / 32; ++i) t += red[q][i];
+            acc[q] += scale * t;
+        }
+}
+
+// Pass B. out = base1 + base2 + scale * J_R(v)^T x, from pass A's fields; base1/base2 may be NULL.
+__global__ void __launch_bounds__(ADJ_THREADS)
+vjp_b_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __restrict__ vc,
+             const float* __restrict__ vrho, const float* __restrict__ xrho, const float* __restrict__ muc_bar,
+             const float* __restrict__ M_bar, const float* __restrict__ muf_bar, const float* __restrict__ s_bar,
+             float scale, const float* __restrict__ b1phi, const float* __restrict__ b1c,
+             const float* __restrict__ b1rho, const float* __restrict__ b2phi, const float* __restrict__ b2c,
+             const float* __restrict__ b2rho, float* __restrict__ ophi, float* __restrict__ oc,
+             float* __restrict__ orho)
+{
+    const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
+    const long long n = (long long)nx * ny;
+    for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * ADJ_THREADS) {
+        const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
+        const size_t o = (size_t)j * pitch + i;
+        const float f = vphi[o], cc = vc[o], r = vrho[o];
+        const float P = 0.25f * (2.f - f) * (1.f + f) * (1.f + f);
+        const float dP = 0.75f * (1.f - f * f);
+        const float d2P = -1.5f * f;
+        const float g = cc * cc * (1.f - cc) * (1.f - cc);
+        const float dg = 2.f * cc * (1.f - cc) * (1.f - 2.f * cc);
+        const float d2g = 2.f - 12.f * cc + 12.f * cc * cc;
+        const float h = cc * cc * (3.f - 2.f * cc);
+        const float dh = 6.f * cc * (1.f - cc);
+        float dMdf = dP * (h * a.MAb + (1.f - h) * a.MBb);
+        float dMdc = P * (a.MAb - a.MBb) * dh;
+        if (a.MAs != 0.f || a.MBs != 0.f) {
+            const float e = expf(-f * f * a.isig2);
+            dMdf += -2.f * f * a.isig2 * e * (h * a.MAs + (1.f - h) * a.MBs);
+            dMdc += e * (a.MAs - a.MBs) * dh;
+        }
+        const float mub = muc_bar[o], mfb = muf_bar[o], Mb = M_bar[o];
+        // neighbour sums of the mirrored cotangents (symmetric Laplacians)
+        const float Lmub = mirror_at(muc_bar, j, i + 1, nx, ny, pitch) + mirror_at(muc_bar, j, i - 1, nx, ny, pitch) +
+                           mirror_at(muc_bar, j + 1, i, nx, ny, pitch) + mirror_at(muc_bar, j - 1, i, nx, ny, pitch) -
+                           4.f * mub;
+        const float Lmfb = mirror_at(muf_bar, j, i + 1, nx, ny, pitch) + mirror_at(muf_bar, j, i - 1, nx, ny, pitch) +
+                           mirror_at(muf_bar, j + 1, i, nx, ny, pitch) + mirror_at(muf_bar, j - 1, i, nx, ny, pitch) -
+                           4.f * mfb;
+        float cb = a.k.Wc * P * d2g * mub - a.k.kc * Lmub + dP * a.k.Wc * dg * mfb + dMdc * Mb;
+        const float fpp = a.k.Wf * (3.f * f * f - 1.f) + d2P * a.k.Wc * g;
+        float fb = a.k.Wc * dP * dg * mub + fpp * mfb - a.k.kf * Lmfb + dMdf * Mb;
+        // transposed central differences of phi in the source: weights a = (ax, ay) rho s_bar
+        auto aw = [&](int jj, int ii) {  // weight at a neighbour; y-ghosts negated (mirror field)
+            const int jr = refl(jj, ny), ir = wrapx(ii, nx);
+            const size_t q = (size_t)jr * pitch + ir;
+            const float sgn = (jj < 0 || jj >= ny) ? -1.f : 1.f;
+            return sgn * vrho[q] * s_bar[q];
+        };
+        fb += a.k.ax * (aw(j, i - 1) - aw(j, i + 1)) + a.k.ay * (aw(j - 1, i) - aw(j + 1, i));
+        // rho: source factor, diffusion with the transposed boundary rules, transposed advection
+        const float sb = s_bar[o];
+        const float dfx = mirror_at(vphi, j, i + 1, nx, ny, pitch) - mirror_at(vphi, j, i - 1, nx, ny, pitch);
+        const float dfy = mirror_at(vphi, j + 1, i, nx, ny, pitch) - mirror_at(vphi, j - 1, i, nx, ny, pitch);
+        float rb = sb * (a.k.ax * dfx + a.k.ay * dfy);
+        auto wr_lap = [&](int jj, int ii) {  // mirrored below, zero above the top
+            if (jj >= ny) return 0.f;
+            return xrho[(size_t)refl(jj, ny) * pitch + wrapx(ii, nx)];
+        };
+        auto wr_dy = [&](int jj, int ii) {  // negated below, zero above the top
+            if (jj >= ny) return 0.f;
+            const float v = xrho[(size_t)refl(jj, ny) * pitch + wrapx(ii, nx)];
+            return jj < 0 ? -v : v;
+        };
+        const float wr0 = xrho[o];
+        rb += a.k.cD * (wr_lap(j, i + 1) + wr_lap(j, i - 1) + wr_lap(j + 1, i) + wr_lap(j - 1, i) - 4.f * wr0);
+        rb -= a.k.ax * (wr_lap(j, i - 1) - wr_lap(j, i + 1)) + a.k.ay * (wr_dy(j - 1, i) - wr_dy(j + 1, i));
+        float of = scale * fb, oc_ = scale * cb, orr = scale * rb;
+        if (b1phi) {
+            of += b1phi[o];
+            oc_ += b1c[o];
+            orr += b1rho[o];
+        }
+        if (b2phi) {
+            of += b2phi[o];
+            oc_ += b2c[o];
+            orr += b2rho[o];
+        }
+        ophi[o] = of;
+        oc[o] = oc_;
+        orho[o] = orr;
+    }
+}
+
+int adj_blocks(int nx, int ny)
+{
+    long long b = ((long long)nx * ny + 4 * ADJ_THREADS - 1) / (4 * ADJ_THREADS);
+    return (int)(b < 1 ? 1 : (b > ADJ_MAX_BLOCKS ? ADJ_MAX_BLOCKS : b));
+}
+
+}  // namespace
+}  // namespace pf
+
+namespace {
+
+thread_local std::string g_adj_error;
+
+int afail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_adj_error = buf;
+    return code;
+}
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct AdjLayout {
+    size_t plane;   // bytes of one field plane
+    size_t pp;      // ping-pong (2 x 3 planes)
+    size_t ckpt;    // (nseg + 1) x 3 planes
+    size_t seg;     // K x 3 planes
+    size_t lam;     // 3 cotangents x 3 planes
+    size_t ustar;   // 3 planes
+    size_t scratch; // 4 planes
+    size_t partials, acc, total;
+};
+
+bool adj_layout(int nx, int ny, int pitch, long nsteps, int K, AdjLayout& L)
+{
+    if (nx < 1 || ny < 1 || pitch < nx || nsteps < 0 || K < 1) return false;
+    const long nseg = (nsteps + K - 1) / K;
+    L.plane = a256(size_t(ny) * size_t(pitch) * sizeof(float));
+    size_t off = 0;
+    L.pp = off;
+    off += 6 * L.plane;
+    L.ckpt = off;
+    off += size_t(nseg + 1) * 3 * L.plane;
+    L.seg = off;
+    off += size_t(K) * 3 * L.plane;
+    L.lam = off;
+    off += 9 * L.plane;
+    L.ustar = off;
+    off += 3 * L.plane;
+    L.scratch = off;
+    off += 4 * L.plane;
+    L.partials = off;
+    off = a256(off + 3 * size_t(pf::adj_blocks(nx, ny)) * sizeof(double));
+    L.acc = off;
+    off = a256(off + 3 * sizeof(double));
+    L.total = off;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pf_adjoint_workspace_size(int nx, int ny, int pitch, long nsteps, int K)
+{
+    AdjLayout L;
+    return adj_layout(nx, ny, pitch, nsteps, K, L) ? L.total : 0;
+}
+
+int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0, const float* c0, const float* rho0,
+               long nsteps, int K, const float* w_phi, const float* w_c, const float* w_rho, float* g_phi0,
+               float* g_c0, float* g_rho0, double* g_params, float* final_phi, float* final_c, float* final_rho,
+               void* work, size_t work_bytes, void* stream)
+{
+    using namespace pf;
+    if (!p || !phi0 || !c0 || !rho0 || !w_phi || !w_c || !g_phi0 || !g_c0 || !g_rho0 || !g_params || !work)
+        return afail(PF_ERR_ARG, "null pointer");
+    if (nx < 1 || ny < 1 || nx > (1 << 20) || ny > (1 << 20)) return afail(PF_ERR_ARG, "bad grid size");
+    if (pitch < nx || pitch % 4) return afail(PF_ERR_LAYOUT, "bad pitch");
+    if (nsteps < 0 || K < 1) return afail(PF_ERR_ARG, "need nsteps >= 0 and K >= 1");
+    if (reinterpret_cast<uintptr_t>(work) % 256) return afail(PF_ERR_LAYOUT, "workspace must be 256-byte aligned");
+    if (!(p->dx > 0.0) || (p->phi_mode != 0 && p->phi_mode != 1)) return afail(PF_ERR_ARG, "bad dx or phi_mode");
+    if ((p->MA_surf != 0.0 || p->MB_surf != 0.0) && !(p->sigma_surf > 0.0))
+        return afail(PF_ERR_ARG, "sigma_surf must be positive");
+    double lim[4];
+    pf_dt_limit(p, lim);
+    if (!(p->dt > 0.0) || p->dt > lim[0] * (1.0 + 1e-12)) return afail(PF_ERR_UNSTABLE, "dt outside the limit");
+    AdjLayout L;
+    if (!adj_layout(nx, ny, pitch, nsteps, K, L)) return afail(PF_ERR_ARG, "bad sizes");
+    if (work_bytes < L.total) return afail(PF_ERR_LAYOUT, "workspace of %zu bytes, %zu needed", work_bytes, L.total);
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(work);
+    auto planes = [&](size_t off) {
+        float* b = reinterpret_cast<float*>(w + off);
+        const size_t pl = L.plane / sizeof(float);
+        return std::vector<float*>{b, b + pl, b + 2 * pl};
+    };
+    const size_t pl = L.plane / sizeof(float);
+    const StepConst k = step_const_of(*p, nx, ny, pitch);
+    StepConst khalf = k;
+    khalf.dt = float(0.5 * p->dt);
+    const int mob = mob_kind_of(*p), tile = choose_tile(nx, ny);
+    AdjConst ac{};
+    ac.k = k;
+    ac.idx2 = float(1.0 / (p->dx * p->dx));
+    double vxu = 0.0, vyu = 0.0;
+    if (p->deposition) {
+        const double ang = p->v_angle_deg * (M_PI / 180.0);
+        vxu = std::cos(ang);
+        vyu = -std::sin(ang);
+    }
+    ac.cx = float(vxu / (2.0 * p->dx));
+    ac.cy = float(vyu / (2.0 * p->dx));
+    ac.MAb = float(p->MA_bulk);
+    ac.MBb = float(p->MB_bulk);
+    ac.MAs = float(p->MA_surf);
+    ac.MBs = float(p->MB_surf);
+    ac.isig2 = p->sigma_surf > 0.0 ? float(1.0 / (p->sigma_surf * p->sigma_surf)) : 0.f;
+    ac.phi_mode = p->phi_mode;
+    const int nb = adj_blocks(nx, ny);
+    double* partials = reinterpret_cast<double*>(w + L.partials);
+    double* acc = reinterpret_cast<double*>(w + L.acc);
+    const long nseg = (nsteps + K - 1) / K;
+
+    cudaError_t e = cudaSuccess;
+    // field copies move the nx model columns only (padding columns are left as they are)
+    auto copy3 = [&](float* const* dst, const float* const* src) {
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+            e = cudaMemcpy2DAsync(dst[q], size_t(pitch) * sizeof(float), src[q], size_t(pitch) * sizeof(float),
+                                  size_t(nx) * sizeof(float), size_t(ny), cudaMemcpyDeviceToDevice, s);
+    };
+    auto ckpt = [&](long i) { return planes(L.ckpt + size_t(i) * 3 * L.plane); };
+    auto segst = [&](long i) { return planes(L.seg + size_t(i) * 3 * L.plane); };
+    auto step = [&](const std::vector<float*>& a, const std::vector<float*>& b) {
+        if (e == cudaSuccess) e = launch_step(k, tile, p->phi_mode, mob, a[0], a[1], a[2], b[0], b[1], b[2], s);
+    };
+    // ---- forward: checkpoints at multiples of K, final state
+    {
+        const float* init[3] = {phi0, c0, rho0};
+        std::vector<float*> c0v = ckpt(0);
+        copy3(c0v.data(), init);
+        std::vector<float*> A = planes(L.pp), B = {A[0] + 3 * pl, A[1] + 3 * pl, A[2] + 3 * pl};
+        std::vector<float*> cur = c0v;
+        for (long t = 0; t < nsteps && e == cudaSuccess; ++t) {
+            std::vector<float*> dst = ((t + 1) % K == 0) ? ckpt((t + 1) / K) : ((cur == A) ? B : A);
+            step(cur, dst);
+            cur = dst;
+        }
+        if (final_phi && final_c && final_rho && e == cudaSuccess) {
+            float* fin[3] = {final_phi, final_c, final_rho};
+            const float* src[3] = {cur[0], cur[1], cur[2]};
+            copy3(fin, src);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * sizeof(double), s);
+    // ---- backward
+    std::vector<float*> lamA = planes(L.lam), lamB = planes(L.lam + 3 * L.plane), lamS = planes(L.lam + 6 * L.plane);
+    std::vector<float*> us = planes(L.ustar);
+    float* sc = reinterpret_cast<float*>(w + L.scratch);
+    float *muc_b = sc, *M_b = sc + pl, *muf_b = sc + 2 * pl, *s_b = sc + 3 * pl;
+    // cotangent buffers start at zero (also a zero rho cotangent when none is given)
+    if (e == cudaSuccess) e = cudaMemsetAsync(lamA[0], 0, 9 * L.plane, s);
+    {
+        const float* wsrc[3] = {w_phi, w_c, w_rho};
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+            if (wsrc[q])
+                e = cudaMemcpy2DAsync(lamA[q], size_t(pitch) * sizeof(float), wsrc[q], size_t(pitch) * sizeof(float),
+                                      size_t(nx) * sizeof(float), size_t(ny), cudaMemcpyDeviceToDevice, s);
+    }
+    std::vector<float*> lam = lamA, lamNext = lamB;
+    auto vjp = [&](const std::vector<float*>& v, const std::vector<float*>& x, double pscale, float scale,
+                   const std::vector<float*>* b1, const std::vector<float*>* b2, const std::vector<float*>& out) {
+        if (e != cudaSuccess) return;
+        vjp_a_kernel<<<nb, ADJ_THREADS, 0, s>>>(ac, v[0], v[1], v[2], x[0], x[1], x[2], muc_b, M_b, muf_b, s_b,
+                                                partials);
+        accumulate_kernel<<<1, ADJ_THREADS, 0, s>>>(partials, nb, pscale, acc);
+        vjp_b_kernel<<<nb, ADJ_THREADS, 0, s>>>(ac, v[0], v[1], v[2], x[2], muc_b, M_b, muf_b, s_b, scale,
+                                                b1 ? (*b1)[0] : nullptr, b1 ? (*b1)[1] : nullptr,
+                                                b1 ? (*b1)[2] : nullptr, b2 ? (*b2)[0] : nullptr,
+                                                b2 ? (*b2)[1] : nullptr, b2 ? (*b2)[2] : nullptr, out[0], out[1],
+                                                out[2]);
+        e = cudaGetLastError();
+    };
+    const double dt = p->dt;
+    for (long sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+        const long t0 = sg * K, len = std::min<long>(K, nsteps - t0);
+        // recompute the segment's states t0 .. t0+len-1
+        {
+            std::vector<float*> c = ckpt(sg), s0 = segst(0);
+            const float* src[3] = {c[0], c[1], c[2]};
+            copy3(s0.data(), src);
+            for (long i = 1; i < len && e == cudaSuccess; ++i) step(segst(i - 1), segst(i));
+        }
+        for (long i = len - 1; i >= 0 && e == cudaSuccess; --i) {
+            const std::vector<float*> u = segst(i);
+            // u* = u + dt/2 R(u)
+            e = launch_euler(khalf, p->phi_mode, mob, u[0], u[1], u[2], us[0], us[1], us[2], s);
+            // w* = dt J(u*)^T w'
+            vjp(us, lam, dt, float(dt), nullptr, nullptr, lamS);
+            // w = w' + w* + dt/2 J(u)^T w*
+            vjp(u, lamS, 0.5 * dt, float(0.5 * dt), &lam, &lamS, lamNext);
+            std::swap(lam, lamNext);
+        }
+    }
+    if (e == cudaSuccess) {
+        float* g[3] = {g_phi0, g_c0, g_rho0};
+        const float* src[3] = {lam[0], lam[1], lam[2]};
+        copy3(g, src);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_params, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return afail(PF_ERR_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    return PF_OK;
+}
+
+const char* pf_adjoint_last_error(void) { return g_adj_error.c_str(); }
+
+}  // extern "C"

@@ -93,16 +93,7 @@ int check_params(const pf_params* p)
     return PF_OK;
 }
 
-void velocity(const pf_params* p, double* vx, double* vy)
-{
-    if (!p->deposition) {
-        *vx = *vy = 0.0;
-        return;
-    }
-    const double a = p->v_angle_deg * (M_PI / 180.0);
-    *vx = p->v_mag * std::cos(a);
-    *vy = -p->v_mag * std::sin(a);
-}
+void velocity(const pf_params* p, double* vx, double* vy) { pf::velocity_of(*p, vx, vy); }
 
 // |R(z)| of the explicit midpoint method, R(z) = 1 + z + z^2/2.
 double midpoint_gain(std::complex<double> z) { return std::abs(1.0 + z + 0.5 * z * z); }
@@ -122,54 +113,6 @@ bool vapor_stable(const pf_params* p, double dt)
         }
     }
     return true;
-}
-
-pf::StepConst step_const(const pf_params* p, int nx, int ny, int pitch)
-{
-    pf::StepConst k{};
-    const double dx2 = p->dx * p->dx;
-    double vx, vy;
-    velocity(p, &vx, &vy);
-    k.nx = nx;
-    k.ny = ny;
-    k.pitch = pitch;
-    k.Wc = float(p->W_c);
-    k.Wf = float(p->W_phi);
-    k.kc = float(p->kappa_c / dx2);
-    k.kf = float(p->kappa_phi / dx2);
-    k.MBb = float(p->MB_bulk);
-    k.dMb = float(p->MA_bulk - p->MB_bulk);
-    k.MBs = float(p->MB_surf);
-    k.dMs = float(p->MA_surf - p->MB_surf);
-    k.nisig2 = (p->sigma_surf > 0.0) ? float(-1.0 / (M_LN2 * p->sigma_surf * p->sigma_surf)) : 0.f;
-    k.cR = float(0.5 / dx2);
-    k.cF = (p->phi_mode == 0) ? float(p->M_phi / dx2) : float(-p->L_phi);
-    k.ax = float(vx / (2.0 * p->dx));
-    k.ay = float(vy / (2.0 * p->dx));
-    k.cD = float(p->D_rho / dx2);
-    k.rho_top = float(p->rho_top);
-    k.dt = float(p->dt);
-    return k;
-}
-
-int mob_kind(const pf_params* p)
-{
-    if (p->MA_surf != 0.0 || p->MB_surf != 0.0) return pf::MOB_SURF;
-    return (p->MA_bulk == p->MB_bulk) ? pf::MOB_UNIFORM : pf::MOB_BULK;
-}
-
-pf::DiagConst diag_const(const pf_params* p, int nx, int ny, int pitch)
-{
-    pf::DiagConst d{};
-    d.nx = nx;
-    d.ny = ny;
-    d.pitch = pitch;
-    d.Wc = float(p->W_c);
-    d.Wf = float(p->W_phi);
-    d.area = p->dx * p->dx;
-    d.hkf = 0.5 * p->kappa_phi;
-    d.hkc = 0.5 * p->kappa_c;
-    return d;
 }
 
 }  // namespace
@@ -373,9 +316,9 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
     h->hist = reinterpret_cast<long long*>(w + L.hist);
     h->hist_cap = cap;
     h->err = reinterpret_cast<int*>(w + L.err);
-    h->k = step_const(p, nx, ny, pitch);
-    h->d = diag_const(p, nx, ny, pitch);
-    h->mob = mob_kind(p);
+    h->k = pf::step_const_of(*p, nx, ny, pitch);
+    h->d = pf::diag_const_of(*p, nx, ny, pitch);
+    h->mob = pf::mob_kind_of(*p);
     h->tile = pf::choose_tile(nx, ny);
     h->gexec = nullptr;
     h->gsteps = 0;
@@ -418,9 +361,10 @@ int pf_step(pf_handle* h, long n)
     }
     if (h->cur != 0) {
         // leave the state in the caller's buffers
-        const size_t bytes = size_t(h->ny) * size_t(h->pitch) * sizeof(float);
-        for (int q = 0; q < 3; ++q) {
-            cudaError_t e = cudaMemcpyAsync(h->u[0][q], h->u[1][q], bytes, cudaMemcpyDeviceToDevice, h->stream);
+        const size_t rowb = size_t(h->pitch) * sizeof(float);
+        for (int q = 0; q < 3; ++q) {  // the nx model columns; the caller's padding is left alone
+            cudaError_t e = cudaMemcpy2DAsync(h->u[0][q], rowb, h->u[1][q], rowb, size_t(h->nx) * sizeof(float),
+                                              size_t(h->ny), cudaMemcpyDeviceToDevice, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "copy back");
         }
         h->cur = 0;
@@ -521,7 +465,7 @@ int pf_diagnostics(const pf_params* p, int nx, int ny, int pitch, const float* p
     if (work_bytes < pf_diag_workspace_size(nx, ny))
         return fail(PF_ERR_LAYOUT, "workspace of %zu bytes, %zu needed", work_bytes, pf_diag_workspace_size(nx, ny));
     char* w = static_cast<char*>(work);
-    cudaError_t e = pf::launch_diag(diag_const(p, nx, ny, pitch), phi, c, rho, reinterpret_cast<double*>(w),
+    cudaError_t e = pf::launch_diag(pf::diag_const_of(*p, nx, ny, pitch), phi, c, rho, reinterpret_cast<double*>(w),
                                     reinterpret_cast<int*>(w + pf_diag_error_offset(nx, ny)), out_dev, nullptr, 0,
                                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "diagnostic launch");

@@ -80,44 +80,6 @@ bool dt_ok(const pf_params& p)
     return p.dt > 0.0 && p.dt <= lim[0] * (1.0 + 1e-12);
 }
 
-int mob_of(const pf_params& p)
-{
-    if (p.MA_surf != 0.0 || p.MB_surf != 0.0) return pf::MOB_SURF;
-    return (p.MA_bulk == p.MB_bulk) ? pf::MOB_UNIFORM : pf::MOB_BULK;
-}
-
-pf::StepConst const_of(const pf_params& p, int nx, int ny, int pitch)
-{
-    pf::StepConst k{};
-    const double dx2 = p.dx * p.dx;
-    double vx = 0.0, vy = 0.0;
-    if (p.deposition) {
-        const double a = p.v_angle_deg * (M_PI / 180.0);
-        vx = p.v_mag * std::cos(a);
-        vy = -p.v_mag * std::sin(a);
-    }
-    k.nx = nx;
-    k.ny = ny;
-    k.pitch = pitch;
-    k.Wc = float(p.W_c);
-    k.Wf = float(p.W_phi);
-    k.kc = float(p.kappa_c / dx2);
-    k.kf = float(p.kappa_phi / dx2);
-    k.MBb = float(p.MB_bulk);
-    k.dMb = float(p.MA_bulk - p.MB_bulk);
-    k.MBs = float(p.MB_surf);
-    k.dMs = float(p.MA_surf - p.MB_surf);
-    k.nisig2 = (p.sigma_surf > 0.0) ? float(-1.0 / (M_LN2 * p.sigma_surf * p.sigma_surf)) : 0.f;
-    k.cR = float(0.5 / dx2);
-    k.cF = (p.phi_mode == 0) ? float(p.M_phi / dx2) : float(-p.L_phi);
-    k.ax = float(vx / (2.0 * p.dx));
-    k.ay = float(vy / (2.0 * p.dx));
-    k.cD = float(p.D_rho / dx2);
-    k.rho_top = float(p.rho_top);
-    k.dt = float(p.dt);
-    return k;
-}
-
 }  // namespace
 
 struct pf_ens {
@@ -228,7 +190,7 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
             return efail(PF_ERR_ARG, "run %d: bad dx or phi_mode", r);
         if ((p.MA_surf != 0.0 || p.MB_surf != 0.0) && !(p.sigma_surf > 0.0))
             return efail(PF_ERR_ARG, "run %d: sigma_surf must be positive", r);
-        if (p.phi_mode != params[0].phi_mode || mob_of(p) != mob_of(params[0]))
+        if (p.phi_mode != params[0].phi_mode || pf::mob_kind_of(p) != pf::mob_kind_of(params[0]))
             return efail(PF_ERR_ARG, "run %d: all runs must share phi_mode and the mobility form", r);
         if (!dt_ok(p)) return efail(PF_ERR_UNSTABLE, "run %d: dt=%.6g outside (0, stability limit]", r, p.dt);
     }
@@ -246,7 +208,7 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
     e->host_runs.resize(nruns);
     for (int r = 0; r < nruns; ++r) {
         pf::EnsRun& R = e->host_runs[r];
-        R.k = const_of(params[r], nx[r], ny[r], pitch[r]);
+        R.k = pf::step_const_of(params[r], nx[r], ny[r], pitch[r]);
         const size_t plane = size_t(ny[r]) * size_t(pitch[r]);
         float* st = reinterpret_cast<float*>(w + L.state[r]);
         R.f[0][0] = phi[r];
@@ -288,7 +250,7 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
     for (int r = 0; r < nruns; ++r) cells += (long long)nx[r] * ny[r];
     e->tile = cells / nruns <= (1LL << 20) ? pf::TILE_SMALL : pf::TILE_LARGE;
     e->phi_mode = params[0].phi_mode;
-    e->mob = mob_of(params[0]);
+    e->mob = pf::mob_kind_of(params[0]);
     e->parity = 0;
     e->step = 0;
     e->partials = reinterpret_cast<double*>(w + L.partials);
@@ -331,10 +293,11 @@ int pf_ens_step(pf_ens* e, long n)
     }
     if (e->parity != 0) {  // leave every run's state in the caller's buffers
         for (int r = 0; r < e->nruns; ++r) {
-            const size_t bytes = size_t(e->ny[r]) * e->pitch[r] * sizeof(float);
-            for (int q = 0; q < 3; ++q) {
-                cudaError_t c = cudaMemcpyAsync(e->host_runs[r].f[0][q], e->host_runs[r].f[1][q], bytes,
-                                                cudaMemcpyDeviceToDevice, e->stream);
+            const size_t rowb = size_t(e->pitch[r]) * sizeof(float);
+            for (int q = 0; q < 3; ++q) {  // the nx model columns; the caller's padding is left alone
+                cudaError_t c = cudaMemcpy2DAsync(e->host_runs[r].f[0][q], rowb, e->host_runs[r].f[1][q], rowb,
+                                                  size_t(e->nx[r]) * sizeof(float), size_t(e->ny[r]),
+                                                  cudaMemcpyDeviceToDevice, e->stream);
                 if (c != cudaSuccess) return efail(PF_ERR_CUDA, "copy back: %s", cudaGetErrorString(c));
             }
         }
@@ -397,16 +360,7 @@ int pf_ens_diag(pf_ens* e, int run, double out[4])
 {
     if (!e || !out) return efail(PF_ERR_ARG, "null pointer");
     if (run < 0 || run >= e->nruns) return efail(PF_ERR_ARG, "run %d out of range", run);
-    const pf_params& p = e->p[run];
-    pf::DiagConst d{};
-    d.nx = e->nx[run];
-    d.ny = e->ny[run];
-    d.pitch = e->pitch[run];
-    d.Wc = float(p.W_c);
-    d.Wf = float(p.W_phi);
-    d.area = p.dx * p.dx;
-    d.hkf = 0.5 * p.kappa_phi;
-    d.hkc = 0.5 * p.kappa_c;
+    const pf::DiagConst d = pf::diag_const_of(e->p[run], e->nx[run], e->ny[run], e->pitch[run]);
     const pf::EnsRun& R = e->host_runs[run];
     cudaError_t c = pf::launch_diag(d, R.f[e->parity][0], R.f[e->parity][1], R.f[e->parity][2], e->partials, e->err,
                                     e->out, nullptr, 0, e->stream);

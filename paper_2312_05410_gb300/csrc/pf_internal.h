@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pf.h"
+
 namespace pf {
 
 // FP32 constants of one explicit midpoint step, folded from pf_params on the host.
@@ -24,6 +26,7 @@ struct StepConst {
 };
 
 enum MobKind { MOB_UNIFORM = 0, MOB_BULK = 1, MOB_SURF = 2 };
+
 
 // Output tile of the fused step kernel (4-cell halo staged around it): 56 columns
 // by tile_height(kind) rows; TILE_SMALL gives small grids many CTAs.
@@ -51,6 +54,9 @@ cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob,
                         const float* phi0, const float* c0, const float* rho0,
                         float* phi1, float* c1, float* rho1, cudaStream_t s);
 size_t step_smem_bytes(int tile);
+// One forward-Euler update u + k.dt R(u) (the adjoint's u* with k.dt = dt/2), small tile.
+cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,
+                         const float* rho0, float* phi1, float* c1, float* rho1, cudaStream_t s);
 
 // Diagnostics: per-block FP64 partials then a fixed-order final reduction.
 struct DiagConst {
@@ -68,5 +74,11 @@ cudaError_t launch_diag(const DiagConst& d, const float* phi, const float* c, co
                         cudaStream_t s);
 // Reset the history bookkeeping and the error word of a workspace.
 cudaError_t launch_reset(long long* hist, long long capacity, long long next_step, int* err, cudaStream_t s);
+
+// Host-side folding of pf_params (shared by the single-run, ensemble and adjoint layers).
+void velocity_of(const pf_params& p, double* vx, double* vy);
+StepConst step_const_of(const pf_params& p, int nx, int ny, int pitch);
+DiagConst diag_const_of(const pf_params& p, int nx, int ny, int pitch);
+int mob_kind_of(const pf_params& p);
 
 }  // namespace pf

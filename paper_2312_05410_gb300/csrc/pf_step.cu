@@ -228,7 +228,9 @@ __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, i
 }
 
 // One step of the output tile with corner (x0, y0) of one run (the whole CTA).
-template <int TY, int S, int PHI_MODE, int MOB>
+// STAGES = 2: the explicit midpoint step; STAGES = 1: one forward-Euler update
+// u + dt R(u) with the dt held in k (the adjoint uses it for u* with dt/2).
+template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2>
 __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, const float* __restrict__ phi0,
                                           const float* __restrict__ c0, const float* __restrict__ rho0,
                                           float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1)
@@ -306,6 +308,16 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
     const int lo2 = 2 * lane;  // the lane's pair column
     int r0, n;
 
+    if (STAGES == 1) {  // u + dt R(u) on the output rows, straight to global memory
+        segment(dlo > HALO ? dlo : HALO, dhi < HALO + TY ? dhi : HALO + TY, S, warp, r0, n);
+        const int gx = gx0 + lo2;
+        const bool store_x = (lo2 >= HALO) && (lo2 < HALO + TXO) && gx < nx;
+        const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
+        stage<G::L2, PX, PLANE, PHI_MODE, MOB, true>(k, U + lo2, U + lo2, nullptr, r0, n, phi1, c1, rho1, g_off,
+                                                     pitch, store_x, gx + 1 < nx);
+        return;
+    }
+
     // ---- stage 1: u* on staged rows [2, LY-2) inside the domain
     segment(dlo > 2 ? dlo : 2, dhi < LY - 2 ? dhi : LY - 2, S, warp, r0, n);
     stage<G::L1, PX, PLANE, PHI_MODE, MOB, false>(k, U + lo2, nullptr, B + lo2, r0, n, nullptr, nullptr, nullptr, 0,
@@ -356,6 +368,16 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
     step_tile<TY, S, PHI_MODE, MOB>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
 }
 
+// One forward-Euler update of one run (dt taken from k).
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
+euler_kernel(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
+             const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
+             float* __restrict__ rho1)
+{
+    step_tile<TY, S, PHI_MODE, MOB, 1>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
+}
+
 // One step of every run of an ensemble: CTA b takes tile b of the table; runs
 // step in lockstep, so one parity bit says which buffer of each run is current.
 template <int TY, int S, int PHI_MODE, int MOB>
@@ -402,6 +424,21 @@ cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const
 {
     using G = Geo<TY, S>;
     auto kern = step_kernel<TY, S, PHI_MODE, MOB>;
+    static bool configured = false;
+    const dim3 grid((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
+    cudaError_t e = configure_smem(kern, configured, G::BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::BYTES, s, attr);
+    return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1);
+}
+
+template <int TY, int S, int PHI_MODE, int MOB>
+cudaError_t launch_euler_t(const StepConst& k, const float* f0, const float* c0, const float* r0, float* f1,
+                           float* c1, float* r1, cudaStream_t s)
+{
+    using G = Geo<TY, S>;
+    auto kern = euler_kernel<TY, S, PHI_MODE, MOB>;
     static bool configured = false;
     const dim3 grid((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
     cudaError_t e = configure_smem(kern, configured, G::BYTES);
@@ -496,6 +533,20 @@ cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob, con
     if (tile == TILE_MEDIUM)
         return launch_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
     return launch_tile<PF_LARGE_TY, PF_LARGE_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+}
+
+cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
+                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s)
+{
+    constexpr int TY = PF_SMALL_TY, S = PF_SMALL_S;
+    if (phi_mode == 0) {
+        if (mob == MOB_UNIFORM) return launch_euler_t<TY, S, 0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
+        if (mob == MOB_BULK) return launch_euler_t<TY, S, 0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
+        return launch_euler_t<TY, S, 0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
+    }
+    if (mob == MOB_UNIFORM) return launch_euler_t<TY, S, 1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
+    if (mob == MOB_BULK) return launch_euler_t<TY, S, 1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
+    return launch_euler_t<TY, S, 1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
 }
 
 cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,

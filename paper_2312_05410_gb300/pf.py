@@ -82,6 +82,12 @@ def _load():
     L.pf_ens_diag.argtypes, L.pf_ens_diag.restype = [vp, C.c_int, C.POINTER(C.c_double)], C.c_int
     L.pf_ens_destroy.argtypes, L.pf_ens_destroy.restype = [vp], C.c_int
     L.pf_ens_last_error.argtypes, L.pf_ens_last_error.restype = [], C.c_char_p
+    L.pf_adjoint_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int, C.c_long, C.c_int]
+    L.pf_adjoint_workspace_size.restype = sz
+    L.pf_adjoint.argtypes = [P, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_long, C.c_int, vp, vp, vp, vp, vp, vp,
+                             C.POINTER(C.c_double), vp, vp, vp, vp, sz, vp]
+    L.pf_adjoint.restype = C.c_int
+    L.pf_adjoint_last_error.argtypes, L.pf_adjoint_last_error.restype = [], C.c_char_p
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
     L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
     return L
@@ -342,3 +348,95 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- adjoint
+def device_fields(arrays, device="cuda"):
+    """(ny, pitch) float32 CUDA tensors holding the given (ny, nx) arrays."""
+    import torch
+
+    out = []
+    for a in arrays:
+        a = np.asarray(a, dtype=np.float32)
+        ny, nx = a.shape
+        t = torch.zeros((ny, padded_pitch(nx)), dtype=torch.float32, device=device)
+        t[:, :nx] = torch.from_numpy(a).to(device)
+        out.append(t)
+    return out
+
+
+def adjoint(params: dict, init, nx: int, nsteps: int, K: int, w_phi, w_c, w_rho=None, stream=None):
+    """Gradient of sum(w . u_N) through nsteps steps (pf_adjoint).
+
+    init, w_*: (ny, pitch) float32 CUDA tensors (as made by device_fields), model
+    width nx; returns {"phi0", "c0", "rho0": tensors, "v_mag", "m_scale", "kappa_c":
+    floats, "final": (phi, c, rho)}.
+    """
+    import torch
+
+    phi0, c0, rho0 = init
+    ny, pitch = phi0.shape
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    nbytes = int(lib.pf_adjoint_workspace_size(nx, ny, pitch, int(nsteps), int(K)))
+    if nbytes == 0:
+        raise PFError(PF_ERR_ARG, "bad adjoint sizes")
+    work = torch.empty(nbytes + 256, dtype=torch.uint8, device=phi0.device)
+    wp = (work.data_ptr() + 255) // 256 * 256
+    g = [torch.zeros_like(phi0) for _ in range(3)]
+    fin = [torch.zeros_like(phi0) for _ in range(3)]
+    gp = (C.c_double * 3)()
+    torch.cuda.synchronize()
+    rc = lib.pf_adjoint(C.byref(Params.from_dict(params)), nx, ny, pitch, phi0.data_ptr(), c0.data_ptr(),
+                        rho0.data_ptr(), int(nsteps), int(K), w_phi.data_ptr(), w_c.data_ptr(),
+                        None if w_rho is None else w_rho.data_ptr(), g[0].data_ptr(), g[1].data_ptr(),
+                        g[2].data_ptr(), gp, fin[0].data_ptr(), fin[1].data_ptr(), fin[2].data_ptr(), wp, nbytes,
+                        stream.cuda_stream)
+    if rc != PF_OK:
+        raise PFError(rc, f"{strerror(rc)}: {lib.pf_adjoint_last_error().decode()}")
+    return {"phi0": g[0], "c0": g[1], "rho0": g[2], "v_mag": gp[0], "m_scale": gp[1], "kappa_c": gp[2],
+            "final": tuple(fin)}
+
+
+def _scaled(params: dict, v_mag: float, m_scale: float, kappa_c: float) -> dict:
+    q = dict(params, v_mag=v_mag, kappa_c=kappa_c)
+    for k in ("MA_bulk", "MB_bulk", "MA_surf", "MB_surf"):
+        q[k] = params[k] * m_scale
+    return q
+
+
+def make_run_function():
+    """torch.autograd.Function: (v_mag, m_scale, kappa_c, phi0, c0, rho0) -> final (phi, c, rho).
+
+    m_scale multiplies the four composition-mobility coefficients.  Forward runs the
+    fused step kernels; backward runs the hand-written adjoint (checkpoints every K).
+    Fields are (ny, pitch) float32 CUDA tensors of model width nx.
+    """
+    import torch
+
+    class PFRun(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v_mag, m_scale, kappa_c, phi0, c0, rho0, params, nx, nsteps, K):
+            q = _scaled(params, float(v_mag), float(m_scale), float(kappa_c))
+            sim = Sim(q, *(t[:, :nx].detach().cpu().numpy() for t in (phi0, c0, rho0)), history_rows=1)
+            sim.step(int(nsteps))
+            out = tuple(t.clone() for t in sim.fields)
+            sim.close()
+            ctx.save_for_backward(v_mag, m_scale, kappa_c, phi0, c0, rho0)
+            ctx.q, ctx.nx, ctx.nsteps, ctx.K = q, int(nx), int(nsteps), int(K)
+            return out
+
+        @staticmethod
+        def backward(ctx, gf, gc, gr):
+            v_mag, m_scale, kappa_c, phi0, c0, rho0 = ctx.saved_tensors
+            z = torch.zeros_like(phi0)
+            gf = z if gf is None else gf.contiguous()
+            gc = z if gc is None else gc.contiguous()
+            gr = z if gr is None else gr.contiguous()
+            res = adjoint(ctx.q, (phi0.contiguous(), c0.contiguous(), rho0.contiguous()), ctx.nx, ctx.nsteps,
+                          ctx.K, gf, gc, gr)
+            dv = torch.tensor(res["v_mag"], dtype=v_mag.dtype, device=v_mag.device)
+            dm = torch.tensor(res["m_scale"] / float(m_scale), dtype=m_scale.dtype, device=m_scale.device)
+            dk = torch.tensor(res["kappa_c"], dtype=kappa_c.dtype, device=kappa_c.device)
+            return dv, dm, dk, res["phi0"], res["c0"], res["rho0"], None, None, None, None
+
+    return PFRun
