@@ -54,6 +54,9 @@ WORKLOADS = {
                              steps=50000, desc="plain DNS 512x512, 50000 steps, oblique incidence at 50 degrees"),
     "paper512_ac": dict(spec=I.PAPER_512["spec"], params=dict(I.PAPER_512["params"], phi_mode=1),
                         steps=50000, desc="plain DNS 512x512, 50000 steps, Allen-Cahn order parameter + source"),
+    "adjoint256": dict(kind="adjoint", spec=I.FilmSpec(256, 256, 16.0, seed=4), params=dict(v_mag=0.4), steps=1000,
+                       K=50, bytes_per_cell_update=84,
+                       desc="adjoint 256x256, 1000 steps, checkpoint every 50, gradient of a final-state loss"),
     "ensemble64": dict(kind="ensemble", n_runs=64, seed=3, steps=10000,
                        desc="batched DNS ensemble: 64 runs, sides in {128,192,256,384,512}, V~U[0.1,0.9], "
                             "c_inc~U[0.3,0.7], 10000 steps"),
@@ -200,6 +203,52 @@ class EnsembleRun:
         self.ens.close()
 
 
+class AdjointRun:
+    """Gradient of a final-microstructure loss through nsteps steps (forward with checkpoints
+    every K steps, then the hand-written adjoint backwards), as one pf_adjoint call."""
+
+    def __init__(self, pf, W):
+        import torch
+
+        spec = W["spec"]
+        p = I.default_params(**W["params"])
+        p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
+        self.pf, self.p, self.nx = pf, p, spec.nx
+        self.nsteps, self.K = W["steps"], W["K"]
+        st = I.film_state(spec, p)
+        self.fields = pf.device_fields(st)
+        # target: the same film deposited 30 % faster (the gradient points towards its rate)
+        tsim = pf.Sim(dict(p, v_mag=1.3 * p["v_mag"]), *st)
+        tsim.step(self.nsteps)
+        self.target = [t.clone() for t in tsim.fields]
+        tsim.close()
+        self.stream = torch.cuda.current_stream()
+        self.cells = spec.nx * spec.ny
+        self.w = [torch.zeros_like(t) for t in self.fields]
+        self.launches = self.nsteps * (1 + 1 + 1 + 6)  # forward + recompute + Euler + two (A, sum, B) passes
+        self.config = {"nx": spec.nx, "ny": spec.ny, "timesteps_per_run": self.nsteps, "checkpoint_every": self.K,
+                       "loss": "sum (phi_N - phi_T)^2 + (c_N - c_T)^2, target deposited 1.3x faster",
+                       "launch": "pf_adjoint: forward with checkpoints, segment recompute, adjoint passes"}
+        self.last = None
+
+    def reset_counters(self):
+        pass
+
+    def run(self):
+        # cotangent of the loss at the final state from the previous evaluation (fixed after warm-up)
+        res = self.pf.adjoint(self.p, self.fields, self.nx, self.nsteps, self.K, *self.w)
+        for q in range(2):
+            self.w[q].copy_(2.0 * (res["final"][q] - self.target[q]))
+        self.last = res
+
+    def final_diag(self):
+        r = self.last
+        return [r["v_mag"], r["m_scale"], r["kappa_c"]]
+
+    def close(self):
+        pass
+
+
 def run_native(args):
     import torch
 
@@ -216,7 +265,8 @@ def run_native(args):
     from paper_2312_05410_gb300 import pf
 
     W = WORKLOADS[args.workload]
-    R = EnsembleRun(pf, W) if W.get("kind") == "ensemble" else SingleRun(pf, W)
+    kind = W.get("kind")
+    R = EnsembleRun(pf, W) if kind == "ensemble" else (AdjointRun(pf, W) if kind == "adjoint" else SingleRun(pf, W))
     stream = R.stream
     init = [t.clone() for t in R.fields]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
@@ -294,7 +344,8 @@ def run_native(args):
     # Dominant kernel: the fused step. Its average launch duration is bounded above by
     # the timed region per step launch (it also covers the diagnostic kernels and gaps).
     per_launch_s = total_s / (nsteps * args.steps)
-    achieved = BYTES_PER_CELL_UPDATE * cells / per_launch_s / 1e9
+    bpc = W.get("bytes_per_cell_update", BYTES_PER_CELL_UPDATE)
+    achieved = bpc * cells / per_launch_s / 1e9
     tr = NCU_TRAFFIC.get(args.workload)
     traffic = tr["bytes"] if tr and tr["src"] == kernel_source_hash() else None
     line = {
@@ -305,7 +356,7 @@ def run_native(args):
                         "l2": "flushed between timed runs (256 MB write)"}, **R.config),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "peak_source": peaks["source"], "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
+                     "peak_source": peaks["source"], "algorithmic_bytes_per_cell_update": bpc},
         "gpu_launches": R.launches * args.steps,
         "e2e": {"value": cells * nsteps * args.steps * ws / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
@@ -327,6 +378,8 @@ def oracle_problem(W):
     if W.get("kind") == "ensemble":
         m = I.ensemble_members(W["n_runs"], seed=W["seed"])[0]
         return m["spec"], O.with_dt(I.default_params(v_mag=m["v_mag"])), "run 0 of the ensemble"
+    if W.get("kind") == "adjoint":
+        return W["spec"], O.with_dt(I.default_params(**W["params"])), "forward steps only, on the"
     return W["spec"], O.with_dt(I.default_params(**W["params"])), "the"
 
 
