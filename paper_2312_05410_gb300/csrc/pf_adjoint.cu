@@ -39,7 +39,7 @@ namespace pf {
 namespace {
 
 constexpr int ADJ_THREADS = 256;
-constexpr int ADJ_MAX_BLOCKS = 1216;
+constexpr int ADJ_MAX_BLOCKS = 8192;
 
 struct AdjConst {
     StepConst k;
@@ -51,13 +51,16 @@ struct AdjConst {
 
 // Field access with the forward's ghost rules: x periodic; phi and c reflected
 // (mirror); rho mirrored at the bottom, rho_top above the top.
+// (Offsets are at most 2 cells, so one correction suffices unless the grid is tinier than that.)
 __device__ __forceinline__ int wrapx(int i, int nx)
 {
+    if (nx > 2) return i < 0 ? i + nx : (i >= nx ? i - nx : i);
     i %= nx;
     return i < 0 ? i + nx : i;
 }
 __device__ __forceinline__ int refl(int j, int ny)
 {
+    if (ny > 2) return j < 0 ? -1 - j : (j >= ny ? 2 * ny - 1 - j : j);
     for (int it = 0; it < 4 && (j < 0 || j >= ny); ++it) j = j < 0 ? -1 - j : 2 * ny - 1 - j;
     return j < 0 ? 0 : (j >= ny ? ny - 1 : j);
 }
@@ -286,7 +289,7 @@ vjp_b_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
 
 int adj_blocks(int nx, int ny)
 {
-    long long b = ((long long)nx * ny + 4 * ADJ_THREADS - 1) / (4 * ADJ_THREADS);
+    long long b = ((long long)nx * ny + ADJ_THREADS - 1) / ADJ_THREADS;  // one thread per cell up to the cap
     return (int)(b < 1 ? 1 : (b > ADJ_MAX_BLOCKS ? ADJ_MAX_BLOCKS : b));
 }
 
@@ -458,7 +461,7 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
                 e = cudaMemcpy2DAsync(lamA[q], size_t(pitch) * sizeof(float), wsrc[q], size_t(pitch) * sizeof(float),
                                       size_t(nx) * sizeof(float), size_t(ny), cudaMemcpyDeviceToDevice, s);
     }
-    std::vector<float*> lam = lamA, lamNext = lamB;
+    std::vector<float*> lam = lamA;
     auto vjp = [&](const std::vector<float*>& v, const std::vector<float*>& x, double pscale, float scale,
                    const std::vector<float*>* b1, const std::vector<float*>* b2, const std::vector<float*>& out) {
         if (e != cudaSuccess) return;
@@ -473,26 +476,62 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
         e = cudaGetLastError();
     };
     const double dt = p->dt;
-    for (long sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
-        const long t0 = sg * K, len = std::min<long>(K, nsteps - t0);
-        // recompute the segment's states t0 .. t0+len-1
-        {
-            std::vector<float*> c = ckpt(sg), s0 = segst(0);
-            const float* src[3] = {c[0], c[1], c[2]};
-            copy3(s0.data(), src);
-            for (long i = 1; i < len && e == cudaSuccess; ++i) step(segst(i - 1), segst(i));
-        }
+    // One segment: recompute its states from segst(0), then walk them backwards.  The cotangent
+    // starts and ends in lamA (an odd length ends with a copy), so a full segment has fixed
+    // pointers and is captured once as a CUDA graph and replayed for every full segment.
+    auto segment_body = [&](long len) {
+        for (long i = 1; i < len && e == cudaSuccess; ++i) step(segst(i - 1), segst(i));
+        std::vector<float*> l = lamA, ln = lamB;
         for (long i = len - 1; i >= 0 && e == cudaSuccess; --i) {
             const std::vector<float*> u = segst(i);
             // u* = u + dt/2 R(u)
             e = launch_euler(khalf, p->phi_mode, mob, u[0], u[1], u[2], us[0], us[1], us[2], s);
             // w* = dt J(u*)^T w'
-            vjp(us, lam, dt, float(dt), nullptr, nullptr, lamS);
+            vjp(us, l, dt, float(dt), nullptr, nullptr, lamS);
             // w = w' + w* + dt/2 J(u)^T w*
-            vjp(u, lamS, 0.5 * dt, float(0.5 * dt), &lam, &lamS, lamNext);
-            std::swap(lam, lamNext);
+            vjp(u, lamS, 0.5 * dt, float(0.5 * dt), &l, &lamS, ln);
+            std::swap(l, ln);
+        }
+        if (l != lamA) {
+            const float* src[3] = {l[0], l[1], l[2]};
+            copy3(lamA.data(), src);
+        }
+    };
+    cudaGraphExec_t gseg = nullptr;
+    const long full = nsteps / K;  // segments of exactly K steps
+    if (full >= 2 && e == cudaSuccess) {
+        cudaStream_t real = s;
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            s = cap;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                segment_body(K);
+                cudaGraph_t g = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&gseg, g, 0);
+                if (g) cudaGraphDestroy(g);
+            }
+            s = real;
+            cudaStreamDestroy(cap);
         }
     }
+    for (long sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+        const long t0 = sg * K, len = std::min<long>(K, nsteps - t0);
+        {
+            std::vector<float*> c = ckpt(sg), s0 = segst(0);
+            const float* src[3] = {c[0], c[1], c[2]};
+            copy3(s0.data(), src);
+        }
+        if (gseg && len == K)
+            e = cudaGraphLaunch(gseg, s);
+        else
+            segment_body(len);
+    }
+    if (gseg) cudaGraphExecDestroy(gseg);
+    lam = lamA;
     if (e == cudaSuccess) {
         float* g[3] = {g_phi0, g_c0, g_rho0};
         const float* src[3] = {lam[0], lam[1], lam[2]};

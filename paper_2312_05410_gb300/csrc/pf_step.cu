@@ -35,12 +35,23 @@
 namespace pf {
 namespace {
 
+// Pair arithmetic: packed .f32x2 instructions, or (PF_PACKED=0) two scalar FP32 operations.
+#ifndef PF_PACKED
+#define PF_PACKED 1
+#endif
 typedef float2 f2;
 __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+#if PF_PACKED
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
+#else
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
 __device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
 
@@ -55,7 +66,11 @@ struct Geo {
     static constexpr int PX = LX;             // row pitch (floats)
     static constexpr int PLANE = LY * PX;
     static constexpr int THREADS = 32 * S;    // S warps = S row segments
-    static constexpr int MINB = S <= 4 ? 5 : 3;  // resident CTAs per SM the register budget allows
+#ifndef PF_MINB_SMALL
+#define PF_MINB_SMALL 4
+#define PF_MINB_LARGE 3
+#endif
+    static constexpr int MINB = S <= 4 ? PF_MINB_SMALL : PF_MINB_LARGE;  // resident CTAs per SM the register budget allows
     static constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
     static constexpr int L1 = cdiv(TY + 4, S);  // longest stage-1 segment (u* rows)
     static constexpr int L2 = cdiv(TY, S);      // longest stage-2 segment (output rows)
