@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2312_05410_gb300 import inputs as I  # noqa: E402
+from paper_2312_05410_gb300.dist import aggregate  # noqa: E402
 
 METRIC = "DNS cell-updates/s (%HBM peak)"
 UNIT = "cell-updates/s"
@@ -302,11 +303,8 @@ def run_native(args):
         barrier()
         wall = time.perf_counter() - t0
     run_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(run_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    # max time over ranks and the cell-updates of all ranks (independent replicas)
+    total_s, all_units = aggregate(sum(run_ms) / 1e3, cells * nsteps * args.steps, device="cuda")
     final_diag = R.final_diag()
 
     # ---- end to end through the public API with host buffers (pinned H2D + D2H inside)
@@ -327,11 +325,7 @@ def run_native(args):
                 h.copy_(t, non_blocking=True)
         b.record(stream)
     barrier()
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, _ = aggregate(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, 0.0, device="cuda")
     io_bytes = sum(h.numel() * h.element_size() for h in host_in)
     R.close()
 
@@ -339,7 +333,7 @@ def run_native(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    value = cells * nsteps * args.steps * ws / total_s
+    value = all_units / total_s
     peaks = measured_peaks()
     # Dominant kernel: the fused step. Its average launch duration is bounded above by
     # the timed region per step launch (it also covers the diagnostic kernels and gaps).
@@ -358,7 +352,7 @@ def run_native(args):
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peaks["source"], "algorithmic_bytes_per_cell_update": bpc},
         "gpu_launches": R.launches * args.steps,
-        "e2e": {"value": cells * nsteps * args.steps * ws / e2e_s, "unit": UNIT,
+        "e2e": {"value": all_units / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "clocks": clk.summary(),
         "wall_s": wall,

@@ -98,8 +98,10 @@ size_t pf_workspace_size(int nx, int ny, int pitch, int history_rows);
  *                history_rows) bytes, 256-byte aligned; contents undefined on entry.
  *  stream        cudaStream_t (NULL = legacy default stream) for every launch.
  * Validates the parameters (PF_ERR_ARG), the layout (PF_ERR_LAYOUT) and
- * dt <= pf_dt_limit() (PF_ERR_UNSTABLE).  No kernel runs and nothing is copied.
- * The caller keeps ownership of every buffer; the handle holds pointers only.
+ * dt <= pf_dt_limit() (PF_ERR_UNSTABLE) before touching the device; then one
+ * tiny kernel resets the workspace's history counter and error word.  The
+ * fields are not read.  The caller keeps ownership of every buffer; the handle
+ * holds pointers only.
  */
 int pf_init(const pf_params* p, int nx, int ny, int pitch,
             float* phi, float* c, float* rho,

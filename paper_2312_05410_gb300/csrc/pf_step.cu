@@ -36,8 +36,14 @@ namespace pf {
 namespace {
 
 // Pair arithmetic: packed .f32x2 instructions, or (PF_PACKED=0) two scalar FP32 operations.
+// Operations with a constant operand (the *K helpers) can instead be issued as two scalar
+// operations reading the constant directly (PF_CONST_SCALAR=1): a packed operation needs the
+// constant broadcast into a register pair.
 #ifndef PF_PACKED
 #define PF_PACKED 1
+#endif
+#ifndef PF_CONST_SCALAR
+#define PF_CONST_SCALAR 0
 #endif
 typedef float2 f2;
 __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
@@ -45,12 +51,27 @@ __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+#if PF_CONST_SCALAR
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#else
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
+#endif
 #else
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return make_float2(a.x * b.x, a.y * b.y); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
+#if PF_CONST_SCALAR || !PF_PACKED
+__device__ __forceinline__ f2 mulK(f2 x, float a) { return make_float2(x.x * a, x.y * a); }
+__device__ __forceinline__ f2 fmaKV(float a, f2 x, f2 y) { return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y)); }
+__device__ __forceinline__ f2 fmaVK(f2 x, float a, float b) { return make_float2(fmaf(x.x, a, b), fmaf(x.y, a, b)); }
+__device__ __forceinline__ f2 fmaVVK(f2 x, f2 y, float c) { return make_float2(fmaf(x.x, y.x, c), fmaf(x.y, y.y, c)); }
+#else
+__device__ __forceinline__ f2 mulK(f2 x, float a) { return mul2(x, F2(a)); }
+__device__ __forceinline__ f2 fmaKV(float a, f2 x, f2 y) { return fma2(F2(a), x, y); }
+__device__ __forceinline__ f2 fmaVK(f2 x, float a, float b) { return fma2(x, F2(a), F2(b)); }
+__device__ __forceinline__ f2 fmaVVK(f2 x, f2 y, float c) { return fma2(x, y, F2(c)); }
 #endif
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
 __device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
@@ -98,26 +119,26 @@ template <int MOB>
 __device__ __forceinline__ void chem(const StepConst& k, f2 f, f2 c, f2 sf, f2 sc, f2& muc, f2& muf, f2& M)
 {
     const f2 ff = mul2(f, f);
-    const f2 p = fma2(fma2(F2(-0.25f), ff, F2(0.75f)), f, F2(0.5f));  // p = 1/4 (2-phi)(1+phi)^2
-    const f2 q = mul2(c, fma2(c, F2(-1.f), F2(1.f)));                  // c (1 - c)
+    const f2 p = fmaVVK(fmaVK(ff, -0.25f, 0.75f), f, 0.5f);  // p = 1/4 (2-phi)(1+phi)^2
+    const f2 q = mul2(c, fmaVK(c, -1.f, 1.f));                  // c (1 - c)
     const f2 g = mul2(q, q);                                           // g(c) = c^2 (1-c)^2
-    const f2 Wdg = mul2(q, fma2(F2(-4.f * k.Wc), c, F2(2.f * k.Wc)));  // W_c g'(c)
+    const f2 Wdg = mul2(q, fmaVK(c, -4.f * k.Wc, 2.f * k.Wc));  // W_c g'(c)
     // mu_c = p W_c g' - kappa_c L(c)
-    muc = fma2(F2(-k.kc), sc, fma2(F2(4.f * k.kc), c, mul2(p, Wdg)));
+    muc = fmaKV(-k.kc, sc, fmaKV(4.f * k.kc, c, mul2(p, Wdg)));
     // mu_phi = -W_phi phi (1 - phi^2) + p'(phi) W_c g - kappa_phi L(phi),  p' = 3/4 (1 - phi^2)
-    f2 m = mul2(fma2(F2(k.Wf), ff, F2(-k.Wf)), f);
-    m = fma2(fma2(F2(-0.75f * k.Wc), ff, F2(0.75f * k.Wc)), g, m);
-    m = fma2(F2(4.f * k.kf), f, m);
-    muf = fma2(F2(-k.kf), sf, m);
+    f2 m = mul2(fmaVK(ff, k.Wf, -k.Wf), f);
+    m = fma2(fmaVK(ff, -0.75f * k.Wc, 0.75f * k.Wc), g, m);
+    m = fmaKV(4.f * k.kf, f, m);
+    muf = fmaKV(-k.kf, sf, m);
     // M_c = p (MB + h dM) [+ exp(-(phi/sigma)^2)(MBs + h dMs)],  h = c^2 (3 - 2c)
     if (MOB == MOB_UNIFORM) {
-        M = mul2(p, F2(k.MBb));
+        M = mulK(p, k.MBb);
     } else {
-        const f2 h = mul2(mul2(c, c), fma2(F2(-2.f), c, F2(3.f)));
-        M = mul2(p, fma2(h, F2(k.dMb), F2(k.MBb)));
+        const f2 h = mul2(mul2(c, c), fmaVK(c, -2.f, 3.f));
+        M = mul2(p, fmaVK(h, k.dMb, k.MBb));
         if (MOB == MOB_SURF) {
-            const f2 t = mul2(ff, F2(k.nisig2));
-            M = fma2(make_float2(exp2f(t.x), exp2f(t.y)), fma2(h, F2(k.dMs), F2(k.MBs)), M);
+            const f2 t = mulK(ff, k.nisig2);
+            M = fma2(make_float2(exp2f(t.x), exp2f(t.y)), fmaVK(h, k.dMs, k.MBs), M);
         }
     }
 }
@@ -144,7 +165,7 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
     fw[1] = ld2(Fi + (r0 - 1) * PX);
     cw[0] = ld2(Ci + (r0 - 2) * PX);
     cw[1] = ld2(Ci + (r0 - 1) * PX);
-    const f2 hdt = F2(FINAL ? k.dt : 0.5f * k.dt);
+    const float hdt = FINAL ? k.dt : 0.5f * k.dt;
 #pragma unroll
     for (int j = 0; j < L + 2; ++j) {
         // rows entering the window: phi, c at r0 + j (t = j + 2); rho at r0 - 1 + j (t' = j + 2)
@@ -181,21 +202,20 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         const f2 r = rw[(j + 1) % 3], rN = rw[(j + 2) % 3], rS = rw[j % 3];
         const float rW = west(r), rE = east(r);
         // phi at this row is the centre of the mu row computed one iteration earlier
-        const f2 Src = mul2(r, fma2(F2(k.ax), hdiff(fWw[(j + 1) % 2], f, fEw[(j + 1) % 2]),
-                                    mul2(F2(k.ay), sub2(fN, fS))));
+        const f2 Src = mul2(r, fmaKV(k.ax, hdiff(fWw[(j + 1) % 2], f, fEw[(j + 1) % 2]), mulK(sub2(fN, fS), k.ay)));
 
         f2 Rf;
         if (PHI_MODE == 0) {
             const f2 u = mfw[iC];
             const f2 su = add2(hsum(west(u), u, east(u)), add2(mfw[iN], mfw[iS]));
-            Rf = fma2(F2(k.cF), fma2(F2(-4.f), u, su), Src);
+            Rf = fmaKV(k.cF, fmaKV(-4.f, u, su), Src);
         } else {
-            Rf = fma2(F2(k.cF), mfw[iC], Src);
+            Rf = fmaKV(k.cF, mfw[iC], Src);
         }
         // vapor: D L(rho) - div(rho v) - S
-        const f2 lap = fma2(F2(-4.f), r, add2(hsum(rW, r, rE), add2(rN, rS)));
-        const f2 nadv = fma2(F2(-k.ax), hdiff(rW, r, rE), mul2(F2(-k.ay), sub2(rN, rS)));  // -div(rho v)
-        const f2 Rr = sub2(fma2(F2(k.cD), lap, nadv), Src);
+        const f2 lap = fmaKV(-4.f, r, add2(hsum(rW, r, rE), add2(rN, rS)));
+        const f2 nadv = fmaKV(-k.ax, hdiff(rW, r, rE), mulK(sub2(rN, rS), -k.ay));  // -div(rho v)
+        const f2 Rr = sub2(fmaKV(k.cD, lap, nadv), Src);
 
         const int i = j - 2;  // output row r0 + i
         f2 bf, bc, br;
@@ -209,9 +229,9 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
             bc = cw[j % 3];
             br = r;
         }
-        const f2 of = fma2(hdt, Rf, bf);
-        const f2 oc = fma2(hdt, mul2(rc, F2(k.cR)), bc);
-        const f2 orr = fma2(hdt, Rr, br);
+        const f2 of = fmaKV(hdt, Rf, bf);
+        const f2 oc = fmaKV(hdt, mulK(rc, k.cR), bc);
+        const f2 orr = fmaKV(hdt, Rr, br);
         if (i < n) {
             if (!FINAL) {
                 const int o = (r0 + i) * PX;
