@@ -95,6 +95,24 @@ __device__ __forceinline__ Chem chem_at(const AdjConst& a, const float* phi, con
     return r;
 }
 
+// mu_c and M_c of every cell of the state (pass 0 of J_R(v)^T x).
+__global__ void __launch_bounds__(ADJ_THREADS)
+chem_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __restrict__ vc,
+            float* __restrict__ muc, float* __restrict__ Mc)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
+    const long long n = (long long)nx * ny;
+    for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * ADJ_THREADS) {
+        const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
+        const Chem C = chem_at(a, vphi, vc, j, i, nx, ny, pitch);
+        const size_t o = (size_t)j * pitch + i;
+        muc[o] = C.muc;
+        Mc[o] = C.M;
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -107,9 +125,12 @@ __device__ __forceinline__ double warp_sum(double v)
 __global__ void __launch_bounds__(ADJ_THREADS)
 vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __restrict__ vc,
              const float* __restrict__ vrho, const float* __restrict__ xphi, const float* __restrict__ xc,
-             const float* __restrict__ xrho, float* __restrict__ muc_bar, float* __restrict__ M_bar,
-             float* __restrict__ muf_bar, float* __restrict__ s_bar, double* __restrict__ partials)
+             const float* __restrict__ xrho, const float* __restrict__ muc, const float* __restrict__ Mc,
+             float* __restrict__ muc_bar, float* __restrict__ M_bar, float* __restrict__ muf_bar,
+             float* __restrict__ s_bar, double* __restrict__ partials, unsigned* __restrict__ ticket,
+             double pscale, double* __restrict__ acc)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
     const long long n = (long long)nx * ny;
     double accV = 0.0, accM = 0.0, accK = 0.0;
@@ -118,16 +139,17 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
         const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
         const size_t o = (size_t)j * pitch + i;
         const int nj[4] = {j, j, j + 1, j - 1}, ni[4] = {i + 1, i - 1, i, i};
-        const Chem C0 = chem_at(a, vphi, vc, j, i, nx, ny, pitch);
+        const float m0 = muc[o], M0 = Mc[o];
         const float wc = xc[o];
         float mub = 0.f, Mb = 0.f, Rc = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const Chem Cn = chem_at(a, vphi, vc, nj[q], ni[q], nx, ny, pitch);
+            // a ghost neighbour is the mirror copy: its mu and M equal the boundary cell's
+            const float mn = mirror_at(muc, nj[q], ni[q], nx, ny, pitch), Mn = mirror_at(Mc, nj[q], ni[q], nx, ny, pitch);
             const float dw = mirror_at(xc, nj[q], ni[q], nx, ny, pitch) - wc;
-            mub += (C0.M + Cn.M) * dw;
-            Mb -= (Cn.muc - C0.muc) * dw;
-            Rc += (C0.M + Cn.M) * (Cn.muc - C0.muc);
+            mub += (M0 + Mn) * dw;
+            Mb -= (mn - m0) * dw;
+            Rc += (M0 + Mn) * (mn - m0);
         }
         mub *= a.k.cR;
         Mb *= a.k.cR;
@@ -171,35 +193,39 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
         red[2][w] = accK;
     }
     __syncthreads();
+    __shared__ bool last;
     if (threadIdx.x == 0) {
         for (int q = 0; q < 3; ++q) {
             double s = 0.0;
             for (int t = 0; t < ADJ_THREADS / 32; ++t) s += red[q][t];
             partials[(size_t)q * gridDim.x + blockIdx.x] = s;
         }
-    }
-}
-
-// acc[q] += scale * sum_b partials[q][b] (one block, fixed order).
-__global__ void __launch_bounds__(ADJ_THREADS)
-accumulate_kernel(const double* __restrict__ partials, int nblocks, double scale, double* __restrict__ acc)
-{
-    __shared__ double red[3][ADJ_THREADS / 32];
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += ADJ_THREADS)
-        for (int q = 0; q < 3; ++q) s[q] += partials[(size_t)q * nblocks + b];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int q = 0; q < 3; ++q) {
-        s[q] = warp_sum(s[q]);
-        if (lane == 0) red[q][w] = s[q];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (last) {
+        // The last block to finish adds scale x (sum of the block partials): every thread
+        // sums a fixed strided subset, then the same fixed-order warp/block reduction.
+        __threadfence();
+        double t3[3] = {0.0, 0.0, 0.0};
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += ADJ_THREADS)
+            for (int q = 0; q < 3; ++q) t3[q] += partials[(size_t)q * gridDim.x + b];
+        __syncthreads();  // red[] is reused
         for (int q = 0; q < 3; ++q) {
-            double t = 0.0;
-            for (int i = 0; i < ADJ_THREADS / 32; ++i) t += red[q][i];
-            acc[q] += scale * t;
+            t3[q] = warp_sum(t3[q]);
+            if (lane == 0) red[q][w] = t3[q];
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 3; ++q) {
+                double t = 0.0;
+                for (int i = 0; i < ADJ_THREADS / 32; ++i) t += red[q][i];
+                acc[q] += pscale * t;
+            }
+            *ticket = 0u;
+        }
+    }
 }
 
 // Pass B. out = base1 + base2 + scale * J_R(v)^T x, from pass A's fields; base1/base2 may be NULL.
@@ -212,6 +238,7 @@ vjp_b_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
              const float* __restrict__ b2rho, float* __restrict__ ophi, float* __restrict__ oc,
              float* __restrict__ orho)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
     const long long n = (long long)nx * ny;
     for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
@@ -320,7 +347,7 @@ struct AdjLayout {
     size_t seg;     // K x 3 planes
     size_t lam;     // 3 cotangents x 3 planes
     size_t ustar;   // 3 planes
-    size_t scratch; // 4 planes
+    size_t scratch; // 6 planes (mu_c, M, and the four pass-A fields)
     size_t partials, acc, total;
 };
 
@@ -341,11 +368,11 @@ bool adj_layout(int nx, int ny, int pitch, long nsteps, int K, AdjLayout& L)
     L.ustar = off;
     off += 3 * L.plane;
     L.scratch = off;
-    off += 4 * L.plane;
+    off += 6 * L.plane;
     L.partials = off;
     off = a256(off + 3 * size_t(pf::adj_blocks(nx, ny)) * sizeof(double));
     L.acc = off;
-    off = a256(off + 3 * sizeof(double));
+    off = a256(off + 3 * sizeof(double) + sizeof(unsigned));  // accumulators, then the block ticket
     L.total = off;
     return true;
 }
@@ -414,6 +441,7 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
     const int nb = adj_blocks(nx, ny);
     double* partials = reinterpret_cast<double*>(w + L.partials);
     double* acc = reinterpret_cast<double*>(w + L.acc);
+    unsigned* ticket = reinterpret_cast<unsigned*>(acc + 3);
     const long nseg = (nsteps + K - 1) / K;
 
     cudaError_t e = cudaSuccess;
@@ -446,12 +474,13 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
             copy3(fin, src);
         }
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * sizeof(double) + sizeof(unsigned), s);
     // ---- backward
     std::vector<float*> lamA = planes(L.lam), lamB = planes(L.lam + 3 * L.plane), lamS = planes(L.lam + 6 * L.plane);
     std::vector<float*> us = planes(L.ustar);
     float* sc = reinterpret_cast<float*>(w + L.scratch);
-    float *muc_b = sc, *M_b = sc + pl, *muf_b = sc + 2 * pl, *s_b = sc + 3 * pl;
+    float *muc_b = sc, *M_b = sc + pl, *muf_b = sc + 2 * pl, *s_b = sc + 3 * pl, *muc_v = sc + 4 * pl,
+          *M_v = sc + 5 * pl;
     // cotangent buffers start at zero (also a zero rho cotangent when none is given)
     if (e == cudaSuccess) e = cudaMemsetAsync(lamA[0], 0, 9 * L.plane, s);
     {
@@ -465,15 +494,30 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
     auto vjp = [&](const std::vector<float*>& v, const std::vector<float*>& x, double pscale, float scale,
                    const std::vector<float*>* b1, const std::vector<float*>* b2, const std::vector<float*>& out) {
         if (e != cudaSuccess) return;
-        vjp_a_kernel<<<nb, ADJ_THREADS, 0, s>>>(ac, v[0], v[1], v[2], x[0], x[1], x[2], muc_b, M_b, muf_b, s_b,
-                                                partials);
-        accumulate_kernel<<<1, ADJ_THREADS, 0, s>>>(partials, nb, pscale, acc);
-        vjp_b_kernel<<<nb, ADJ_THREADS, 0, s>>>(ac, v[0], v[1], v[2], x[2], muc_b, M_b, muf_b, s_b, scale,
-                                                b1 ? (*b1)[0] : nullptr, b1 ? (*b1)[1] : nullptr,
-                                                b1 ? (*b1)[2] : nullptr, b2 ? (*b2)[0] : nullptr,
-                                                b2 ? (*b2)[1] : nullptr, b2 ? (*b2)[2] : nullptr, out[0], out[1],
-                                                out[2]);
-        e = cudaGetLastError();
+        // programmatic dependent launch: each kernel waits for its predecessor before reading
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nb);
+        cfg.blockDim = dim3(ADJ_THREADS);
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const float* nil = nullptr;
+        e = cudaLaunchKernelEx(&cfg, chem_kernel, ac, (const float*)v[0], (const float*)v[1], muc_v, M_v);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernelEx(&cfg, vjp_a_kernel, ac, (const float*)v[0], (const float*)v[1],
+                                   (const float*)v[2], (const float*)x[0], (const float*)x[1], (const float*)x[2],
+                                   (const float*)muc_v, (const float*)M_v, muc_b, M_b, muf_b, s_b, partials, ticket,
+                                   pscale, acc);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernelEx(&cfg, vjp_b_kernel, ac, (const float*)v[0], (const float*)v[1],
+                                   (const float*)v[2], (const float*)x[2], (const float*)muc_b, (const float*)M_b,
+                                   (const float*)muf_b, (const float*)s_b, scale, b1 ? (const float*)(*b1)[0] : nil,
+                                   b1 ? (const float*)(*b1)[1] : nil, b1 ? (const float*)(*b1)[2] : nil,
+                                   b2 ? (const float*)(*b2)[0] : nil, b2 ? (const float*)(*b2)[1] : nil,
+                                   b2 ? (const float*)(*b2)[2] : nil, out[0], out[1], out[2]);
     };
     const double dt = p->dt;
     // One segment: recompute its states from segst(0), then walk them backwards.  The cotangent
