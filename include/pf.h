@@ -136,6 +136,19 @@ int pf_diag_history(pf_handle* h, double* out, int max_rows, int* rows);
 long pf_get_step(const pf_handle* h);
 int pf_set_step(pf_handle* h, long step);
 
+/* Polls a step kernel spends waiting for its TMA copies before it gives up
+ * (default 2^22, a few milliseconds; a copy lands in about a microsecond).  On a
+ * timeout the kernel sets the error word, lets the copies in flight land, leaves
+ * its tile unwritten and returns; pf_diag then reports PF_ERR_TIMEOUT.  A limit
+ * of 0 makes every wait give up at once, to exercise that path. */
+int pf_set_wait_limit(pf_handle* h, int polls);
+
+/* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids
+ * above 2^20 cells, which use the 56 x 32 tile), 0 when every tile uses per-thread
+ * asynchronous copies (smaller, L2-resident grids, or a driver without tensor-map
+ * support); -1 on NULL. */
+int pf_staging_mode(const pf_handle* h);
+
 /* Clear the sticky device error word (async). */
 int pf_clear_error(pf_handle* h);
 

@@ -133,6 +133,8 @@ struct pf_handle {
     pf::DiagConst d;
     int mob;
     int tile;
+    bool tma;               // interior tiles staged by TMA through maps[buffer]
+    pf::StepMaps maps[2];   // tensor maps of u[0] and u[1]
     cudaGraphExec_t gexec;
     long gsteps;  // steps per graph replay (0: no graph yet)
 };
@@ -143,7 +145,7 @@ int do_step(pf_handle* h)
 {
     const int a = h->cur, b = 1 - h->cur;
     cudaError_t e = pf::launch_step(h->k, h->tile, h->p.phi_mode, h->mob, h->u[a][0], h->u[a][1], h->u[a][2], h->u[b][0],
-                                    h->u[b][1], h->u[b][2], h->stream);
+                                    h->u[b][1], h->u[b][2], h->stream, h->tma ? &h->maps[a] : nullptr, h->err);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
     h->cur = b;
     return PF_OK;
@@ -320,6 +322,11 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
     h->d = pf::diag_const_of(*p, nx, ny, pitch);
     h->mob = pf::mob_kind_of(*p);
     h->tile = pf::choose_tile(nx, ny);
+    // TMA staging pays off for the large tile (HBM-resident grids); the short tile of small,
+    // L2-resident grids keeps the per-thread asynchronous copies, whose kernel needs fewer registers.
+    h->tma = h->tile == pf::TILE_LARGE &&
+             pf::make_step_maps(h->u[0][0], h->u[0][1], h->u[0][2], nx, ny, pitch, h->tile, &h->maps[0]) &&
+             pf::make_step_maps(h->u[1][0], h->u[1][1], h->u[1][2], nx, ny, pitch, h->tile, &h->maps[1]);
     h->gexec = nullptr;
     h->gsteps = 0;
     cudaError_t e = pf::launch_reset(h->hist, cap, 0, h->err, h->stream);
@@ -384,6 +391,7 @@ int pf_diag(pf_handle* h, double out[4])
     e = cudaMemcpy(out, h->out, 4 * sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostic read-back");
+    if (err & pf::ERR_BIT_TIMEOUT) return fail(PF_ERR_TIMEOUT, "a step kernel's bounded wait for its TMA copies ran out");
     if (err & 1) return fail(PF_ERR_NONFINITE, "a diagnostic pass saw a NaN or Inf");
     return PF_OK;
 }
@@ -423,6 +431,20 @@ int pf_set_step(pf_handle* h, long step)
     if (e != cudaSuccess) return cuda_fail(e, "history reset");
     return PF_OK;
 }
+
+int pf_set_wait_limit(pf_handle* h, int polls)
+{
+    if (!h) return fail(PF_ERR_ARG, "null handle");
+    if (polls < 0) return fail(PF_ERR_ARG, "the wait limit must be >= 0");
+    if (h->gexec) {  // the captured graph holds the old constants
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    h->k.wait_cap = polls;
+    return PF_OK;
+}
+
+int pf_staging_mode(const pf_handle* h) { return h ? (h->tma ? 1 : 0) : -1; }
 
 int pf_clear_error(pf_handle* h)
 {

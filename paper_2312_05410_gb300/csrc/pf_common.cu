@@ -2,6 +2,8 @@
 // the single-run (pf_api.cu), ensemble (pf_ens.cu) and adjoint (pf_adjoint.cu) layers.
 #include <cmath>
 
+#include <cudaTypedefs.h>
+
 #include "pf_internal.h"
 
 namespace pf {
@@ -43,6 +45,7 @@ StepConst step_const_of(const pf_params& p, int nx, int ny, int pitch)
     k.cD = float(p.D_rho / dx2);
     k.rho_top = float(p.rho_top);
     k.dt = float(p.dt);
+    k.wait_cap = 1 << 22;  // a few milliseconds of polling; a TMA box lands in about a microsecond
     return k;
 }
 
@@ -64,6 +67,44 @@ int mob_kind_of(const pf_params& p)
 {
     if (p.MA_surf != 0.0 || p.MB_surf != 0.0) return MOB_SURF;
     return (p.MA_bulk == p.MB_bulk) ? MOB_UNIFORM : MOB_BULK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// Tiled FP32 maps of the three planes of one state: dims (nx, ny), row stride pitch*4 bytes,
+// box 64 x (tile height + 8) -- the staged window of one CTA.
+bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
+                    StepMaps* out)
+{
+    const int LY = tile_height(tile) + 8;
+    if (nx < 64 || ny < LY) return false;  // no tile can be interior: the TMA path is never taken
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {cuuint64_t(nx), cuuint64_t(ny)};
+    const cuuint64_t strides[1] = {cuuint64_t(pitch) * sizeof(float)};
+    const cuuint32_t box[2] = {64u, cuuint32_t(LY)};
+    const cuuint32_t elem[2] = {1u, 1u};
+    const float* f[3] = {phi, c, rho};
+    CUtensorMap* m[3] = {&out->phi, &out->c, &out->rho};
+    for (int q = 0; q < 3; ++q)
+        if (enc(m[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(f[q]), dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    return true;
 }
 
 }  // namespace pf

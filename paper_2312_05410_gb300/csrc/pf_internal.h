@@ -1,5 +1,6 @@
 // Internal declarations shared by the kernels and the C-ABI layer (not installed).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +24,7 @@ struct StepConst {
     float cD;          // D_rho / dx^2
     float rho_top;     // reservoir ghost value above the top row
     float dt;          // time step
+    int wait_cap;      // polls of a bounded TMA wait before it reports a timeout
 };
 
 enum MobKind { MOB_UNIFORM = 0, MOB_BULK = 1, MOB_SURF = 2 };
@@ -48,11 +50,25 @@ struct EnsTile {
 cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
                             int parity, cudaStream_t s);
 
+// TMA descriptors of the three fields of one state, box = 64 columns x (tile height + 8) rows.
+struct StepMaps {
+    CUtensorMap phi, c, rho;
+};
+// Encode the maps for a state (false: the driver refused, use the cp.async staging).
+bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
+                    StepMaps* out);
+
+// Error-word bits set by kernels (bit 0: NaN/Inf seen by diagnostics).
+constexpr int ERR_BIT_TIMEOUT = 2;  // a bounded wait for a TMA copy ran out
+
 // Launch one fused step: (phi0, c0, rho0) -> (phi1, c1, rho1) with programmatic
 // dependent launch enabled (the kernel waits for the previous grid before reading).
+// maps (may be NULL) are the tensor maps of (phi0, c0, rho0): interior tiles are then
+// staged by TMA; err receives ERR_BIT_TIMEOUT if a staging wait ran out.
 cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob,
                         const float* phi0, const float* c0, const float* rho0,
-                        float* phi1, float* c1, float* rho1, cudaStream_t s);
+                        float* phi1, float* c1, float* rho1, cudaStream_t s,
+                        const StepMaps* maps = nullptr, int* err = nullptr);
 size_t step_smem_bytes(int tile);
 // One forward-Euler update u + k.dt R(u) (the adjoint's u* with k.dt = dt/2), small tile.
 cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,

@@ -32,6 +32,20 @@
 // After stage 1, CTAs that touch a boundary write the same ghost rows of u*.
 #include "pf_internal.h"
 
+// Tile heights TY and warps S of the three tile kinds (overridable for sweeps).
+#ifndef PF_SMALL_TY
+#define PF_SMALL_TY 8
+#define PF_SMALL_S 4
+#endif
+#ifndef PF_MEDIUM_TY
+#define PF_MEDIUM_TY 16
+#define PF_MEDIUM_S 4
+#endif
+#ifndef PF_LARGE_TY
+#define PF_LARGE_TY 32
+#define PF_LARGE_S 8
+#endif
+
 namespace pf {
 namespace {
 
@@ -97,6 +111,7 @@ struct Geo {
     static constexpr int L2 = cdiv(TY, S);      // longest stage-2 segment (output rows)
     static constexpr int GUARD = (L1 + 4) * PX; // rows read past a plane by the last segment's tail
     static constexpr size_t BYTES = (size_t(6) * PLANE + GUARD) * sizeof(float);
+    static constexpr size_t TMA_BYTES = BYTES + 128;  // + slack to align the TMA destinations to 128 bytes
 };
 
 // West and east neighbours of the lane's pair (x, x+1): x-1 from the lane below, x+2 from the lane above.
@@ -265,14 +280,18 @@ __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, i
 // One step of the output tile with corner (x0, y0) of one run (the whole CTA).
 // STAGES = 2: the explicit midpoint step; STAGES = 1: one forward-Euler update
 // u + dt R(u) with the dt held in k (the adjoint uses it for u* with dt/2).
-template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2>
+template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2, bool TMA = false>
 __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, const float* __restrict__ phi0,
                                           const float* __restrict__ c0, const float* __restrict__ rho0,
-                                          float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1)
+                                          float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1,
+                                          const StepMaps* maps = nullptr, int* err = nullptr)
 {
     using G = Geo<TY, S>;
     constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(128) float smraw[];
+    // TMA destinations need a 128-byte aligned base; that launch reserves the extra bytes
+    float* const sm = TMA ? reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127))
+                          : smraw;
     float* const U = sm;               // u^n: phi, c, rho
     float* const B = sm + 3 * PLANE;   // u*:  phi, c, rho (followed by the guard rows)
 
@@ -283,8 +302,48 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
     // Wait for the previous step's grid (programmatic dependent launch) before reading.
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    // ---- stage u^n with its ghost rows; every 16-byte group is an asynchronous copy
-    {
+    // ---- interior tiles: three TMA box copies (64 x LY each) completing on one mbarrier
+    bool staged = false;
+    if (TMA && gx0 >= 0 && gx0 + LX <= nx && gy0 >= 0 && gy0 + LY <= ny) {
+        __shared__ __align__(8) uint64_t mbar;
+        const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            constexpr unsigned bytes = 3u * PLANE * sizeof(float);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+            const CUtensorMap* tm[3] = {&maps->phi, &maps->c, &maps->rho};
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(U + f * PLANE);
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+                    "l"(reinterpret_cast<uint64_t>(tm[f])), "r"(gx0), "r"(gy0), "r"(mb)
+                    : "memory");
+            }
+        }
+        // bounded wait on phase 0; every thread votes so the whole CTA leaves together on a timeout
+        unsigned done = 0;
+        for (int it = 0; it < k.wait_cap && !done; ++it)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                : "=r"(done) : "r"(mb) : "memory");
+        if (__syncthreads_or(!done)) {
+            if (tid == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
+            for (int it = 0; it < (1 << 22) && !done; ++it)  // let the copies in flight land before leaving
+                asm volatile(
+                    "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                    : "=r"(done) : "r"(mb) : "memory");
+            return;
+        }
+        staged = true;
+    }
+    // ---- other tiles: stage u^n with its ghost rows; every 16-byte group is an asynchronous copy
+    if (!staged) {
         auto field = [&](int f) { return f == 0 ? phi0 : (f == 1 ? c0 : rho0); };
         auto wrap = [&](int gx) {  // periodic x; one correction suffices when nx >= LX
             if (nx >= LX) {
@@ -403,6 +462,17 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
     step_tile<TY, S, PHI_MODE, MOB>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
 }
 
+// The same, with interior tiles staged through the tensor maps of the source state.
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
+step_kernel_tma(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
+                const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
+                float* __restrict__ rho1, const __grid_constant__ StepMaps maps, int* __restrict__ err)
+{
+    step_tile<TY, S, PHI_MODE, MOB, 2, true>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1,
+                                             &maps, err);
+}
+
 // One forward-Euler update of one run (dt taken from k).
 template <int TY, int S, int PHI_MODE, int MOB>
 __global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
@@ -455,15 +525,27 @@ cudaLaunchConfig_t pdl_config(dim3 grid, int threads, size_t smem, cudaStream_t 
 
 template <int TY, int S, int PHI_MODE, int MOB>
 cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const float* r0, float* f1,
-                     float* c1, float* r1, cudaStream_t s)
+                     float* c1, float* r1, cudaStream_t s, const StepMaps* maps, int* err)
 {
     using G = Geo<TY, S>;
+    const dim3 grid((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
+    cudaLaunchAttribute attr[1];
+    // TMA staging is built for the large tile only (grids above 2^20 cells); smaller
+    // tiles ignore the maps
+    if constexpr (TY == PF_LARGE_TY && S == PF_LARGE_S) {
+        if (maps) {
+            auto kern = step_kernel_tma<TY, S, PHI_MODE, MOB>;
+            static bool configured = false;
+            cudaError_t e = configure_smem(kern, configured, G::TMA_BYTES);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::TMA_BYTES, s, attr);
+            return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1, *maps, err);
+        }
+    }
     auto kern = step_kernel<TY, S, PHI_MODE, MOB>;
     static bool configured = false;
-    const dim3 grid((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
     cudaError_t e = configure_smem(kern, configured, G::BYTES);
     if (e != cudaSuccess) return e;
-    cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::BYTES, s, attr);
     return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1);
 }
@@ -499,16 +581,17 @@ cudaError_t launch_ens_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, i
 
 template <int TY, int S>
 cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
-                        const float* r0, float* f1, float* c1, float* r1, cudaStream_t s)
+                        const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
+                        int* err)
 {
     if (phi_mode == 0) {
-        if (mob == MOB_UNIFORM) return launch_t<TY, S, 0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
-        if (mob == MOB_BULK) return launch_t<TY, S, 0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
-        return launch_t<TY, S, 0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
+        if (mob == MOB_UNIFORM) return launch_t<TY, S, 0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+        if (mob == MOB_BULK) return launch_t<TY, S, 0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+        return launch_t<TY, S, 0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
     }
-    if (mob == MOB_UNIFORM) return launch_t<TY, S, 1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s);
-    if (mob == MOB_BULK) return launch_t<TY, S, 1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s);
-    return launch_t<TY, S, 1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s);
+    if (mob == MOB_UNIFORM) return launch_t<TY, S, 1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    if (mob == MOB_BULK) return launch_t<TY, S, 1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    return launch_t<TY, S, 1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
 }
 
 template <int TY, int S>
@@ -526,19 +609,6 @@ cudaError_t launch_ens_tile(int phi_mode, int mob, const EnsTile* tiles, const E
 }
 
 }  // namespace
-
-#ifndef PF_SMALL_TY
-#define PF_SMALL_TY 8
-#define PF_SMALL_S 4
-#endif
-#ifndef PF_MEDIUM_TY
-#define PF_MEDIUM_TY 16
-#define PF_MEDIUM_S 4
-#endif
-#ifndef PF_LARGE_TY
-#define PF_LARGE_TY 32
-#define PF_LARGE_S 8
-#endif
 
 int choose_tile(int nx, int ny)
 {
@@ -561,13 +631,14 @@ size_t step_smem_bytes(int tile)
 }
 
 cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob, const float* f0, const float* c0,
-                        const float* r0, float* f1, float* c1, float* r1, cudaStream_t s)
+                        const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
+                        int* err)
 {
     if (tile == TILE_SMALL)
-        return launch_tile<PF_SMALL_TY, PF_SMALL_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+        return launch_tile<PF_SMALL_TY, PF_SMALL_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s, maps, err);
     if (tile == TILE_MEDIUM)
-        return launch_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
-    return launch_tile<PF_LARGE_TY, PF_LARGE_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s);
+        return launch_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s, maps, err);
+    return launch_tile<PF_LARGE_TY, PF_LARGE_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s, maps, err);
 }
 
 cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,

@@ -62,6 +62,8 @@ def _load():
     L.pf_get_step.argtypes, L.pf_get_step.restype = [vp], C.c_long
     L.pf_set_step.argtypes, L.pf_set_step.restype = [vp, C.c_long], C.c_int
     L.pf_clear_error.argtypes, L.pf_clear_error.restype = [vp], C.c_int
+    L.pf_set_wait_limit.argtypes, L.pf_set_wait_limit.restype = [vp, C.c_int], C.c_int
+    L.pf_staging_mode.argtypes, L.pf_staging_mode.restype = [vp], C.c_int
     L.pf_destroy.argtypes, L.pf_destroy.restype = [vp], C.c_int
     L.pf_diag_workspace_size.argtypes, L.pf_diag_workspace_size.restype = [C.c_int, C.c_int], sz
     L.pf_diag_error_offset.argtypes, L.pf_diag_error_offset.restype = [C.c_int, C.c_int], sz
@@ -157,6 +159,14 @@ def pf_set_step(h, step: int) -> int:
 
 def pf_clear_error(h) -> int:
     return lib.pf_clear_error(h)
+
+
+def pf_set_wait_limit(h, polls: int) -> int:
+    return lib.pf_set_wait_limit(h, int(polls))
+
+
+def pf_staging_mode(h) -> int:
+    return int(lib.pf_staging_mode(h))
 
 
 def pf_destroy(h) -> int:

@@ -82,6 +82,16 @@ def test_rough_random_fields(pf):
     assert max_err(got, ref) <= 1e-5
 
 
+def test_tma_staged_large_grid_matches_oracle(pf):
+    """A grid above 2^20 cells (56 x 32 tiles, interior tiles staged by TMA, boundary tiles by
+    per-thread copies with ghost rows) against the oracle."""
+    p = O.with_dt(I.default_params(v_angle_deg=75.0))
+    state = I.film_state(I.FilmSpec(1100, 1000, 40.0, seed=12), p)
+    ref = O.step(p, *state, 12)
+    got, _ = run_gpu(pf, p, state, 12)
+    assert max_err(got, ref) <= 1e-5
+
+
 def test_paper_scale_grid_graph_path(pf):
     """512 x 512, the benchmark's kernel and graph replay (diagnostics every 100 steps)."""
     cfg = I.PAPER_512
@@ -123,6 +133,14 @@ def test_composition_conserved_long_run(pf):
     assert d1[1] > d0[1]  # film grew
     assert np.all(np.isfinite(hist))
     assert hist.shape[0] == 20
+
+
+def test_tma_staging_is_used_where_tiles_fit(pf):
+    p = O.with_dt(I.default_params())
+    for (nx, ny), mode in (((2048, 1024), 1), ((1120, 960), 1), ((512, 512), 0), ((37, 23), 0)):
+        sim = pf.Sim(p, *I.film_state(I.FilmSpec(nx, ny, ny / 3.0, seed=1), p))
+        assert pf.pf_staging_mode(sim.h) == mode, (nx, ny)
+        sim.close()
 
 
 def test_runs_are_bitwise_deterministic(pf):
@@ -178,6 +196,29 @@ def test_nonfinite_is_reported(pf):
     assert rc == pf.PF_ERR_NONFINITE
     assert pf.pf_clear_error(sim.h) == 0
     sim.close()
+
+
+def test_staging_wait_timeout_is_reported_and_recoverable(pf):
+    """A bounded TMA wait that runs out (limit of zero polls) sets the error word; pf_diag reports
+    PF_ERR_TIMEOUT, the context stays usable, and with the default limit the run is correct again."""
+    p = O.with_dt(I.default_params())
+    state = I.film_state(I.FilmSpec(1120, 960, 16.0, seed=4), p)  # above 2^20 cells: TMA-staged tiles
+    sim = pf.Sim(p, *state)
+    assert pf.pf_staging_mode(sim.h) == 1
+    assert pf.pf_set_wait_limit(sim.h, 0) == 0
+    sim.step(1)
+    rc, _ = pf.pf_diag(sim.h)
+    assert rc == pf.PF_ERR_TIMEOUT
+    sim.close()
+    sim = pf.Sim(p, *state)
+    assert pf.pf_set_wait_limit(sim.h, 1 << 22) == 0
+    assert pf.pf_clear_error(sim.h) == 0
+    sim.step(10)
+    rc, _ = pf.pf_diag(sim.h)
+    assert rc == 0
+    got = sim.numpy()
+    sim.close()
+    assert max_err(got, O.step(p, *state, 10)) <= 1e-5
 
 
 def test_standalone_diagnostics_entry_point(pf):
