@@ -67,8 +67,8 @@ WORKLOADS = {
 # keyed by workload, with the hash of the kernel source it was taken on; reported as
 # null once the source changes.  Summaries: profiles/step_kernel_*_full.md.
 NCU_TRAFFIC = {
-    "paper512": {"bytes": 3169792, "src": "59d817940e9dc76c"},
-    "large4096": {"bytes": 360521216, "src": "59d817940e9dc76c"},
+    "paper512": {"bytes": 3169536, "src": "f5d11f4d9510b4d7"},
+    "large4096": {"bytes": 360379648, "src": "0862ee43f7e71514"},
 }
 
 

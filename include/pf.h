@@ -144,7 +144,7 @@ int pf_set_step(pf_handle* h, long step);
 int pf_set_wait_limit(pf_handle* h, int polls);
 
 /* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids
- * above 2^20 cells, which use the 56 x 32 tile), 0 when every tile uses per-thread
+ * above 2^20 cells, which use the 56 x 24 tile), 0 when every tile uses per-thread
  * asynchronous copies (smaller, L2-resident grids, or a driver without tensor-map
  * support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
@@ -211,7 +211,7 @@ int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
  *   shape and keep the fastest; these are real steps of the simulation (3 x
  *   (trial_steps + 2) in total).  chosen (may be NULL) receives the tile kind,
  *   seconds_per_step (may be NULL, 3 doubles) the timings.  Synchronises.
- * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x32), 2 (56x16).
+ * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x24), 2 (56x16).
  * pf_ens_diag: pf_diag of run `run` (synchronises).
  */
 typedef struct pf_ens pf_ens;

@@ -42,8 +42,8 @@
 #define PF_MEDIUM_S 4
 #endif
 #ifndef PF_LARGE_TY
-#define PF_LARGE_TY 32
-#define PF_LARGE_S 8
+#define PF_LARGE_TY 24
+#define PF_LARGE_S 4
 #endif
 
 namespace pf {

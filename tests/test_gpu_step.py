@@ -83,7 +83,7 @@ def test_rough_random_fields(pf):
 
 
 def test_tma_staged_large_grid_matches_oracle(pf):
-    """A grid above 2^20 cells (56 x 32 tiles, interior tiles staged by TMA, boundary tiles by
+    """A grid above 2^20 cells (56 x 24 tiles, interior tiles staged by TMA, boundary tiles by
     per-thread copies with ghost rows) against the oracle."""
     p = O.with_dt(I.default_params(v_angle_deg=75.0))
     state = I.film_state(I.FilmSpec(1100, 1000, 40.0, seed=12), p)
