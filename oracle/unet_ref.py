@@ -1,0 +1,198 @@
+"""Reference forward pass of the U-Net with temporal conditioning (FP64, CPU, PyTorch ops).
+
+TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: only tests, the smoke
+check and the benchmark's CPU baseline may import it.
+
+What it computes ("U-Net with temporal conditioning", Methods; readings where
+the paper is silent are marked READING):
+
+  f(dt)      = w2 sin(w1 sin(w0 dt + b0) + b1) + b2          (MLP, 2 hidden layers of 128, sin activation)
+  conv(u)    = cross-correlation with a 3x3 kernel, zero 'same' padding, no bias
+               (READING: kernel size 3x3 and zero padding; GroupNorm follows, so a bias would cancel)
+  GN(u)      = per-sample group normalisation with affine gamma/beta, eps 1e-5 (READING: 8 groups)
+  GELU(u)    = 0.5 u (1 + tanh(sqrt(2/pi)(u + 0.044715 u^3)))  (the paper's tanh form)
+  block(u)   = GELU(GN(conv(u)))
+  down       = 2x2 max pooling, stride 2
+  up         = transposed convolution, 2x2 kernel, stride 2, channel-mixing, no bias
+               (READING: the printed up-sampling formula omits the channel sums)
+
+  encoder    z1 = block(x), zp = block(down(z_{p-1})), p = 2, 3, 4       (unconditioned chain)
+  condition  zc_p = z_p * (W_p f(dt))  (per-channel product, p = 1..4)
+  decoder    d3 = up(block(zc4)); d2 = up(block(zc3 ++ d3)); d1 = up(block(zc2 ++ d2))
+  output     y  = GN(conv(block(zc1 ++ d1)))   (READING: GN with one group per output channel)
+
+Channels 32-64-128-256.  Input x = (phi, c, dt / dt_ref) planes (READING: the two
+fields plus a plane holding the jump length; the paper feeds lb = 3 frames of c).
+
+Precision model of the GPU path that this mirrors: inputs, weights and every
+stored activation are BF16 (round to nearest even); products are exact and sums
+are kept in high precision (FP64 here, FP32 on the GPU); group statistics are
+taken from the unrounded convolution outputs; GN + GELU are evaluated in high
+precision on the rounded stored values.  ``bf16`` below is written from the
+format definition (1 sign, 8 exponent, 7 fraction bits), not taken from a library.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+DT = torch.float64
+CH = (32, 64, 128, 256)
+GROUPS = 8
+EPS = 1e-5
+FDIM = 128       # width of the MLP's hidden layers and of the basis f(dt)
+IN_CH, OUT_CH = 3, 2
+
+
+def bf16(a) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), returned as float64.
+
+    The FP32 value's 16 low bits are dropped after adding 0x7FFF plus the
+    lowest kept bit (round half to even on the discarded half-word)."""
+    x = np.array(a, dtype=np.float32, copy=True)
+    shape = x.shape
+    x = x.reshape(-1)
+    u = x.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    out[np.isnan(x)] = np.nan
+    return out.reshape(shape)
+
+
+def _t(a) -> torch.Tensor:
+    return torch.as_tensor(np.asarray(a, dtype=np.float64), dtype=DT)
+
+
+def _rb(t: torch.Tensor) -> torch.Tensor:
+    return _t(bf16(t.numpy()))
+
+
+def init_weights(seed: int = 0) -> dict:
+    """Seeded He-normal weights (FP32 arrays, PyTorch conventions: conv [Cout, Cin, 3, 3], tconv
+    [Cin, Cout, 2, 2]).  The training of the network is not part of this reference."""
+    g = np.random.default_rng(seed)
+    W = {}
+
+    def he(shape, fan_in):
+        return (g.standard_normal(shape) * math.sqrt(2.0 / fan_in)).astype(np.float32)
+
+    W["mlp_w0"] = he((FDIM, 1), 1)
+    W["mlp_b0"] = (g.standard_normal(FDIM) * 0.5).astype(np.float32)
+    W["mlp_w1"] = he((FDIM, FDIM), FDIM)
+    W["mlp_b1"] = (g.standard_normal(FDIM) * 0.1).astype(np.float32)
+    W["mlp_w2"] = he((FDIM, FDIM), FDIM)
+    W["mlp_b2"] = (g.standard_normal(FDIM) * 0.1).astype(np.float32)
+    for p, c in enumerate(CH, 1):
+        W[f"proj{p}"] = (g.standard_normal((c, FDIM)) / math.sqrt(FDIM)).astype(np.float32)
+    cin = IN_CH
+    for p, c in enumerate(CH, 1):
+        W[f"enc{p}"] = he((c, cin, 3, 3), 9 * cin)
+        cin = c
+    # decoder blocks: dec4 on zc4 (256 -> 256), dec3 on zc3 ++ d3 (256 -> 128), dec2 (128 -> 64), dec1 (64 -> 32)
+    W["dec4"] = he((256, 256, 3, 3), 9 * 256)
+    W["dec3"] = he((128, 256, 3, 3), 9 * 256)
+    W["dec2"] = he((64, 128, 3, 3), 9 * 128)
+    W["dec1"] = he((32, 64, 3, 3), 9 * 64)
+    W["up4"] = he((256, 128, 2, 2), 256)
+    W["up3"] = he((128, 64, 2, 2), 128)
+    W["up2"] = he((64, 32, 2, 2), 64)
+    W["out"] = he((OUT_CH, 32, 3, 3), 9 * 32)
+    for name, c in (("enc1", 32), ("enc2", 64), ("enc3", 128), ("enc4", 256), ("dec4", 256), ("dec3", 128),
+                    ("dec2", 64), ("dec1", 32), ("out", OUT_CH)):
+        W[name + "_gamma"] = (1.0 + 0.1 * g.standard_normal(c)).astype(np.float32)
+        W[name + "_beta"] = (0.1 * g.standard_normal(c)).astype(np.float32)
+    return W
+
+
+def basis(W: dict, tau: float) -> np.ndarray:
+    """f(dt) of the MLP with sin activations, in FP64 (tau = dt / dt_ref)."""
+    h = np.sin(W["mlp_w0"].astype(np.float64)[:, 0] * tau + W["mlp_b0"])
+    h = np.sin(W["mlp_w1"].astype(np.float64) @ h + W["mlp_b1"])
+    return W["mlp_w2"].astype(np.float64) @ h + W["mlp_b2"]
+
+
+def scales(W: dict, tau: float) -> list[np.ndarray]:
+    """Per-channel conditioning factors W_p f(dt) of the four levels, in FP64."""
+    f = basis(W, tau)
+    return [W[f"proj{p}"].astype(np.float64) @ f for p in range(1, 5)]
+
+
+def conv3x3(x: torch.Tensor, w) -> torch.Tensor:
+    """Zero-padded 'same' 3x3 cross-correlation of NCHW x with w [Cout, Cin, 3, 3] (BF16 weights)."""
+    return F.conv2d(x, _t(bf16(w)), padding=1)
+
+
+def group_stats(y: torch.Tensor, groups: int):
+    n, c, h, w = y.shape
+    v = y.reshape(n, groups, (c // groups) * h * w)
+    mean = v.mean(dim=2)
+    var = ((v - mean[:, :, None]) ** 2).mean(dim=2)
+    return mean, var
+
+
+def group_norm(y_store: torch.Tensor, mean, var, gamma, beta, groups: int) -> torch.Tensor:
+    n, c, h, w = y_store.shape
+    cg = c // groups
+    m = mean.repeat_interleave(cg, dim=1)[:, :, None, None]
+    r = (1.0 / torch.sqrt(var + EPS)).repeat_interleave(cg, dim=1)[:, :, None, None]
+    return (y_store - m) * r * _t(gamma)[None, :, None, None] + _t(beta)[None, :, None, None]
+
+
+def gelu(u: torch.Tensor) -> torch.Tensor:
+    return 0.5 * u * (1.0 + torch.tanh(math.sqrt(2.0 / math.pi) * (u + 0.044715 * u ** 3)))
+
+
+def block(x: torch.Tensor, W: dict, name: str, groups: int = GROUPS, act: bool = True) -> torch.Tensor:
+    """conv -> (stats of the unrounded output) -> BF16 store -> GN -> GELU -> BF16 store."""
+    y = conv3x3(x, W[name])
+    mean, var = group_stats(y, groups)
+    y = group_norm(_rb(y), mean, var, W[name + "_gamma"], W[name + "_beta"], groups)
+    return _rb(gelu(y)) if act else y
+
+
+def down(x: torch.Tensor) -> torch.Tensor:
+    return F.max_pool2d(x, 2, 2)
+
+
+def up(x: torch.Tensor, w) -> torch.Tensor:
+    return _rb(F.conv_transpose2d(x, _t(bf16(w)), stride=2))
+
+
+def forward(W: dict, x, tau: float, taps: dict | None = None) -> np.ndarray:
+    """Network output for x [N, 3, H, W] (float array; rounded to BF16 here); returns [N, 2, H, W] FP64.
+    If `taps` is a dict it receives the intermediate tensors by name."""
+    x = _rb(_t(x))
+    s = [_t(bf16(v)) for v in scales(W, tau)]     # conditioning factors are stored as BF16
+    z1 = block(x, W, "enc1")
+    z2 = block(down(z1), W, "enc2")
+    z3 = block(down(z2), W, "enc3")
+    z4 = block(down(z3), W, "enc4")
+    zc = [_rb(z * sp[None, :, None, None]) for z, sp in zip((z1, z2, z3, z4), s)]
+    d3 = up(block(zc[3], W, "dec4"), W["up4"])
+    d2 = up(block(torch.cat([zc[2], d3], 1), W, "dec3"), W["up3"])
+    d1 = up(block(torch.cat([zc[1], d2], 1), W, "dec2"), W["up2"])
+    h1 = block(torch.cat([zc[0], d1], 1), W, "dec1")
+    y = block(h1, W, "out", groups=OUT_CH, act=False)
+    if taps is not None:
+        taps.update(z1=z1, z2=z2, z3=z3, z4=z4, zc1=zc[0], zc2=zc[1], zc3=zc[2], zc4=zc[3], d3=d3, d2=d2,
+                    d1=d1, h1=h1, y=y)
+    return y.numpy()
+
+
+def flops_per_sample(h: int, w: int) -> float:
+    """Multiply-add FLOPs (2 per MAC) of one forward pass on an h x w input."""
+    tot = 0.0
+    cin = IN_CH
+    for p, c in enumerate(CH):
+        tot += 2 * 9 * cin * c * (h >> p) * (w >> p)
+        cin = c
+    for cin, cout, p in ((256, 256, 3), (256, 128, 2), (128, 64, 1), (64, 32, 0)):
+        tot += 2 * 9 * cin * cout * (h >> p) * (w >> p)
+    for cin, cout, p in ((256, 128, 3), (128, 64, 2), (64, 32, 1)):
+        tot += 2 * cin * cout * 4 * (h >> p) * (w >> p)
+    tot += 2 * 9 * 32 * OUT_CH * h * w
+    return tot

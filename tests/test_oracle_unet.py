@@ -1,0 +1,161 @@
+"""Pins of the FP64 reference U-Net (oracle/unet_ref.py).
+
+Each building block is checked against a direct, loop-level restatement of its
+definition ("U-Net with temporal conditioning", Methods) on tiny inputs, and the
+assembled network against invariants its structure implies: a group
+normalisation after the first convolution removes an input scale, and one after
+the bottleneck's decoder block removes the scale of the deepest conditioning
+factor, but not that of the shallow ones.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+from oracle import unet_ref as U  # noqa: E402
+
+
+def test_bf16_rounding_matches_the_format():
+    # spacing at 1 is 2^-7; ties go to the even significand
+    cases = {1.0: 1.0, 1.0 + 2**-8: 1.0, 1.0 + 3 * 2**-8: 1.0 + 2**-6, 1.0 + 2**-7: 1.0 + 2**-7,
+             -2.5: -2.5, 3.0e38: 2.9975e38, 1e-40: 9.99995e-41}
+    for x, want in cases.items():
+        got = float(U.bf16(np.float32(x)))
+        assert got == pytest.approx(want, rel=2**-8), (x, got)
+    assert float(U.bf16(np.float32(1.0 + 2**-8))) == 1.0
+    assert float(U.bf16(np.float32(1.0 + 3 * 2**-8))) == 1.0 + 2**-6
+    # against an independent implementation of the same rounding
+    x = np.random.default_rng(0).standard_normal(10000).astype(np.float32) * 100
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(U.bf16(x), ref)
+
+
+def test_conv3x3_is_zero_padded_cross_correlation():
+    g = np.random.default_rng(1)
+    x = U.bf16(g.standard_normal((1, 2, 5, 6)))
+    w = g.standard_normal((3, 2, 3, 3)).astype(np.float32)
+    wb = U.bf16(w)
+    got = U.conv3x3(torch.tensor(x), w).numpy()
+    ref = np.zeros((1, 3, 5, 6))
+    for co in range(3):
+        for i in range(5):
+            for j in range(6):
+                s = 0.0
+                for ci in range(2):
+                    for m in range(3):
+                        for n in range(3):
+                            ii, jj = i + m - 1, j + n - 1
+                            if 0 <= ii < 5 and 0 <= jj < 6:
+                                s += x[0, ci, ii, jj] * wb[co, ci, m, n]
+                ref[0, co, i, j] = s
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+
+
+def test_transposed_conv_scatters_each_pixel_into_a_2x2_block():
+    g = np.random.default_rng(2)
+    x = U.bf16(g.standard_normal((1, 3, 2, 3)))
+    w = g.standard_normal((3, 2, 2, 2)).astype(np.float32)
+    wb = U.bf16(w)
+    got = U.up(torch.tensor(x), w).numpy()
+    ref = np.zeros((1, 2, 4, 6))
+    for co in range(2):
+        for i in range(2):
+            for j in range(3):
+                for di in range(2):
+                    for dj in range(2):
+                        ref[0, co, 2 * i + di, 2 * j + dj] = sum(x[0, ci, i, j] * wb[ci, co, di, dj] for ci in range(3))
+    np.testing.assert_array_equal(got, U.bf16(ref))
+
+
+def test_group_norm_and_pooling_follow_their_definitions():
+    g = np.random.default_rng(3)
+    y = g.standard_normal((2, 8, 4, 4)) * 3 + 1
+    gamma = g.standard_normal(8)
+    beta = g.standard_normal(8)
+    t = torch.tensor(y)
+    mean, var = U.group_stats(t, 4)
+    got = U.group_norm(t, mean, var, gamma, beta, 4).numpy()
+    for n in range(2):
+        for gi in range(4):
+            v = y[n, 2 * gi:2 * gi + 2]
+            m, s2 = v.mean(), ((v - v.mean()) ** 2).mean()
+            for k in range(2):
+                c = 2 * gi + k
+                want = (y[n, c] - m) / math.sqrt(s2 + U.EPS) * gamma[c] + beta[c]
+                np.testing.assert_allclose(got[n, c], want, rtol=1e-12, atol=1e-12)
+    p = U.down(t).numpy()
+    np.testing.assert_array_equal(p, y.reshape(2, 8, 2, 2, 2, 2).max(axis=(3, 5)))
+
+
+def test_gelu_is_the_tanh_form_and_close_to_the_erf_form():
+    for u in np.linspace(-6, 6, 61):
+        want = 0.5 * u * (1 + math.tanh(math.sqrt(2 / math.pi) * (u + 0.044715 * u**3)))
+        assert float(U.gelu(torch.tensor(u))) == pytest.approx(want, rel=1e-14, abs=1e-15)
+        assert abs(want - 0.5 * u * (1 + math.erf(u / math.sqrt(2)))) < 1e-3
+
+
+def test_mlp_basis_matches_a_loop_restatement():
+    W = U.init_weights(5)
+    tau = 0.37
+    w0, b0, w1, b1, w2, b2 = (W[k].astype(np.float64).tolist() for k in
+                              ("mlp_w0", "mlp_b0", "mlp_w1", "mlp_b1", "mlp_w2", "mlp_b2"))
+    h0 = [math.sin(w0[k][0] * tau + b0[k]) for k in range(U.FDIM)]
+    h1 = [math.sin(sum(w1[k][j] * h0[j] for j in range(U.FDIM)) + b1[k]) for k in range(U.FDIM)]
+    f = [sum(w2[k][j] * h1[j] for j in range(U.FDIM)) + b2[k] for k in range(U.FDIM)]
+    np.testing.assert_allclose(U.basis(W, tau), f, rtol=1e-12, atol=1e-12)
+    s = U.scales(W, tau)
+    assert [v.shape[0] for v in s] == list(U.CH)
+    np.testing.assert_allclose(s[2], W["proj3"].astype(np.float64) @ np.array(f), rtol=1e-12)
+
+
+def _net_input(seed=4, n=2, h=32, w=32):
+    g = np.random.default_rng(seed)
+    x = np.empty((n, 3, h, w))
+    x[:, 0] = np.tanh(g.standard_normal((n, h, w)))
+    x[:, 1] = 0.5 + 0.2 * g.standard_normal((n, h, w))
+    x[:, 2] = 0.25
+    return x
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_network_shapes_and_output_normalisation():
+    W = U.init_weights(0)
+    W["out_gamma"][:] = 1.0
+    W["out_beta"][:] = 0.0
+    taps = {}
+    y = U.forward(W, _net_input(), 0.25, taps)
+    assert y.shape == (2, 2, 32, 32)
+    assert taps["z4"].shape == (2, 256, 4, 4) and taps["d1"].shape == (2, 32, 32, 32)
+    # one group per output channel: zero mean and unit variance per sample and channel, up to the
+    # BF16 rounding of the stored pre-normalisation values
+    np.testing.assert_allclose(y.mean(axis=(2, 3)), 0.0, atol=2e-3)
+    np.testing.assert_allclose(y.var(axis=(2, 3)), 1.0, atol=5e-3)
+
+
+def test_network_invariants_of_the_normalisation_and_conditioning():
+    W = U.init_weights(0)
+    x = _net_input()
+    y = U.forward(W, x, 0.25)
+    # the first convolution is linear and GN follows it: an input scale of 2 (exact in BF16) drops out
+    x2 = x.copy()
+    x2[:, :2] *= 2.0
+    x2[:, 2] *= 2.0
+    assert _rel(U.forward(W, x2, 0.25), y) < 1e-2
+    # the bottleneck block sees only zc4 and normalises it: scaling W_4 changes nothing
+    W4 = dict(W, proj4=W["proj4"] * 2.0)
+    assert _rel(U.forward(W4, x, 0.25), y) < 1e-2
+    # the shallow skip zc1 is concatenated with d1 before the block: scaling W_1 changes the output
+    W1 = dict(W, proj1=W["proj1"] * 2.0)
+    assert _rel(U.forward(W1, x, 0.25), y) > 0.05
+    # the jump length enters through the basis: another tau gives another prediction
+    assert _rel(U.forward(W, x, 0.75), y) > 0.05
+
+
+def test_flop_count_matches_the_layer_shapes():
+    # 256^2: encoder 113 M + 3 x 604 M, decoder 1208 M + 3 x 2416 M, up-sampling 3 x 268 M, output 75.5 M
+    want = 113.2e6 + 3 * 604.0e6 + 1208.0e6 + 3 * 2416.0e6 + 3 * 268.4e6 + 75.5e6
+    assert U.flops_per_sample(256, 256) == pytest.approx(want, rel=1e-3)
