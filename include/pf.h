@@ -254,6 +254,36 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch,
 const char* pf_adjoint_last_error(void);
 
 /* Text for an error code, and the last error message of the calling thread. */
+/*
+ * Tensor-core convolution primitives of the U-Net surrogate ("U-Net with temporal
+ * conditioning", Methods: the convolution of each conv_block and the transposed
+ * convolution of the up-sampling path), as implicit GEMMs on tcgen05 with BF16
+ * operands and FP32 accumulation in tensor memory.
+ *
+ * pf_conv3x3_bf16: out[n][y][x][out_coff + co] = BF16( sum_{ky,kx,ci} in[n][y+ky-1][x+kx-1][ci]
+ *   * wgt[3 ky + kx][co][ci] ), zero outside the image (the paper's conv with 'same'
+ *   zero padding, no bias).  in: device BF16 NHWC [n][h][w][cin]; wgt: device BF16
+ *   [9][cout][cin]; out: device BF16 NHWC buffer of out_cstride channels per pixel,
+ *   of which [out_coff, out_coff + cout) are written.  partials (device, may be NULL):
+ *   FP32 [n][groups][h*w/128][2], the sum and the sum of squares of the FP32
+ *   results of each 128-pixel tile over each of `groups` equal channel groups (the
+ *   group-normalisation statistics).
+ * pf_tconv2x2_bf16: out[n][2y+dy][2x+dx][out_coff + co] = BF16( sum_ci in[n][y][x][ci]
+ *   * wgt[(2 dy + dx) cout + co][ci] ) (stride-2 2x2 transposed convolution, no bias);
+ *   out is n x 2h x 2w pixels.
+ * Shapes: cin % 32 == 0 (<= 1024), cout % 16 == 0 (conv: <= 256, divisible by
+ * groups <= 8), h*w % 128 == 0 and w a multiple or a divisor of 128; pointers
+ * 16-byte aligned; out_coff and out_cstride multiples of 8.  err_dev: device int;
+ * bit 1 is set if a bounded pipeline wait ran out (the kernel then stops early).
+ * Asynchronous on `stream`; PF_ERR_ARG / PF_ERR_LAYOUT / PF_ERR_CUDA on errors, with
+ * the text in pf_unet_last_error().  Nothing is allocated.
+ */
+int pf_conv3x3_bf16(const void* in, int n, int h, int w, int cin, const void* wgt, int cout, void* out,
+                    int out_cstride, int out_coff, int groups, float* partials, int* err_dev, void* stream);
+int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* wgt, int cout, void* out,
+                     int out_cstride, int out_coff, int* err_dev, void* stream);
+const char* pf_unet_last_error(void);
+
 const char* pf_strerror(int code);
 const char* pf_last_error(void);
 

@@ -70,7 +70,7 @@ int mob_kind_of(const pf_params& p)
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void* f = nullptr;

@@ -90,6 +90,13 @@ def _load():
                              C.POINTER(C.c_double), vp, vp, vp, vp, sz, vp]
     L.pf_adjoint.restype = C.c_int
     L.pf_adjoint_last_error.argtypes, L.pf_adjoint_last_error.restype = [], C.c_char_p
+    L.pf_conv3x3_bf16.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int,
+                                  C.c_int, vp, vp, vp]
+    L.pf_conv3x3_bf16.restype = C.c_int
+    L.pf_tconv2x2_bf16.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int,
+                                   vp, vp]
+    L.pf_tconv2x2_bf16.restype = C.c_int
+    L.pf_unet_last_error.argtypes, L.pf_unet_last_error.restype = [], C.c_char_p
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
     L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
     return L
@@ -450,3 +457,58 @@ def make_run_function():
             return dv, dm, dk, res["phi0"], res["c0"], res["rho0"], None, None, None, None
 
     return PFRun
+
+
+# ---------------------------------------------------------------------------------------------
+# U-Net surrogate: tensor-core convolution primitives (BF16 NHWC tensors on the device)
+
+def _ucheck(rc: int) -> int:
+    if rc != PF_OK:
+        raise PFError(rc, f"{strerror(rc)}: {lib.pf_unet_last_error().decode()}")
+    return rc
+
+
+def conv_weight_layout(w):
+    """[Cout, Cin, 3, 3] (PyTorch convention) -> BF16 [9][Cout][Cin] on the device (tap = 3 ky + kx)."""
+    import torch
+    t = torch.as_tensor(np.asarray(w, dtype=np.float32))
+    return t.permute(2, 3, 0, 1).reshape(9, t.shape[0], t.shape[1]).contiguous().to("cuda", torch.bfloat16)
+
+
+def tconv_weight_layout(w):
+    """[Cin, Cout, 2, 2] (PyTorch convention) -> BF16 [4 Cout][Cin] on the device (row (2 dy + dx) Cout + co)."""
+    import torch
+    t = torch.as_tensor(np.asarray(w, dtype=np.float32))
+    return t.permute(2, 3, 1, 0).reshape(4 * t.shape[1], t.shape[0]).contiguous().to("cuda", torch.bfloat16)
+
+
+def conv3x3_bf16(x, w_dev, groups: int, out=None, out_coff: int = 0, partials=None, err=None, stream=None):
+    """x: BF16 NHWC [n, h, w, cin] on the device; w_dev from conv_weight_layout.  Returns (out, partials)."""
+    import torch
+    n, h, wd, cin = x.shape
+    cout = w_dev.shape[1]
+    if out is None:
+        out = torch.empty((n, h, wd, cout), dtype=torch.bfloat16, device=x.device)
+    if partials is None:
+        partials = torch.zeros((n, groups, h * wd // 128, 2), dtype=torch.float32, device=x.device)
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _ucheck(lib.pf_conv3x3_bf16(x.data_ptr(), n, h, wd, cin, w_dev.data_ptr(), cout, out.data_ptr(), out.shape[3],
+                                out_coff, groups, partials.data_ptr(), err.data_ptr(), s))
+    return out, partials
+
+
+def tconv2x2_bf16(x, w_dev, out=None, out_coff: int = 0, err=None, stream=None):
+    """x: BF16 NHWC [n, h, w, cin]; w_dev from tconv_weight_layout.  Returns out [n, 2h, 2w, cout]."""
+    import torch
+    n, h, wd, cin = x.shape
+    cout = w_dev.shape[0] // 4
+    if out is None:
+        out = torch.empty((n, 2 * h, 2 * wd, cout), dtype=torch.bfloat16, device=x.device)
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _ucheck(lib.pf_tconv2x2_bf16(x.data_ptr(), n, h, wd, cin, w_dev.data_ptr(), cout, out.data_ptr(), out.shape[3],
+                                 out_coff, err.data_ptr(), s))
+    return out

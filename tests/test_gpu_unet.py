@@ -1,0 +1,110 @@
+"""Tensor-core U-Net kernels against the FP64 reference U-Net (oracle/unet_ref.py).
+
+The convolutions take BF16 operands, whose products are exact, and sum them in FP32
+in tensor memory. Against the FP64 sum of the same BF16 values, each stored BF16
+result therefore differs by at most
+- one BF16 unit in the last place (the two sums may round to neighbouring values),
+- plus the FP32 accumulation error.
+
+The accumulation error is bounded by (K/4) 2^-24 sum|x w|. The tensor core rounds
+to FP32 at most once per 4 products (K = taps x input channels), and cancellation
+makes sum|x w| the relevant scale near zero. A missing or misplaced tap would
+change a result by about sum|x w| / 9, thousands of times this bound.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet_ref as U
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pf(cuda_ok):
+    from paper_2312_05410_gb300 import build as B
+    B.build()
+    from paper_2312_05410_gb300 import pf as mod
+    return mod
+
+
+def ulp_bf16(x):
+    a = np.abs(np.asarray(x, dtype=np.float64))
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -126)))
+    return 2.0 ** (e - 7)
+
+
+def bound(ref, absdot, k):
+    return ulp_bf16(ref) + (k / 4.0) * 2.0 ** -24 * absdot
+
+
+def nhwc_dev(x_nchw):
+    return torch.as_tensor(np.ascontiguousarray(np.transpose(x_nchw, (0, 2, 3, 1))), dtype=torch.float32).to(
+        "cuda", torch.bfloat16)
+
+
+def to_nchw(t):
+    return np.transpose(t.float().cpu().numpy(), (0, 3, 1, 2)).astype(np.float64)
+
+
+@pytest.mark.parametrize("n,h,w,cin,cout", [(2, 32, 32, 64, 128), (1, 16, 64, 32, 64), (1, 8, 256, 128, 32),
+                                            (3, 8, 16, 256, 256), (1, 4, 32, 96, 48)])
+def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
+    g = np.random.default_rng(n * 1000 + cin + cout)
+    x = U.bf16(g.standard_normal((n, cin, h, w)))
+    wt = (g.standard_normal((cout, cin, 3, 3)) / np.sqrt(9 * cin)).astype(np.float32)
+    groups = 8 if cout % 8 == 0 else 1
+    out, part = pf.conv3x3_bf16(nhwc_dev(x), pf.conv_weight_layout(wt), groups)
+    torch.cuda.synchronize()
+    got = to_nchw(out)
+    ref = U.conv3x3(torch.tensor(x), wt).numpy()
+    absdot = U.conv3x3(torch.tensor(np.abs(x)), np.abs(U.bf16(wt))).numpy()
+    tol = bound(ref, absdot, 9 * cin)
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+    # group sums and sums of squares of the FP32 results, per 128-pixel tile
+    p = part.cpu().numpy().astype(np.float64)
+    cg = cout // groups
+    tot = p.sum(axis=2)
+    for i in range(n):
+        for gi in range(groups):
+            v = ref[i, gi * cg:(gi + 1) * cg]
+            np.testing.assert_allclose(tot[i, gi, 0], v.sum(), rtol=1e-4, atol=1e-3)
+            np.testing.assert_allclose(tot[i, gi, 1], (v * v).sum(), rtol=1e-4)
+
+
+def test_conv3x3_writes_only_its_channel_slice(pf):
+    g = np.random.default_rng(9)
+    x = U.bf16(g.standard_normal((1, 64, 16, 16)))
+    wt = (g.standard_normal((32, 64, 3, 3)) / 24).astype(np.float32)
+    buf = torch.full((1, 16, 16, 96), 7.0, dtype=torch.bfloat16, device="cuda")
+    pf.conv3x3_bf16(nhwc_dev(x), pf.conv_weight_layout(wt), 8, out=buf, out_coff=32)
+    torch.cuda.synchronize()
+    b = buf.float().cpu().numpy()
+    assert np.all(b[..., :32] == 7.0) and np.all(b[..., 64:] == 7.0)
+    ref = U.conv3x3(torch.tensor(x), wt).numpy()
+    absdot = U.conv3x3(torch.tensor(np.abs(x)), np.abs(U.bf16(wt))).numpy()
+    got = np.transpose(b[..., 32:64], (0, 3, 1, 2))
+    assert np.all(np.abs(got - ref) <= bound(ref, absdot, 9 * 64))
+
+
+@pytest.mark.parametrize("n,h,w,cin,cout", [(2, 16, 16, 256, 128), (1, 32, 32, 128, 64), (2, 64, 64, 64, 32)])
+def test_transposed_conv_within_one_bf16_ulp(pf, n, h, w, cin, cout):
+    g = np.random.default_rng(h + cin)
+    x = U.bf16(g.standard_normal((n, cin, h, w)))
+    wt = (g.standard_normal((cin, cout, 2, 2)) / np.sqrt(cin)).astype(np.float32)
+    out = pf.tconv2x2_bf16(nhwc_dev(x), pf.tconv_weight_layout(wt))
+    torch.cuda.synchronize()
+    got = to_nchw(out)
+    import torch.nn.functional as F
+    ref = F.conv_transpose2d(torch.tensor(x), torch.tensor(U.bf16(wt)), stride=2).numpy()
+    absdot = F.conv_transpose2d(torch.tensor(np.abs(x)), torch.tensor(np.abs(U.bf16(wt))), stride=2).numpy()
+    tol = bound(ref, absdot, cin)
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+
+
+def test_unsupported_shapes_are_rejected(pf):
+    x = torch.zeros((1, 10, 10, 64), dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros((9, 32, 64), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(pf.PFError) as e:
+        pf.conv3x3_bf16(x, w, 8)
+    assert e.value.code == pf.PF_ERR_ARG
