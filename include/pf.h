@@ -282,6 +282,55 @@ int pf_conv3x3_bf16(const void* in, int n, int h, int w, int cin, const void* wg
                     int out_cstride, int out_coff, int groups, float* partials, int* err_dev, void* stream);
 int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* wgt, int cout, void* out,
                      int out_cstride, int out_coff, int* err_dev, void* stream);
+/*
+ * The time-conditioned U-Net surrogate and its jump ("U-Net with temporal
+ * conditioning", Methods; the hybrid solver of Results alternates DNS stretches
+ * with such jumps).  For each of `batch` runs it maps (phi, c) at time t to a
+ * prediction at t + dt.  Structure:
+ *   - input planes (phi, c, tau), with tau = dt / dt_ref;
+ *   - encoder z1 = block(x), zp = block(down(z_{p-1})), with block = GELU(GN(conv3x3));
+ *   - conditioning zc_p = z_p * (W_p f(tau)), where f is the sin MLP;
+ *   - decoder d3 = up(block(zc4)), d2 = up(block(zc3 ++ d3)), d1 = up(block(zc2 ++ d2));
+ *   - output (phi, c) = GN(conv3x3(block(zc1 ++ d1))).
+ * Channels are 32-64-128-256, with 8 groups in the hidden normalisations and one
+ * group per output channel.  Weights and activations are stored as BF16 and
+ * accumulated in FP32; the 3x3 and transposed convolutions of levels 2-4 and of
+ * the decoder run on the tensor cores (pf_conv3x3_bf16 / pf_tconv2x2_bf16).
+ *
+ * pf_unet_workspace_size: bytes of caller-owned device workspace (weights in
+ *   device layouts, all activations, statistics, tables); 0 if the shape is
+ *   unsupported.  Supported shapes: sides >= 128 and multiples of 8, nx/8 dividing
+ *   or a multiple of 128, (nx/8)(ny/8) a multiple of 128 (e.g. 128^2, 256^2, 512^2).
+ * pf_unet_init: weights = 40 host FP32 arrays, in PyTorch layouts and this order:
+ *   0-5   mlp_w0 [128][1], mlp_b0 [128], mlp_w1 [128][128], mlp_b1, mlp_w2 [128][128], mlp_b2
+ *   6-9   proj1..proj4 [C_p][128] (C = 32, 64, 128, 256)
+ *   10-13 enc1 [32][3][3][3], enc2 [64][32][3][3], enc3 [128][64][3][3], enc4 [256][128][3][3]
+ *   14-17 dec4 [256][256][3][3], dec3 [128][256][3][3], dec2 [64][128][3][3], dec1 [32][64][3][3]
+ *   18-20 up4 [256][128][2][2], up3 [128][64][2][2], up2 [64][32][2][2]  ([Cin][Cout][dy][dx])
+ *   21    out [2][32][3][3]
+ *   22-39 (gamma, beta) of enc1..enc4, dec4..dec1, out.
+ *   They are rounded to BF16, except the MLP, projections (FP64) and GN affine
+ *   parameters (FP32), and copied into the workspace (synchronises once).
+ *   work: 256-byte aligned.
+ * pf_unet_jump: replaces (phi[i], c[i]) of runs i < n (n == batch; device FP32
+ *   fields ny x nx with row pitch `pitch` floats) by the prediction for jump
+ *   length tau.  It sets rho[i] = rho_top (1 - phi) / 2, the initial-state vapor
+ *   profile; the surrogate does not predict rho.  Asynchronous on the handle's
+ *   stream, about 30 kernel launches.
+ * pf_unet_sync: synchronise; PF_ERR_TIMEOUT if a tensor-core pipeline wait ran out.
+ * pf_unet_buffer: device pointer and channel count of activation buffer `which`
+ *   (0-15: pre1, cat1, p1, pre2, cat2, p2, pre3, cat3, p3, pre4, zc4, h4, h3, h2,
+ *   h1, pre_out; NHWC BF16 at level resolution), for inspection.
+ */
+typedef struct pf_unet pf_unet;
+size_t pf_unet_workspace_size(int batch, int nx, int ny);
+int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, int ny, void* work, size_t work_bytes,
+                 void* stream, pf_unet** out);
+int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau,
+                 double rho_top);
+int pf_unet_sync(pf_unet* u);
+int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels);
+int pf_unet_destroy(pf_unet* u);
 const char* pf_unet_last_error(void);
 
 const char* pf_strerror(int code);

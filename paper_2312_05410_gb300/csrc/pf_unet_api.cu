@@ -2,12 +2,17 @@
 // convolution primitives, and (below) the time-conditioned U-Net jump of the
 // hybrid DNS / U-Net solver ("U-Net with temporal conditioning", Methods;
 // "Hybrid" in Results: the surrogate leaps over a stretch of DNS steps).
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
+#include <new>
 #include <string>
+#include <vector>
 
 #include "pf.h"
 #include "pf_unet_internal.h"
+#include "pf_unet_net.h"
 
 namespace {
 
@@ -62,6 +67,129 @@ int conv_common(int mode, const void* in, int n, int h, int w, int cin, const vo
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------------------------
+// The network: weights, activations and the jump.
+
+namespace {
+
+constexpr int NW = 40;  // weight arrays, in the order documented in pf.h
+const int CH[4] = {32, 64, 128, 256};
+
+// host BF16 rounding (nearest, ties to even) from the format definition
+uint16_t host_bf16(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float host_rbf(float f)
+{
+    const uint32_t u = (uint32_t)host_bf16(f) << 16;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct UnetLayout {
+    size_t mlp, proj, win, wout, wc[7], wt[3], gb[9][2];
+    size_t act[16];  // see ACT_* below
+    size_t partials, stats, scales, err, ptrs, total;
+};
+enum { A_PRE1, A_CAT1, A_P1, A_PRE2, A_CAT2, A_P2, A_PRE3, A_CAT3, A_P3, A_PRE4, A_ZC4, A_H4, A_H3, A_H2, A_H1, A_PREO };
+
+bool shape_ok(int n, int h, int w)
+{
+    if (n < 1 || n > 4096 || h < 128 || w < 128 || h > 8192 || w > 8192 || h % 8 || w % 8) return false;
+    const int w8 = w / 8;
+    if ((w8 % 128) && (128 % w8)) return false;
+    return ((long long)(h / 8) * w8) % 128 == 0;
+}
+
+UnetLayout unet_layout(int n, int h, int w)
+{
+    UnetLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = al256(off + bytes);
+        return o;
+    };
+    L.mlp = take(sizeof(double) * (3 * 128 + 2 * 128 * 128 + 128));
+    L.proj = take(sizeof(double) * 480 * 128);
+    L.win = take(sizeof(float) * 27 * 32);
+    L.wout = take(sizeof(float) * 9 * 32 * 2);
+    const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
+    for (int k = 0; k < 7; ++k) L.wc[k] = take(2 * 9 * (size_t)conv_io[k][0] * conv_io[k][1]);
+    const int tc_io[3][2] = {{256, 128}, {128, 64}, {64, 32}};
+    for (int k = 0; k < 3; ++k) L.wt[k] = take(2 * 4 * (size_t)tc_io[k][0] * tc_io[k][1]);
+    const int gbc[9] = {32, 64, 128, 256, 256, 128, 64, 32, 2};
+    for (int k = 0; k < 9; ++k)
+        for (int q = 0; q < 2; ++q) L.gb[k][q] = take(sizeof(float) * gbc[k]);
+    const size_t P0 = (size_t)n * h * w, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+    const size_t elems[16] = {P0 * 32, P0 * 64, P1 * 32, P1 * 64, P1 * 128, P2 * 64, P2 * 128, P2 * 256,
+                              P3 * 128, P3 * 256, P3 * 256, P3 * 256, P2 * 128, P1 * 64, P0 * 32, P0 * 2};
+    for (int k = 0; k < 16; ++k) L.act[k] = take(2 * elems[k]);
+    L.partials = take(sizeof(float) * (size_t)n * 8 * (h * (size_t)w / 128) * 2);
+    L.stats = take(sizeof(float) * (size_t)n * 8 * 2);
+    L.scales = take(sizeof(float) * 480);
+    L.err = take(sizeof(int));
+    L.ptrs = take(sizeof(float*) * 3 * (size_t)n);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct pf_unet {
+    int n, h, w;
+    char* base;
+    UnetLayout L;
+    cudaStream_t stream;
+    std::vector<float*> ptrs;  // host copy of the run pointer table (phi[n], c[n], rho[n])
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+namespace {
+
+int upload(pf_unet* u, size_t off, const void* src, size_t bytes)
+{
+    cudaError_t e = cudaMemcpyAsync(u->base + off, src, bytes, cudaMemcpyHostToDevice, u->stream);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "weight upload: %s", cudaGetErrorString(e));
+    return PF_OK;
+}
+
+int conv_tc(pf_unet* u, int mode, const uint16_t* in, int h, int w, int cin, const uint16_t* wgt, int cout,
+            uint16_t* out, int cstride, int coff, bool stats_too)
+{
+    pf::ConvArgs a = {};
+    a.n = u->n;
+    a.h = h;
+    a.w = w;
+    a.cin = cin;
+    a.cout = cout;
+    a.groups = pf::GN_MAX_GROUPS;
+    a.out = out;
+    a.out_cstride = cstride;
+    a.out_coff = coff;
+    a.partials = stats_too ? u->at<float>(u->L.partials) : nullptr;
+    a.err = u->at<int>(u->L.err);
+    a.wait_cap = 1 << 22;
+    cudaError_t e = pf::launch_umma_conv(mode, in, wgt, a, u->stream);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "tensor-core convolution: %s", cudaGetErrorString(e));
+    if (!stats_too) return PF_OK;
+    e = pf::launch_gn_stats(u->at<float>(u->L.partials), u->n, pf::GN_MAX_GROUPS, h * w / 128,
+                            (double)(cout / pf::GN_MAX_GROUPS) * h * w, u->at<float>(u->L.stats), u->stream);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "group statistics: %s", cudaGetErrorString(e));
+    return PF_OK;
+}
+
+}  // namespace
 extern "C" {
 
 int pf_conv3x3_bf16(const void* in, int n, int h, int w, int cin, const void* wgt, int cout, void* out,
@@ -76,6 +204,192 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
 {
     return conv_common(pf::TCONV, in, n, h, w, cin, wgt, cout, out, out_cstride, out_coff, 1, nullptr, err_dev,
                        stream);
+}
+
+size_t pf_unet_workspace_size(int batch, int nx, int ny)
+{
+    if (!shape_ok(batch, ny, nx)) return 0;
+    return unet_layout(batch, ny, nx).total;
+}
+
+int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, int ny, void* work, size_t work_bytes,
+                 void* stream, pf_unet** out)
+{
+    if (!out) return ufail(PF_ERR_ARG, "null output handle pointer");
+    *out = nullptr;
+    if (!weights || nweights != NW) return ufail(PF_ERR_ARG, "expected %d weight arrays", NW);
+    for (int k = 0; k < NW; ++k)
+        if (!weights[k]) return ufail(PF_ERR_ARG, "weight array %d is null", k);
+    if (!shape_ok(batch, ny, nx))
+        return ufail(PF_ERR_ARG, "batch %d of %d x %d unsupported (sides >= 128, multiples of 8, nx/8 dividing "
+                     "or a multiple of 128, nx*ny %% 8192 == 0)", batch, nx, ny);
+    if (!work || reinterpret_cast<uintptr_t>(work) % 256) return ufail(PF_ERR_LAYOUT, "workspace must be 256-byte aligned");
+    const UnetLayout L = unet_layout(batch, ny, nx);
+    if (work_bytes < L.total) return ufail(PF_ERR_LAYOUT, "workspace of %zu bytes, %zu needed", work_bytes, L.total);
+    pf_unet* u = new (std::nothrow) pf_unet();
+    if (!u) return ufail(PF_ERR_ARG, "out of host memory");
+    u->n = batch;
+    u->h = ny;
+    u->w = nx;
+    u->base = static_cast<char*>(work);
+    u->L = L;
+    u->stream = static_cast<cudaStream_t>(stream);
+    u->ptrs.assign(3 * (size_t)batch, nullptr);
+    // ---- host-side conversion into the device layouts (once)
+    std::vector<double> mlp;
+    for (int k = 0; k < 6; ++k) {
+        const size_t cnt = (k == 2 || k == 4) ? 128 * 128 : 128;
+        mlp.insert(mlp.end(), weights[k], weights[k] + cnt);
+    }
+    std::vector<double> proj;
+    for (int p = 0; p < 4; ++p) proj.insert(proj.end(), weights[6 + p], weights[6 + p] + (size_t)CH[p] * 128);
+    // first conv [32][3][3][3] -> [(ky,kx,ci)][co], BF16 values
+    std::vector<float> win(27 * 32);
+    for (int co = 0; co < 32; ++co)
+        for (int ci = 0; ci < 3; ++ci)
+            for (int t = 0; t < 9; ++t) win[(t * 3 + ci) * 32 + co] = host_rbf(weights[10][((co * 3 + ci) * 9) + t]);
+    // last conv [2][32][3][3] -> [tap][ci][co]
+    std::vector<float> wout(9 * 32 * 2);
+    for (int co = 0; co < 2; ++co)
+        for (int ci = 0; ci < 32; ++ci)
+            for (int t = 0; t < 9; ++t) wout[(t * 32 + ci) * 2 + co] = host_rbf(weights[21][((co * 32 + ci) * 9) + t]);
+    // tensor-core convs [Cout][Cin][3][3] -> [tap][Cout][Cin] BF16: enc2..4 (11..13), dec4..1 (14..17)
+    const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
+    const int conv_src[7] = {11, 12, 13, 14, 15, 16, 17};
+    int rc = PF_OK;
+    std::vector<std::vector<uint16_t>> keep;
+    for (int k = 0; k < 7 && rc == PF_OK; ++k) {
+        const int ci_n = conv_io[k][0], co_n = conv_io[k][1];
+        std::vector<uint16_t> v((size_t)9 * co_n * ci_n);
+        for (int co = 0; co < co_n; ++co)
+            for (int ci = 0; ci < ci_n; ++ci)
+                for (int t = 0; t < 9; ++t)
+                    v[((size_t)t * co_n + co) * ci_n + ci] = host_bf16(weights[conv_src[k]][((size_t)co * ci_n + ci) * 9 + t]);
+        keep.push_back(std::move(v));
+        rc = upload(u, L.wc[k], keep.back().data(), keep.back().size() * 2);
+    }
+    // transposed convs [Cin][Cout][2][2] -> [(2 dy + dx) Cout + co][Cin]: up4, up3, up2 (18..20)
+    const int tc_io[3][2] = {{256, 128}, {128, 64}, {64, 32}};
+    for (int k = 0; k < 3 && rc == PF_OK; ++k) {
+        const int ci_n = tc_io[k][0], co_n = tc_io[k][1];
+        std::vector<uint16_t> v((size_t)4 * co_n * ci_n);
+        for (int ci = 0; ci < ci_n; ++ci)
+            for (int co = 0; co < co_n; ++co)
+                for (int s = 0; s < 4; ++s)
+                    v[((size_t)s * co_n + co) * ci_n + ci] = host_bf16(weights[18 + k][((size_t)ci * co_n + co) * 4 + s]);
+        keep.push_back(std::move(v));
+        rc = upload(u, L.wt[k], keep.back().data(), keep.back().size() * 2);
+    }
+    const int gbc[9] = {32, 64, 128, 256, 256, 128, 64, 32, 2};
+    if (rc == PF_OK) rc = upload(u, L.mlp, mlp.data(), mlp.size() * sizeof(double));
+    if (rc == PF_OK) rc = upload(u, L.proj, proj.data(), proj.size() * sizeof(double));
+    if (rc == PF_OK) rc = upload(u, L.win, win.data(), win.size() * sizeof(float));
+    if (rc == PF_OK) rc = upload(u, L.wout, wout.data(), wout.size() * sizeof(float));
+    for (int k = 0; k < 9 && rc == PF_OK; ++k)
+        for (int q = 0; q < 2 && rc == PF_OK; ++q) rc = upload(u, L.gb[k][q], weights[22 + 2 * k + q], gbc[k] * sizeof(float));
+    if (rc == PF_OK) {
+        cudaError_t e = cudaMemsetAsync(u->base + L.err, 0, sizeof(int), u->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);  // host staging vectors go out of scope
+        if (e != cudaSuccess) rc = ufail(PF_ERR_CUDA, "U-Net init: %s", cudaGetErrorString(e));
+    }
+    if (rc != PF_OK) {
+        delete u;
+        return rc;
+    }
+    *out = u;
+    return PF_OK;
+}
+
+int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau,
+                 double rho_top)
+{
+    if (!u || !phi || !c || !rho) return ufail(PF_ERR_ARG, "null pointer");
+    if (n != u->n) return ufail(PF_ERR_ARG, "batch %d, the handle was built for %d", n, u->n);
+    if (pitch < u->w) return ufail(PF_ERR_LAYOUT, "pitch %d < nx %d", pitch, u->w);
+    if (!std::isfinite(tau)) return ufail(PF_ERR_ARG, "jump length is not finite");
+    for (int i = 0; i < n; ++i) {
+        if (!phi[i] || !c[i] || !rho[i]) return ufail(PF_ERR_ARG, "run %d: null field", i);
+        u->ptrs[i] = phi[i];
+        u->ptrs[n + i] = c[i];
+        u->ptrs[2 * n + i] = rho[i];
+    }
+    cudaStream_t s = u->stream;
+    cudaError_t e = cudaMemcpyAsync(u->base + u->L.ptrs, u->ptrs.data(), sizeof(float*) * 3 * n,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "pointer table: %s", cudaGetErrorString(e));
+    float** dp = u->at<float*>(u->L.ptrs);
+    const UnetLayout& L = u->L;
+    const int H = u->h, W = u->w;
+    auto act = [&](int k) { return u->at<uint16_t>(L.act[k]); };
+    float* part = u->at<float>(L.partials);
+    float* stats = u->at<float>(L.stats);
+    float* sc = u->at<float>(L.scales);
+    auto gam = [&](int k) { return u->at<float>(L.gb[k][0]); };
+    auto bet = [&](int k) { return u->at<float>(L.gb[k][1]); };
+    const int G = pf::GN_MAX_GROUPS;
+    int rc = PF_OK;
+    auto ck = [&](cudaError_t ce, const char* what) {
+        if (rc == PF_OK && ce != cudaSuccess) rc = ufail(PF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ce));
+    };
+    // conditioning factors of the four levels
+    ck(pf::launch_cond(u->at<double>(L.mlp), u->at<double>(L.proj), tau, sc, 480, s), "conditioning");
+    // ---- encoder
+    ck(pf::launch_in_conv(dp, dp + n, pitch, n, H, W, (float)tau, u->at<float>(L.win), act(A_PRE1), part, s), "input conv");
+    ck(pf::launch_gn_stats(part, n, G, H * W / 128, 4.0 * H * W, stats, s), "statistics");
+    ck(pf::launch_gn_enc(act(A_PRE1), n, H, W, 32, G, stats, gam(0), bet(0), sc, act(A_CAT1), 64, act(A_P1), s), "level 1");
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P1), H / 2, W / 2, 32, u->at<uint16_t>(L.wc[0]), 64, act(A_PRE2), 64, 0, true);
+    ck(pf::launch_gn_enc(act(A_PRE2), n, H / 2, W / 2, 64, G, stats, gam(1), bet(1), sc + 32, act(A_CAT2), 128, act(A_P2), s), "level 2");
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P2), H / 4, W / 4, 64, u->at<uint16_t>(L.wc[1]), 128, act(A_PRE3), 128, 0, true);
+    ck(pf::launch_gn_enc(act(A_PRE3), n, H / 4, W / 4, 128, G, stats, gam(2), bet(2), sc + 96, act(A_CAT3), 256, act(A_P3), s), "level 3");
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P3), H / 8, W / 8, 128, u->at<uint16_t>(L.wc[2]), 256, act(A_PRE4), 256, 0, true);
+    ck(pf::launch_gn_enc(act(A_PRE4), n, H / 8, W / 8, 256, G, stats, gam(3), bet(3), sc + 224, act(A_ZC4), 256, nullptr, s), "level 4");
+    // ---- decoder
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_ZC4), H / 8, W / 8, 256, u->at<uint16_t>(L.wc[3]), 256, act(A_PRE4), 256, 0, true);
+    ck(pf::launch_gn_dec(act(A_PRE4), n, H / 8, W / 8, 256, G, stats, gam(4), bet(4), act(A_H4), s), "decoder 4");
+    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H4), H / 8, W / 8, 256, u->at<uint16_t>(L.wt[0]), 128, act(A_CAT3), 256, 128, false);
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT3), H / 4, W / 4, 256, u->at<uint16_t>(L.wc[4]), 128, act(A_PRE3), 128, 0, true);
+    ck(pf::launch_gn_dec(act(A_PRE3), n, H / 4, W / 4, 128, G, stats, gam(5), bet(5), act(A_H3), s), "decoder 3");
+    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H3), H / 4, W / 4, 128, u->at<uint16_t>(L.wt[1]), 64, act(A_CAT2), 128, 64, false);
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT2), H / 2, W / 2, 128, u->at<uint16_t>(L.wc[5]), 64, act(A_PRE2), 64, 0, true);
+    ck(pf::launch_gn_dec(act(A_PRE2), n, H / 2, W / 2, 64, G, stats, gam(6), bet(6), act(A_H2), s), "decoder 2");
+    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H2), H / 2, W / 2, 64, u->at<uint16_t>(L.wt[2]), 32, act(A_CAT1), 64, 32, false);
+    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT1), H, W, 64, u->at<uint16_t>(L.wc[6]), 32, act(A_PRE1), 32, 0, true);
+    ck(pf::launch_gn_dec(act(A_PRE1), n, H, W, 32, G, stats, gam(7), bet(7), act(A_H1), s), "decoder 1");
+    // ---- output: conv 32 -> 2, GN per channel, into the DNS fields
+    ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), act(A_PREO), part, s), "output conv");
+    ck(pf::launch_gn_stats(part, n, 2, H * W / 128, (double)H * W, stats, s), "output statistics");
+    ck(pf::launch_gn_out(act(A_PREO), n, H, W, stats, gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch, (float)rho_top, s),
+       "output");
+    return rc;
+}
+
+int pf_unet_sync(pf_unet* u)
+{
+    if (!u) return ufail(PF_ERR_ARG, "null handle");
+    int err = 0;
+    cudaError_t e = cudaStreamSynchronize(u->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, u->base + u->L.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "U-Net sync: %s", cudaGetErrorString(e));
+    if (err & pf::UNET_ERR_TIMEOUT) return ufail(PF_ERR_TIMEOUT, "a bounded tensor-core pipeline wait ran out");
+    return PF_OK;
+}
+
+int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels)
+{
+    if (!u || !ptr || !channels || which < 0 || which > 15) return ufail(PF_ERR_ARG, "bad buffer query");
+    const int ch[16] = {32, 64, 32, 64, 128, 64, 128, 256, 128, 256, 256, 256, 128, 64, 32, 2};
+    *ptr = u->base + u->L.act[which];
+    *channels = ch[which];
+    return PF_OK;
+}
+
+int pf_unet_destroy(pf_unet* u)
+{
+    if (!u) return PF_OK;
+    cudaError_t e = cudaStreamSynchronize(u->stream);
+    delete u;
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    return PF_OK;
 }
 
 const char* pf_unet_last_error(void) { return g_unet_error.c_str(); }

@@ -1,0 +1,435 @@
+// CUDA-core kernels of the time-conditioned U-Net ("U-Net with temporal
+// conditioning", Methods), around the tensor-core convolutions of
+// pf_unet_conv.cu:
+//
+//   cond_kernel     the MLP basis f(dt) = w2 sin(w1 sin(w0 dt + b0) + b1) + b2 and the
+//                   per-level conditioning factors W_p f(dt), in FP64, stored as BF16 values
+//   in_conv_kernel  the first 3x3 convolution (3 -> 32 channels) straight from the DNS
+//                   fields (phi, c and a plane holding dt / dt_ref), with its group sums
+//   out_conv_kernel the last 3x3 convolution (32 -> 2), with its per-channel sums
+//   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums, FP64, fixed order
+//   gn_apply_*      GN + GELU (+ conditioning product, + 2x2 max pooling) on stored BF16
+//                   values; the last one writes the predicted phi and c into the DNS fields
+//
+// Storage follows the precision model of the reference: every stored activation is BF16
+// (round to nearest even), sums are FP32 (FP64 for the statistics), products of BF16 values
+// are exact in FP32.
+#include <cstdint>
+
+#include "pf_unet_internal.h"
+#include "pf_unet_net.h"
+
+namespace pf {
+namespace {
+
+constexpr int TPB = 128;  // one 128-pixel tile per block in the tile-shaped kernels
+
+__device__ __forceinline__ float bf(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+__device__ __forceinline__ uint16_t to_bf(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+__device__ __forceinline__ float rbf(float f) { return bf(to_bf(f)); }
+
+// the paper's tanh form of GELU
+__device__ __forceinline__ float gelu(float u)
+{
+    return 0.5f * u * (1.0f + tanhf(0.7978845608028654f * (u + 0.044715f * u * u * u)));
+}
+
+// Sum of `v` over a 128-thread block in a fixed order (warp butterfly, then warps 0..3).
+__device__ __forceinline__ float block_sum128(float v, float* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    return red[0] + red[1] + red[2] + red[3];
+}
+
+__global__ void cond_kernel(const double* __restrict__ mlp, const double* __restrict__ proj, double tau,
+                            float* __restrict__ scales, int nscales)
+{
+    // mlp: w0[128], b0[128], w1[128][128], b1[128], w2[128][128], b2[128]; proj: [nscales][128]
+    __shared__ double h0[UNET_FDIM], h1[UNET_FDIM], f[UNET_FDIM];
+    const int k = threadIdx.x;
+    const double* w0 = mlp;
+    const double* b0 = w0 + UNET_FDIM;
+    const double* w1 = b0 + UNET_FDIM;
+    const double* b1 = w1 + UNET_FDIM * UNET_FDIM;
+    const double* w2 = b1 + UNET_FDIM;
+    const double* b2 = w2 + UNET_FDIM * UNET_FDIM;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    h0[k] = sin(w0[k] * tau + b0[k]);
+    __syncthreads();
+    double s = b1[k];
+    for (int j = 0; j < UNET_FDIM; ++j) s += w1[k * UNET_FDIM + j] * h0[j];
+    h1[k] = sin(s);
+    __syncthreads();
+    s = b2[k];
+    for (int j = 0; j < UNET_FDIM; ++j) s += w2[k * UNET_FDIM + j] * h1[j];
+    f[k] = s;
+    __syncthreads();
+    for (int i = k; i < nscales; i += UNET_FDIM) {
+        double v = 0.0;
+        for (int j = 0; j < UNET_FDIM; ++j) v += proj[(size_t)i * UNET_FDIM + j] * f[j];
+        scales[i] = rbf((float)v);  // FP64 -> FP32 -> BF16, as the reference stores it
+    }
+}
+
+// First convolution: x = BF16(phi, c, tau) with zero padding outside the image, 3x3, 3 -> 32.
+// One thread per output pixel, one 128-pixel tile per block.
+__global__ void __launch_bounds__(TPB)
+in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c, int pitch, int h, int w,
+               float tau, const float* __restrict__ wgt /* [27][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
+               float* __restrict__ partials)
+{
+    __shared__ float ws[27 * 32];
+    __shared__ float red[4];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int i = threadIdx.x; i < 27 * 32; i += TPB) ws[i] = wgt[i];
+    __syncthreads();
+    const int tpi = h * w / TPB;
+    const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
+    const int p = t * TPB + threadIdx.x, y = p / w, x = p % w;
+    const float* F = phi[img];
+    const float* C = c[img];
+    const float tb = rbf(tau);
+    float acc[32];
+#pragma unroll
+    for (int o = 0; o < 32; ++o) acc[o] = 0.f;
+    for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+            const int yy = y + ky - 1, xx = x + kx - 1;
+            const bool in = yy >= 0 && yy < h && xx >= 0 && xx < w;
+            const float v0 = in ? rbf(F[(size_t)yy * pitch + xx]) : 0.f;
+            const float v1 = in ? rbf(C[(size_t)yy * pitch + xx]) : 0.f;
+            const float v2 = in ? tb : 0.f;
+            const float* wk = ws + (ky * 3 + kx) * 3 * 32;
+#pragma unroll
+            for (int o = 0; o < 32; ++o) acc[o] = fmaf(v0, wk[o], fmaf(v1, wk[32 + o], fmaf(v2, wk[64 + o], acc[o])));
+        }
+    uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)img * h * w + p) * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            pk[j] = (uint32_t)to_bf(acc[8 * q + 2 * j]) | ((uint32_t)to_bf(acc[8 * q + 2 * j + 1]) << 16);
+        dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    // group sums: 8 groups of 4 channels
+    for (int g = 0; g < 8; ++g) {
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float v = acc[4 * g + j];
+            s1 += v;
+            s2 = fmaf(v, v, s2);
+        }
+        s1 = block_sum128(s1, red);
+        s2 = block_sum128(s2, red);
+        if (threadIdx.x == 0) {
+            partials[(((size_t)img * 8 + g) * tpi + t) * 2 + 0] = s1;
+            partials[(((size_t)img * 8 + g) * tpi + t) * 2 + 1] = s2;
+        }
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Last convolution: 3x3, 32 -> 2 channels, from BF16 NHWC [n][h][w][32]; per-channel sums.
+__global__ void __launch_bounds__(TPB)
+out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __restrict__ wgt /* [9][32][2] */,
+                uint16_t* __restrict__ out, float* __restrict__ partials)
+{
+    __shared__ float ws[9 * 32 * 2];
+    __shared__ float red[4];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int i = threadIdx.x; i < 9 * 32 * 2; i += TPB) ws[i] = wgt[i];
+    __syncthreads();
+    const int tpi = h * w / TPB;
+    const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
+    const int p = t * TPB + threadIdx.x, y = p / w, x = p % w;
+    float a0 = 0.f, a1 = 0.f;
+    for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+            const int yy = y + ky - 1, xx = x + kx - 1;
+            if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+            const uint4* src = reinterpret_cast<const uint4*>(in + ((size_t)img * h * w + (size_t)yy * w + xx) * 32);
+            const float* wk = ws + (ky * 3 + kx) * 64;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 v = src[q];
+                const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int ci = 8 * q + 2 * j;
+                    const float lo = bf((uint16_t)(u[j] & 0xffffu)), hi = bf((uint16_t)(u[j] >> 16));
+                    a0 = fmaf(lo, wk[2 * ci], fmaf(hi, wk[2 * ci + 2], a0));
+                    a1 = fmaf(lo, wk[2 * ci + 1], fmaf(hi, wk[2 * ci + 3], a1));
+                }
+            }
+        }
+    reinterpret_cast<uint32_t*>(out)[(size_t)img * h * w + p] = (uint32_t)to_bf(a0) | ((uint32_t)to_bf(a1) << 16);
+    const float s[4] = {a0, a0 * a0, a1, a1 * a1};
+    for (int k = 0; k < 4; ++k) {
+        const float v = block_sum128(s[k], red);
+        if (threadIdx.x == 0) partials[(((size_t)img * 2 + (k >> 1)) * tpi + t) * 2 + (k & 1)] = v;
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// (mean, 1/sqrt(var + eps)) per image and group from the per-tile sums, FP64 in a fixed order.
+__global__ void gn_stats_kernel(const float* __restrict__ partials, int tpi, double count, float* __restrict__ stats)
+{
+    __shared__ double r1[TPB], r2[TPB];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const float* p = partials + (size_t)blockIdx.x * tpi * 2;
+    double s1 = 0.0, s2 = 0.0;
+    for (int t = threadIdx.x; t < tpi; t += TPB) {
+        s1 += (double)p[2 * t];
+        s2 += (double)p[2 * t + 1];
+    }
+    r1[threadIdx.x] = s1;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = TPB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+            r2[threadIdx.x] += r2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = r1[0] / count;
+        double var = r2[0] / count - mean * mean;
+        var = var < 0.0 ? 0.0 : var;
+        stats[2 * blockIdx.x] = (float)mean;
+        stats[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var + (double)UNET_EPS));
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+struct Gn8 {  // GN parameters of 8 consecutive channels
+    float m[8], r[8], g[8], b[8];
+};
+
+__device__ __forceinline__ Gn8 gn8(const float* stats, const float* gamma, const float* beta, int img, int groups,
+                                   int C, int c0)
+{
+    Gn8 q;
+    const int cg = C / groups;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int ch = c0 + j, g = ch / cg;
+        q.m[j] = stats[2 * (img * groups + g)];
+        q.r[j] = stats[2 * (img * groups + g) + 1];
+        q.g[j] = gamma[ch];
+        q.b[j] = beta[ch];
+    }
+    return q;
+}
+
+__device__ __forceinline__ void unpack8(const uint4 v, float* f)
+{
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f[2 * j] = bf((uint16_t)(u[j] & 0xffffu));
+        f[2 * j + 1] = bf((uint16_t)(u[j] >> 16));
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* f)
+{
+    uint32_t u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = (uint32_t)to_bf(f[2 * j]) | ((uint32_t)to_bf(f[2 * j + 1]) << 16);
+    return make_uint4(u[0], u[1], u[2], u[3]);
+}
+
+// Encoder level: z = BF16(GELU(GN(x))); zc = BF16(z * s) into the skip slice (channels [0, C) of a
+// buffer with cat_stride channels); pool (if not NULL) = 2x2 max of z.  One thread per 8 channels
+// of a 2x2 pixel block (pool) or of one pixel (no pool).
+__global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h, int w, int C, int groups,
+                                    const float* __restrict__ stats, const float* __restrict__ gamma,
+                                    const float* __restrict__ beta, const float* __restrict__ scale,
+                                    uint16_t* __restrict__ cat, int cat_stride, uint16_t* __restrict__ pool)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int c8 = C / 8;
+    const int ph = pool ? h / 2 : h, pw = pool ? w / 2 : w;
+    const long long total = (long long)n * ph * pw * c8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cb = (int)(i % c8);
+        long long r = i / c8;
+        const int px = (int)(r % pw);
+        r /= pw;
+        const int py = (int)(r % ph);
+        const int img = (int)(r / ph);
+        const Gn8 q = gn8(stats, gamma, beta, img, groups, C, cb * 8);
+        float s[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = scale[cb * 8 + j];
+        float mx[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mx[j] = -INFINITY;
+        const int nsub = pool ? 4 : 1;
+        for (int sidx = 0; sidx < nsub; ++sidx) {
+            const int yy = pool ? 2 * py + (sidx >> 1) : py, xx = pool ? 2 * px + (sidx & 1) : px;
+            const size_t pix = ((size_t)img * h + yy) * w + xx;
+            float v[8], z[8], zc[8];
+            unpack8(reinterpret_cast<const uint4*>(x + pix * C)[cb], v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                z[j] = rbf(gelu((v[j] - q.m[j]) * q.r[j] * q.g[j] + q.b[j]));
+                zc[j] = z[j] * s[j];
+                mx[j] = fmaxf(mx[j], z[j]);
+            }
+            reinterpret_cast<uint4*>(cat + pix * cat_stride)[cb] = pack8(zc);
+        }
+        if (pool) reinterpret_cast<uint4*>(pool + (((size_t)img * ph + py) * pw + px) * C)[cb] = pack8(mx);
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Decoder level: y = BF16(GELU(GN(x))), NHWC with C channels.
+__global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pixels, int C, int hw, int groups,
+                                    const float* __restrict__ stats, const float* __restrict__ gamma,
+                                    const float* __restrict__ beta, uint16_t* __restrict__ y)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int c8 = C / 8;
+    const long long total = pixels * c8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cb = (int)(i % c8);
+        const long long pix = i / c8;
+        const int img = (int)(pix / hw);
+        const Gn8 q = gn8(stats, gamma, beta, img, groups, C, cb * 8);
+        float v[8];
+        unpack8(reinterpret_cast<const uint4*>(x + pix * C)[cb], v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = gelu((v[j] - q.m[j]) * q.r[j] * q.g[j] + q.b[j]);
+        reinterpret_cast<uint4*>(y + pix * C)[cb] = pack8(v);
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Output: (phi, c) = GN(x) with one group per channel, written as FP32 into the DNS fields; the
+// vapor density is reset to its initial-state profile rho_top (1 - phi) / 2.
+__global__ void gn_apply_out_kernel(const uint16_t* __restrict__ x, int n, int h, int w,
+                                    const float* __restrict__ stats, const float* __restrict__ gamma,
+                                    const float* __restrict__ beta, float* const* __restrict__ phi,
+                                    float* const* __restrict__ c, float* const* __restrict__ rho, int pitch,
+                                    float rho_top)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const long long total = (long long)n * h * w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int img = (int)(i / ((long long)h * w));
+        const int p = (int)(i % ((long long)h * w)), yy = p / w, xx = p % w;
+        const uint32_t u = reinterpret_cast<const uint32_t*>(x)[i];
+        const float v0 = bf((uint16_t)(u & 0xffffu)), v1 = bf((uint16_t)(u >> 16));
+        const float f = (v0 - stats[4 * img]) * stats[4 * img + 1] * gamma[0] + beta[0];
+        const float cc = (v1 - stats[4 * img + 2]) * stats[4 * img + 3] * gamma[1] + beta[1];
+        const size_t o = (size_t)yy * pitch + xx;
+        phi[img][o] = f;
+        c[img][o] = cc;
+        rho[img][o] = rho_top * (1.0f - f) * 0.5f;
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+cudaLaunchConfig_t cfg_of(dim3 grid, int threads, cudaStream_t s, cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+unsigned grid_for(long long items, int threads)
+{
+    long long b = (items + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_cond(const double* mlp, const double* proj, double tau, float* scales, int nscales, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3(1), UNET_FDIM, s, attr);
+    return cudaLaunchKernelEx(&cfg, cond_kernel, mlp, proj, tau, scales, nscales);
+}
+
+cudaError_t launch_in_conv(const float* const* phi, const float* const* c, int pitch, int n, int h, int w, float tau,
+                           const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
+    return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, pitch, h, w, tau, wgt, out, partials);
+}
+
+cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, uint16_t* out, float* partials,
+                            cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
+    return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, out, partials);
+}
+
+cudaError_t launch_gn_stats(const float* partials, int n, int groups, int tpi, double count, float* stats,
+                            cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * groups)), TPB, s, attr);
+    return cudaLaunchKernelEx(&cfg, gn_stats_kernel, partials, tpi, count, stats);
+}
+
+cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
+                          const float* gamma, const float* beta, const float* scale, uint16_t* cat, int cat_stride,
+                          uint16_t* pool, cudaStream_t s)
+{
+    const long long items = (long long)n * (pool ? (h / 2) * (w / 2) : h * w) * (C / 8);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(items, 256)), 256, s, attr);
+    return cudaLaunchKernelEx(&cfg, gn_apply_enc_kernel, x, n, h, w, C, groups, stats, gamma, beta, scale, cat,
+                              cat_stride, pool);
+}
+
+cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
+                          const float* gamma, const float* beta, uint16_t* y, cudaStream_t s)
+{
+    const long long pixels = (long long)n * h * w;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(pixels * (C / 8), 256)), 256, s, attr);
+    return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, pixels, C, h * w, groups, stats, gamma, beta, y);
+}
+
+cudaError_t launch_gn_out(const uint16_t* x, int n, int h, int w, const float* stats, const float* gamma,
+                          const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
+                          float rho_top, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for((long long)n * h * w, 256)), 256, s, attr);
+    return cudaLaunchKernelEx(&cfg, gn_apply_out_kernel, x, n, h, w, stats, gamma, beta, phi, c, rho, pitch,
+                              rho_top);
+}
+
+}  // namespace pf

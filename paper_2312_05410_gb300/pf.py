@@ -97,6 +97,16 @@ def _load():
                                    vp, vp]
     L.pf_tconv2x2_bf16.restype = C.c_int
     L.pf_unet_last_error.argtypes, L.pf_unet_last_error.restype = [], C.c_char_p
+    L.pf_unet_workspace_size.argtypes, L.pf_unet_workspace_size.restype = [C.c_int, C.c_int, C.c_int], sz
+    L.pf_unet_init.argtypes = [C.POINTER(C.POINTER(C.c_float)), C.c_int, C.c_int, C.c_int, C.c_int, vp, sz, vp,
+                               C.POINTER(vp)]
+    L.pf_unet_init.restype = C.c_int
+    L.pf_unet_jump.argtypes = [vp, C.c_int, pp, pp, pp, C.c_int, C.c_double, C.c_double]
+    L.pf_unet_jump.restype = C.c_int
+    L.pf_unet_sync.argtypes, L.pf_unet_sync.restype = [vp], C.c_int
+    L.pf_unet_buffer.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(C.c_int)]
+    L.pf_unet_buffer.restype = C.c_int
+    L.pf_unet_destroy.argtypes, L.pf_unet_destroy.restype = [vp], C.c_int
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
     L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
     return L
@@ -512,3 +522,67 @@ def tconv2x2_bf16(x, w_dev, out=None, out_coff: int = 0, err=None, stream=None):
     _ucheck(lib.pf_tconv2x2_bf16(x.data_ptr(), n, h, wd, cin, w_dev.data_ptr(), cout, out.data_ptr(), out.shape[3],
                                  out_coff, err.data_ptr(), s))
     return out
+
+
+UNET_WEIGHT_NAMES = (["mlp_w0", "mlp_b0", "mlp_w1", "mlp_b1", "mlp_w2", "mlp_b2", "proj1", "proj2", "proj3", "proj4",
+                      "enc1", "enc2", "enc3", "enc4", "dec4", "dec3", "dec2", "dec1", "up4", "up3", "up2", "out"]
+                     + [f"{n}_{g}" for n in ("enc1", "enc2", "enc3", "enc4", "dec4", "dec3", "dec2", "dec1", "out")
+                        for g in ("gamma", "beta")])
+UNET_BUFFERS = ("pre1", "cat1", "p1", "pre2", "cat2", "p2", "pre3", "cat3", "p3", "pre4", "zc4", "h4", "h3", "h2",
+                "h1", "pre_out")
+_UNET_LEVEL = (0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 2, 1, 0, 0)
+
+
+class UNet:
+    """The time-conditioned U-Net surrogate (pf_unet_*): weights in PyTorch layouts by name (see
+    UNET_WEIGHT_NAMES), a batch of `batch` runs of ny x nx cells."""
+
+    def __init__(self, weights: dict, batch: int, nx: int, ny: int, stream=None):
+        import torch
+        self.batch, self.nx, self.ny = batch, nx, ny
+        self.stream = stream or torch.cuda.current_stream()
+        size = lib.pf_unet_workspace_size(batch, nx, ny)
+        if size == 0:
+            raise PFError(PF_ERR_ARG, f"U-Net shape {batch} x {ny} x {nx} unsupported")
+        self._arrays = [np.ascontiguousarray(np.asarray(weights[k], dtype=np.float32)) for k in UNET_WEIGHT_NAMES]
+        ptrs = (C.POINTER(C.c_float) * len(self._arrays))(
+            *[a.ctypes.data_as(C.POINTER(C.c_float)) for a in self._arrays])
+        self.work = torch.empty(size + 256, dtype=torch.uint8, device="cuda")
+        self._base = (self.work.data_ptr() + 255) // 256 * 256
+        h = C.c_void_p()
+        _ucheck(lib.pf_unet_init(ptrs, len(self._arrays), batch, nx, ny, self._base, size, self.stream.cuda_stream,
+                                 C.byref(h)))
+        self.h = h
+
+    def jump(self, fields, tau: float, rho_top: float = 1.0):
+        """fields: `batch` tuples (phi, c, rho) of (ny, pitch) float32 CUDA tensors, updated in place."""
+        n = len(fields)
+        arr = [(C.c_void_p * n)(*[int(f[q].data_ptr()) for f in fields]) for q in range(3)]
+        pitch = fields[0][0].shape[1]
+        _ucheck(lib.pf_unet_jump(self.h, n, arr[0], arr[1], arr[2], pitch, float(tau), float(rho_top)))
+
+    def sync(self):
+        _ucheck(lib.pf_unet_sync(self.h))
+
+    def buffer(self, name: str):
+        """Activation buffer `name` (see UNET_BUFFERS) as a BF16 NHWC tensor view of the workspace."""
+        import torch
+        k = UNET_BUFFERS.index(name)
+        ptr, ch = C.c_void_p(), C.c_int()
+        _ucheck(lib.pf_unet_buffer(self.h, k, C.byref(ptr), C.byref(ch)))
+        lev = _UNET_LEVEL[k]
+        hh, ww = self.ny >> lev, self.nx >> lev
+        off = ptr.value - self.work.data_ptr()
+        nel = self.batch * hh * ww * ch.value
+        return self.work[off:off + 2 * nel].view(torch.bfloat16).view(self.batch, hh, ww, ch.value)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            _ucheck(lib.pf_unet_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -108,3 +108,47 @@ def test_unsupported_shapes_are_rejected(pf):
     with pytest.raises(pf.PFError) as e:
         pf.conv3x3_bf16(x, w, 8)
     assert e.value.code == pf.PF_ERR_ARG
+
+
+def _unet_case(pf, n=2, H=128, seed=0, tau=0.5):
+    import oracle as O
+    from paper_2312_05410_gb300 import inputs as I
+    W = U.init_weights(seed)
+    p = O.with_dt(I.default_params())
+    states = [I.film_state(I.FilmSpec(H, H, 40.0 + 10 * k, seed=k), p) for k in range(n)]
+    fields = [tuple(pf.device_fields(st)) for st in states]
+    net = pf.UNet(W, n, H, H)
+    net.jump(fields, tau, rho_top=1.0)
+    net.sync()
+    x = np.stack([np.stack([st[0], st[1], np.full((H, H), tau)]) for st in states])
+    taps = {}
+    ref = U.forward(W, x, tau, taps)
+    return net, fields, ref, taps
+
+
+def _layer_report(net, taps):
+    pairs = [("zc1", "cat1", 0, 32), ("d1", "cat1", 32, 64), ("zc2", "cat2", 0, 64), ("d2", "cat2", 64, 128),
+             ("zc3", "cat3", 0, 128), ("d3", "cat3", 128, 256), ("zc4", "zc4", 0, 256), ("h1", "h1", 0, 32)]
+    rep = {}
+    for tap, buf, c0, c1 in pairs:
+        got = to_nchw(net.buffer(buf)[..., c0:c1])
+        ref = taps[tap].numpy()
+        d = np.abs(got - ref)
+        rep[tap] = (float(np.mean(d > ulp_bf16(ref))), float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    return rep
+
+
+def test_unet_jump_matches_the_reference_network(pf):
+    net, fields, ref, taps = _unet_case(pf)
+    rep = _layer_report(net, taps)
+    print("per-layer (fraction beyond 1 BF16 ulp, relative L2):", rep)
+    for i, f in enumerate(fields):
+        phi = f[0][:, :128].cpu().numpy().astype(np.float64)
+        c = f[1][:, :128].cpu().numpy().astype(np.float64)
+        rho = f[2][:, :128].cpu().numpy()
+        e_phi = np.linalg.norm(phi - ref[i, 0]) / np.linalg.norm(ref[i, 0])
+        e_c = np.linalg.norm(c - ref[i, 1]) / np.linalg.norm(ref[i, 1])
+        print(f"run {i}: relative L2 phi {e_phi:.3e} c {e_c:.3e}")
+        assert e_phi <= 2e-2 and e_c <= 2e-2
+        np.testing.assert_array_equal(rho, (np.float32(1.0) * (np.float32(1.0) - phi.astype(np.float32))) * np.float32(0.5))
+    net.close()
