@@ -58,6 +58,9 @@ WORKLOADS = {
     "adjoint256": dict(kind="adjoint", spec=I.FilmSpec(256, 256, 16.0, seed=4), params=dict(v_mag=0.4), steps=1000,
                        K=50, bytes_per_cell_update=84,
                        desc="adjoint 256x256, 1000 steps, checkpoint every 50, gradient of a final-state loss"),
+    "hybrid256": dict(kind="hybrid", n_runs=16, side=256, seed=5, steps=100000, dns_stretch=2000, jump=2000,
+                      desc="hybrid DNS / U-Net: 16 runs of 256x256, 2000 DNS steps alternating with one U-Net jump "
+                           "of 2000 steps, to 100000 steps"),
     "ensemble64": dict(kind="ensemble", n_runs=64, seed=3, steps=10000,
                        desc="batched DNS ensemble: 64 runs, sides in {128,192,256,384,512}, V~U[0.1,0.9], "
                             "c_inc~U[0.3,0.7], 10000 steps"),
@@ -82,8 +85,8 @@ def measured_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return dict(hbm_gbs=d["hbm_gbs"], source="measured")
-    return dict(hbm_gbs=6800.0, source="fallback")
+        return dict(hbm_gbs=d["hbm_gbs"], bf16_tflops=d.get("bf16_tflops", 1900.0), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source="fallback")
 
 
 class ClockSampler:
@@ -250,6 +253,103 @@ class AdjointRun:
         pass
 
 
+class HybridRun:
+    """The hybrid solver: a batch of runs advanced by DNS stretches (one fused ensemble launch per
+    step) alternating with jumps of the time-conditioned U-Net (tensor-core convolutions), against
+    the same runs advanced by plain DNS.  The weights are seeded and untrained."""
+
+    def __init__(self, pf, W):
+        import torch
+
+        ms = []
+        for m in I.hybrid_members(W["n_runs"], W["side"], seed=W["seed"]):
+            p = I.default_params(v_mag=m["v_mag"])
+            p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
+            ms.append((p, *I.film_state(m["spec"], p)))
+        self.pf = pf
+        self.ens = pf.Ensemble(ms)
+        self.ens.set_tile(0)
+        self.stream = self.ens.stream
+        self.fields = [t for run in self.ens.fields for t in run]
+        side = W["side"]
+        self.net = pf.UNet(I.unet_weights(0), W["n_runs"], side, side, stream=self.stream)
+        self.cells = W["n_runs"] * side * side
+        self.nsteps = W["steps"]
+        self.stretch, self.jump_steps = W["dns_stretch"], W["jump"]
+        self.cycles = self.nsteps // (self.stretch + self.jump_steps)
+        self.rho_top = ms[0][0]["rho_top"]
+        self.launches = self.cycles * (self.stretch + 31)
+        self.fallbacks = 0
+        init = [t.clone() for t in self.fields]
+        self.backup = [t.clone() for t in self.fields]
+        # plain-DNS reference run (outside the timed region): final state and its time
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(self.stream)
+        self.ens.step(self.nsteps)
+        ev[1].record(self.stream)
+        torch.cuda.synchronize()
+        self.dns_s = ev[0].elapsed_time(ev[1]) / 1e3
+        self.dns_final = [t.clone() for t in self.fields]
+        for t, s in zip(self.fields, init):
+            t.copy_(s)
+        # one jump alone, timed
+        self.net.jump(self.ens.fields, 1.0, self.rho_top)
+        torch.cuda.synchronize()
+        ev[0].record(self.stream)
+        for _ in range(5):
+            self.net.jump(self.ens.fields, 1.0, self.rho_top)
+        ev[1].record(self.stream)
+        torch.cuda.synchronize()
+        self.jump_s = ev[0].elapsed_time(ev[1]) / 5e3
+        self.net.sync()
+        for t, s in zip(self.fields, init):
+            t.copy_(s)
+        from paper_2312_05410_gb300.unet_flops import flops_per_sample
+        self.jump_flops = W["n_runs"] * flops_per_sample(side, side)
+        self.config = {"runs": W["n_runs"], "nx": side, "ny": side, "timesteps_per_run": self.nsteps,
+                       "dns_stretch": self.stretch, "jump_steps": self.jump_steps, "cycles": self.cycles,
+                       "unet": "32-64-128-256, BF16 tensor-core convolutions, seeded untrained weights",
+                       "launch": "fused ensemble step launches (graph replays) + ~31 U-Net launches per jump"}
+
+    def reset_counters(self):
+        pass
+
+    def run(self):
+        import torch
+
+        # DNS stretch, snapshot, jump; a jump whose prediction fails the plausibility check
+        # (non-finite, or phi / c out of range in any run) is undone and the stretch is run by DNS
+        self.fallbacks = 0
+        for _ in range(self.cycles):
+            self.ens.step(self.stretch)
+            with torch.cuda.stream(self.stream):
+                for b, t in zip(self.backup, self.fields):
+                    b.copy_(t)
+            self.net.jump(self.ens.fields, self.jump_steps / 2000.0, self.rho_top)
+            if not all(self.net.check()):
+                with torch.cuda.stream(self.stream):
+                    for b, t in zip(self.backup, self.fields):
+                        t.copy_(b)
+                self.ens.step(self.jump_steps)
+                self.fallbacks += 1
+
+    def final_diag(self):
+        self.net.sync()
+        err = []
+        for q in range(2):
+            num = sum(float(((a[q] - b[q]) ** 2).sum()) for a, b in zip(self.ens.fields, self._dns_runs()))
+            den = sum(float((b[q] ** 2).sum()) for b in self._dns_runs())
+            err.append((num / den) ** 0.5)
+        return err
+
+    def _dns_runs(self):
+        return [tuple(self.dns_final[3 * r + q] for q in range(3)) for r in range(len(self.ens.fields))]
+
+    def close(self):
+        self.net.close()
+        self.ens.close()
+
+
 def run_native(args):
     import torch
 
@@ -267,7 +367,8 @@ def run_native(args):
 
     W = WORKLOADS[args.workload]
     kind = W.get("kind")
-    R = EnsembleRun(pf, W) if kind == "ensemble" else (AdjointRun(pf, W) if kind == "adjoint" else SingleRun(pf, W))
+    runners = {"ensemble": EnsembleRun, "adjoint": AdjointRun, "hybrid": HybridRun}
+    R = runners.get(kind, SingleRun)(pf, W)
     stream = R.stream
     init = [t.clone() for t in R.fields]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
@@ -338,6 +439,9 @@ def run_native(args):
     # Dominant kernel: the fused step. Its average launch duration is bounded above by
     # the timed region per step launch (it also covers the diagnostic kernels and gaps).
     per_launch_s = total_s / (nsteps * args.steps)
+    if kind == "hybrid":  # the DNS launches only: the jumps' time (measured alone) is taken out
+        dns_steps = R.cycles * R.stretch + R.fallbacks * R.jump_steps
+        per_launch_s = max(total_s / args.steps - R.cycles * R.jump_s, 1e-9) / dns_steps
     bpc = W.get("bytes_per_cell_update", BYTES_PER_CELL_UPDATE)
     achieved = bpc * cells / per_launch_s / 1e9
     tr = NCU_TRAFFIC.get(args.workload)
@@ -358,6 +462,16 @@ def run_native(args):
         "wall_s": wall,
         "final_diag": final_diag,
     }
+    if kind == "hybrid":
+        hyb_s = total_s / args.steps
+        jump_tf = R.jump_flops / R.jump_s / 1e12
+        line["hybrid"] = {"hybrid_s": hyb_s, "plain_dns_s": R.dns_s, "speedup_vs_dns": R.dns_s / hyb_s,
+                          "jumps": R.cycles, "dns_fallbacks": R.fallbacks,
+                          "rel_l2_vs_dns": {"phi": final_diag[0], "c": final_diag[1]},
+                          "jump_ms": R.jump_s * 1e3, "jump_tflops": jump_tf,
+                          "jump_tensor_frac_of_bf16_peak": jump_tf / peaks["bf16_tflops"],
+                          "weights": "seeded, untrained (training is not built): jumps that fail the "
+                                     "plausibility check fall back to DNS"}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)

@@ -265,9 +265,9 @@ const char* pf_adjoint_last_error(void);
  *   zero padding, no bias).  in: device BF16 NHWC [n][h][w][cin]; wgt: device BF16
  *   [9][cout][cin]; out: device BF16 NHWC buffer of out_cstride channels per pixel,
  *   of which [out_coff, out_coff + cout) are written.  partials (device, may be NULL):
- *   FP32 [n][groups][h*w/128][2], the sum and the sum of squares of the FP32
- *   results of each 128-pixel tile over each of `groups` equal channel groups (the
- *   group-normalisation statistics).
+ *   the group-normalisation statistics of the FP32 results over `groups` equal
+ *   channel groups, as FP32 [n][groups][h*w/128][4][2]: the sum and the sum of
+ *   squares over each quarter (32 pixels) of each 128-pixel tile.
  * pf_tconv2x2_bf16: out[n][2y+dy][2x+dx][out_coff + co] = BF16( sum_ci in[n][y][x][ci]
  *   * wgt[(2 dy + dx) cout + co][ci] ) (stride-2 2x2 transposed convolution, no bias);
  *   out is n x 2h x 2w pixels.
@@ -318,6 +318,9 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
  *   profile; the surrogate does not predict rho.  Asynchronous on the handle's
  *   stream, about 30 kernel launches.
  * pf_unet_sync: synchronise; PF_ERR_TIMEOUT if a tensor-core pipeline wait ran out.
+ * pf_unet_check: plausibility of the last jump's prediction, the hybrid solver's
+ *   gate for its plain-DNS fallback.  ok[i] (host, n ints) is 1 if every phi and c
+ *   of run i is finite and inside [phi_lo, phi_hi] x [c_lo, c_hi], else 0.  Synchronises.
  * pf_unet_buffer: device pointer and channel count of activation buffer `which`
  *   (0-15: pre1, cat1, p1, pre2, cat2, p2, pre3, cat3, p3, pre4, zc4, h4, h3, h2,
  *   h1, pre_out; NHWC BF16 at level resolution), for inspection.
@@ -329,6 +332,7 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
 int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau,
                  double rho_top);
 int pf_unet_sync(pf_unet* u);
+int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, int* ok);
 int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels);
 int pf_unet_destroy(pf_unet* u);
 const char* pf_unet_last_error(void);

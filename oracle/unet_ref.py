@@ -24,6 +24,9 @@ the paper is silent are marked READING):
 Channels 32-64-128-256.  Input x = (phi, c, dt / dt_ref) planes (READING: the two
 fields plus a plane holding the jump length; the paper feeds lb = 3 frames of c).
 
+Weights come from ``paper_2312_05410_gb300.inputs.unet_weights`` (seeded numbers,
+no arithmetic of the method).
+
 Precision model of the GPU path that this mirrors: inputs, weights and every
 stored activation are BF16 (round to nearest even); products are exact and sums
 are kept in high precision (FP64 here, FP32 on the GPU); group statistics are
@@ -69,43 +72,6 @@ def _t(a) -> torch.Tensor:
 
 def _rb(t: torch.Tensor) -> torch.Tensor:
     return _t(bf16(t.numpy()))
-
-
-def init_weights(seed: int = 0) -> dict:
-    """Seeded He-normal weights (FP32 arrays, PyTorch conventions: conv [Cout, Cin, 3, 3], tconv
-    [Cin, Cout, 2, 2]).  The training of the network is not part of this reference."""
-    g = np.random.default_rng(seed)
-    W = {}
-
-    def he(shape, fan_in):
-        return (g.standard_normal(shape) * math.sqrt(2.0 / fan_in)).astype(np.float32)
-
-    W["mlp_w0"] = he((FDIM, 1), 1)
-    W["mlp_b0"] = (g.standard_normal(FDIM) * 0.5).astype(np.float32)
-    W["mlp_w1"] = he((FDIM, FDIM), FDIM)
-    W["mlp_b1"] = (g.standard_normal(FDIM) * 0.1).astype(np.float32)
-    W["mlp_w2"] = he((FDIM, FDIM), FDIM)
-    W["mlp_b2"] = (g.standard_normal(FDIM) * 0.1).astype(np.float32)
-    for p, c in enumerate(CH, 1):
-        W[f"proj{p}"] = (g.standard_normal((c, FDIM)) / math.sqrt(FDIM)).astype(np.float32)
-    cin = IN_CH
-    for p, c in enumerate(CH, 1):
-        W[f"enc{p}"] = he((c, cin, 3, 3), 9 * cin)
-        cin = c
-    # decoder blocks: dec4 on zc4 (256 -> 256), dec3 on zc3 ++ d3 (256 -> 128), dec2 (128 -> 64), dec1 (64 -> 32)
-    W["dec4"] = he((256, 256, 3, 3), 9 * 256)
-    W["dec3"] = he((128, 256, 3, 3), 9 * 256)
-    W["dec2"] = he((64, 128, 3, 3), 9 * 128)
-    W["dec1"] = he((32, 64, 3, 3), 9 * 64)
-    W["up4"] = he((256, 128, 2, 2), 256)
-    W["up3"] = he((128, 64, 2, 2), 128)
-    W["up2"] = he((64, 32, 2, 2), 64)
-    W["out"] = he((OUT_CH, 32, 3, 3), 9 * 32)
-    for name, c in (("enc1", 32), ("enc2", 64), ("enc3", 128), ("enc4", 256), ("dec4", 256), ("dec3", 128),
-                    ("dec2", 64), ("dec1", 32), ("out", OUT_CH)):
-        W[name + "_gamma"] = (1.0 + 0.1 * g.standard_normal(c)).astype(np.float32)
-        W[name + "_beta"] = (0.1 * g.standard_normal(c)).astype(np.float32)
-    return W
 
 
 def basis(W: dict, tau: float) -> np.ndarray:

@@ -98,7 +98,7 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 struct UnetLayout {
     size_t mlp, proj, win, wout, wc[7], wt[3], gb[9][2];
     size_t act[16];  // see ACT_* below
-    size_t partials, stats, scales, err, ptrs, total;
+    size_t partials, stats, scales, err, ptrs, flags, total;
 };
 enum { A_PRE1, A_CAT1, A_P1, A_PRE2, A_CAT2, A_P2, A_PRE3, A_CAT3, A_P3, A_PRE4, A_ZC4, A_H4, A_H3, A_H2, A_H1, A_PREO };
 
@@ -134,11 +134,12 @@ UnetLayout unet_layout(int n, int h, int w)
     const size_t elems[16] = {P0 * 32, P0 * 64, P1 * 32, P1 * 64, P1 * 128, P2 * 64, P2 * 128, P2 * 256,
                               P3 * 128, P3 * 256, P3 * 256, P3 * 256, P2 * 128, P1 * 64, P0 * 32, P0 * 2};
     for (int k = 0; k < 16; ++k) L.act[k] = take(2 * elems[k]);
-    L.partials = take(sizeof(float) * (size_t)n * 8 * (h * (size_t)w / 128) * 2);
+    L.partials = take(sizeof(float) * (size_t)n * 8 * (h * (size_t)w / 128) * 4 * 2);
     L.stats = take(sizeof(float) * (size_t)n * 8 * 2);
     L.scales = take(sizeof(float) * 480);
     L.err = take(sizeof(int));
     L.ptrs = take(sizeof(float*) * 3 * (size_t)n);
+    L.flags = take(sizeof(int) * (size_t)n);
     L.total = off;
     return L;
 }
@@ -151,6 +152,9 @@ struct pf_unet {
     UnetLayout L;
     cudaStream_t stream;
     std::vector<float*> ptrs;  // host copy of the run pointer table (phi[n], c[n], rho[n])
+    double cond_tau;           // jump length the stored conditioning factors belong to
+    int last_pitch;            // row pitch of the fields of the last jump
+    bool cond_valid;
     template <class T>
     T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
 };
@@ -183,7 +187,7 @@ int conv_tc(pf_unet* u, int mode, const uint16_t* in, int h, int w, int cin, con
     cudaError_t e = pf::launch_umma_conv(mode, in, wgt, a, u->stream);
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "tensor-core convolution: %s", cudaGetErrorString(e));
     if (!stats_too) return PF_OK;
-    e = pf::launch_gn_stats(u->at<float>(u->L.partials), u->n, pf::GN_MAX_GROUPS, h * w / 128,
+    e = pf::launch_gn_stats(u->at<float>(u->L.partials), u->n, pf::GN_MAX_GROUPS, h * w / 128 * 4,
                             (double)(cout / pf::GN_MAX_GROUPS) * h * w, u->at<float>(u->L.stats), u->stream);
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "group statistics: %s", cudaGetErrorString(e));
     return PF_OK;
@@ -235,6 +239,9 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     u->L = L;
     u->stream = static_cast<cudaStream_t>(stream);
     u->ptrs.assign(3 * (size_t)batch, nullptr);
+    u->cond_valid = false;
+    u->last_pitch = nx;
+    u->cond_tau = 0.0;
     // ---- host-side conversion into the device layouts (once)
     std::vector<double> mlp;
     for (int k = 0; k < 6; ++k) {
@@ -314,6 +321,7 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
         u->ptrs[2 * n + i] = rho[i];
     }
     cudaStream_t s = u->stream;
+    u->last_pitch = pitch;
     cudaError_t e = cudaMemcpyAsync(u->base + u->L.ptrs, u->ptrs.data(), sizeof(float*) * 3 * n,
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "pointer table: %s", cudaGetErrorString(e));
@@ -331,8 +339,12 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     auto ck = [&](cudaError_t ce, const char* what) {
         if (rc == PF_OK && ce != cudaSuccess) rc = ufail(PF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ce));
     };
-    // conditioning factors of the four levels
-    ck(pf::launch_cond(u->at<double>(L.mlp), u->at<double>(L.proj), tau, sc, 480, s), "conditioning");
+    // conditioning factors of the four levels (kept while the jump length stays the same)
+    if (!u->cond_valid || u->cond_tau != tau) {
+        ck(pf::launch_cond(u->at<double>(L.mlp), u->at<double>(L.proj), tau, sc, 480, s), "conditioning");
+        u->cond_valid = rc == PF_OK;
+        u->cond_tau = tau;
+    }
     // ---- encoder
     ck(pf::launch_in_conv(dp, dp + n, pitch, n, H, W, (float)tau, u->at<float>(L.win), act(A_PRE1), part, s), "input conv");
     ck(pf::launch_gn_stats(part, n, G, H * W / 128, 4.0 * H * W, stats, s), "statistics");
@@ -371,6 +383,24 @@ int pf_unet_sync(pf_unet* u)
     if (e == cudaSuccess) e = cudaMemcpy(&err, u->base + u->L.err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "U-Net sync: %s", cudaGetErrorString(e));
     if (err & pf::UNET_ERR_TIMEOUT) return ufail(PF_ERR_TIMEOUT, "a bounded tensor-core pipeline wait ran out");
+    return PF_OK;
+}
+
+int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, int* ok)
+{
+    if (!u || !ok) return ufail(PF_ERR_ARG, "null pointer");
+    const int n = u->n;
+    int* flags = u->at<int>(u->L.flags);
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * n, u->stream);
+    float** dp = u->at<float*>(u->L.ptrs);  // the fields of the last jump
+    if (e == cudaSuccess)
+        e = pf::launch_check(dp, dp + n, n, u->h, u->w, u->last_pitch, (float)phi_lo, (float)phi_hi, (float)c_lo,
+                             (float)c_hi, flags, u->stream);
+    std::vector<int> f(n, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f.data(), flags, sizeof(int) * n, cudaMemcpyDeviceToHost, u->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "plausibility check: %s", cudaGetErrorString(e));
+    for (int i = 0; i < n; ++i) ok[i] = f[i] ? 0 : 1;
     return PF_OK;
 }
 

@@ -86,29 +86,46 @@ __device__ __forceinline__ uint16_t f_to_bf16(float f)
     return (uint16_t)(u >> 16);
 }
 
+// Tile geometry: tile T of a launch -> image, first pixel (x0, y0) and first GEMM column n0.
+struct TileGeo {
+    int img, t, x0, y0, n0;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const ConvArgs& a, int T, int mtiles, int NT)
+{
+    TileGeo g;
+    const int mt = T % mtiles, nt = T / mtiles;
+    const int tpi = (a.h * a.w) / TM;
+    const int BW = a.w < TM ? a.w : TM, BR = TM / BW, tiles_per_row = a.w / BW;
+    g.img = mt / tpi;
+    g.t = mt % tpi;
+    g.y0 = (g.t / tiles_per_row) * BR;
+    g.x0 = (g.t % tiles_per_row) * BW;
+    g.n0 = nt * NT;
+    return g;
+}
+
+// Persistent kernel: CTA b takes tiles b, b + gridDim.x, ...  The TMA / MMA stream runs through
+// all of them without draining; two accumulators in tensor memory let the epilogue of one tile
+// overlap the MMAs of the next.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
 umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ConvArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[MAX_ST], empty_bar[MAX_ST], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[MAX_ST], empty_bar[MAX_ST], accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
-    __shared__ float gn_part[4][2 * GN_MAX_GROUPS];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KC = a.kc, NT = a.nt, ST = a.stages;
     const uint32_t a_bytes = TM * KC * 2, b_bytes = NT * KC * 2, stage_bytes = a_bytes + b_bytes;
     const int kblocks = a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = ntaps * kblocks;
-
-    // tile -> (image, first pixel): tiles_per_image = H*W/128, rows of BW pixels, BR rows per tile
+    const int ncols = MODE == CONV3 ? a.cout : 4 * a.cout;
+    const int mtiles = a.n * ((a.h * a.w) / TM), tiles = mtiles * (ncols / NT);
     const int tpi = (a.h * a.w) / TM;
-    const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
-    const int BW = a.w < TM ? a.w : TM, BR = TM / BW;
-    const int tiles_per_row = a.w / BW;
-    const int y0 = (t / tiles_per_row) * BR, x0 = (t % tiles_per_row) * BW;
-    const int n0 = blockIdx.y * NT;  // first output column (channel or sub-pixel x channel)
+    const int BW = a.w < TM ? a.w : TM;
 
     if (tid == 0) {
         abort_flag = 0;
@@ -116,10 +133,13 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])) : "memory");
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_bar)) : "memory");
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {  // the whole warp allocates the accumulator columns
+    if (warp == 1) {  // the whole warp allocates both accumulators (2 NT columns)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&tmem_slot)), "r"(a.tmem_cols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -130,86 +150,102 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const uint32_t tmem = tmem_slot;
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    bool ok = true;
     if (warp == 0) {
-        if (lane == 0) {  // ---- producer
-            int issued_unconsumed = 0;
-            for (int it = 0; it < iters && ok; ++it) {
-                const int s = it % ST;
-                const uint32_t ph = (uint32_t)(it / ST) & 1u;
-                ok = mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, a.wait_cap, &abort_flag);
-                if (!ok) break;
-                const int tap = it / kblocks, kb = it % kblocks;
-                const int dy = MODE == CONV3 ? tap / 3 - 1 : 0, dx = MODE == CONV3 ? tap % 3 - 1 : 0;
-                const uint32_t fb = smem_u32(&full_bar[s]);
-                const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_bytes)
-                             : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
-                    "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * KC), "r"(x0 + dx), "r"(y0 + dy), "r"(img),
-                    "r"(fb)
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sb),
-                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * KC), "r"(n0), "r"(tap), "r"(fb)
-                    : "memory");
-                issued_unconsumed = it + 1;
+        if (lane == 0) {  // ---- producer: a continuous stream of (tile, tap, channel block) stages
+            int it = 0;  // stage counter over all tiles
+            bool ok = true;
+            for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x) {
+                const TileGeo g = tile_geo(a, T, mtiles, NT);
+                for (int k = 0; k < iters && ok; ++k, ++it) {
+                    const int s = it % ST;
+                    ok = mbar_wait(smem_u32(&empty_bar[s]), ((uint32_t)(it / ST) & 1u) ^ 1u, a.wait_cap, &abort_flag);
+                    if (!ok) break;
+                    const int tap = k / kblocks, kb = k % kblocks;
+                    const int dy = MODE == CONV3 ? tap / 3 - 1 : 0, dx = MODE == CONV3 ? tap % 3 - 1 : 0;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_bytes)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
+                        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * KC), "r"(g.x0 + dx), "r"(g.y0 + dy),
+                        "r"(g.img), "r"(fb)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sb),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * KC), "r"(g.n0), "r"(tap), "r"(fb)
+                        : "memory");
+                }
             }
             if (!ok) {
                 abort_flag = 1;
                 atomicOr(a.err, UNET_ERR_TIMEOUT);
-                // let every copy already issued land before the CTA leaves (bounded)
-                for (int it = (issued_unconsumed > ST ? issued_unconsumed - ST : 0); it < issued_unconsumed; ++it)
-                    mbar_wait(smem_u32(&full_bar[it % ST]), (uint32_t)(it / ST) & 1u, a.wait_cap, &abort_flag);
+                // let the copies already issued land before the CTA leaves (bounded)
+                for (int j = (it > ST ? it - ST : 0); j < it; ++j)
+                    mbar_wait(smem_u32(&full_bar[j % ST]), (uint32_t)(j / ST) & 1u, a.wait_cap, &abort_flag);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA issuer
             const uint32_t idesc = umma_idesc(NT);
-            int it = 0;
-            for (; it < iters && ok; ++it) {
-                const int s = it % ST;
-                const uint32_t ph = (uint32_t)(it / ST) & 1u;
-                ok = mbar_wait(smem_u32(&full_bar[s]), ph, a.wait_cap, &abort_flag);
+            int it = 0, local = 0;
+            bool ok = true;
+            for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x, ++local) {
+                const int b = local & 1;
+                // the epilogue must have drained this accumulator (its previous use)
+                ok = mbar_wait(smem_u32(&acce_bar[b]), ((uint32_t)(local >> 1) & 1u) ^ 1u, a.wait_cap, &abort_flag);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
-                for (int k = 0; k < KC / 16; ++k) {
-                    const uint64_t ad = umma_desc(sa + k * 32, KC), bd = umma_desc(sb + k * 32, KC);
-                    const uint32_t acc = (it | k) ? 1u : 0u;
-                    asm volatile(
-                        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                        : "memory");
+                const uint32_t d = tmem + (uint32_t)(b * NT);
+                for (int k = 0; k < iters && ok; ++k, ++it) {
+                    const int s = it % ST;
+                    ok = mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(it / ST) & 1u, a.wait_cap, &abort_flag);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
+                    for (int kk = 0; kk < KC / 16; ++kk) {
+                        const uint64_t ad = umma_desc(sa + kk * 32, KC), bd = umma_desc(sb + kk * 32, KC);
+                        const uint32_t acc = (k | kk) ? 1u : 0u;
+                        asm volatile(
+                            "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(smem_u32(&empty_bar[s])) : "memory");
                 }
+                if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(smem_u32(&empty_bar[s])) : "memory");
+                             ::"r"(smem_u32(&accf_bar[b])) : "memory");
             }
             if (!ok) {
                 abort_flag = 1;
                 atomicOr(a.err, UNET_ERR_TIMEOUT);
             }
-            // completion of everything issued so far (also on the abort path) arrives on acc_bar
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&acc_bar)) : "memory");
         }
     } else {  // ---- epilogue, warps 2..5: TMEM lanes 32 (warp % 4) ... + 31
         const int q = warp & 3;
         const int row = q * 32 + lane;  // pixel within the tile
-        const bool done = mbar_wait(smem_u32(&acc_bar), 0, a.wait_cap, &abort_flag);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int py = y0 + row / BW, px = x0 + row % BW;
-        float s1[GN_MAX_GROUPS], s2[GN_MAX_GROUPS];
+        int local = 0;
+        for (int T = blockIdx.x; T < tiles; T += gridDim.x, ++local) {
+            const int b = local & 1;
+            if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)(local >> 1) & 1u, a.wait_cap, &abort_flag)) {
+                abort_flag = 1;
+                if (lane == 0) atomicOr(a.err, UNET_ERR_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const TileGeo g = tile_geo(a, T, mtiles, NT);
+            const int py = g.y0 + row / BW, px = g.x0 + row % BW;
+            float s1[GN_MAX_GROUPS], s2[GN_MAX_GROUPS];
 #pragma unroll
-        for (int g = 0; g < GN_MAX_GROUPS; ++g) s1[g] = s2[g] = 0.f;
-        if (done && !abort_flag) {
+            for (int gg = 0; gg < GN_MAX_GROUPS; ++gg) s1[gg] = s2[gg] = 0.f;
             for (int c0 = 0; c0 < NT; c0 += 16) {
                 uint32_t r[16];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
                     " [%16];"
@@ -224,59 +260,61 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     const float v0 = __uint_as_float(r[2 * j]), v1 = __uint_as_float(r[2 * j + 1]);
                     pk[j] = (uint32_t)f_to_bf16(v0) | ((uint32_t)f_to_bf16(v1) << 16);
                 }
+                uint16_t* dst;
                 if (MODE == CONV3) {
                     const int cg = a.cout / a.groups;  // channels per group (one N tile holds all Cout)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float v = __uint_as_float(r[j]);
-                        const int g = (n0 + c0 + j) / cg;
+                        const int gi = (c0 + j) / cg;
 #pragma unroll
                         for (int gg = 0; gg < GN_MAX_GROUPS; ++gg)
-                            if (gg == g) {
+                            if (gg == gi) {
                                 s1[gg] += v;
                                 s2[gg] = fmaf(v, v, s2[gg]);
                             }
                     }
-                    uint16_t* dst = a.out + ((size_t)(img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + n0 + c0;
-                    uint4* d4 = reinterpret_cast<uint4*>(dst);
-                    d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + c0;
                 } else {  // TCONV: column n0 + c0 + j = sub-pixel s * cout + channel
-                    const int col = n0 + c0, s = col / a.cout, co = col % a.cout;
+                    const int col = g.n0 + c0, s = col / a.cout, co = col % a.cout;
                     const int oy = 2 * py + (s >> 1), ox = 2 * px + (s & 1);
-                    uint16_t* dst = a.out + ((size_t)(img * 2 * a.h + oy) * (2 * a.w) + ox) * a.out_cstride +
-                                    a.out_coff + co;
-                    uint4* d4 = reinterpret_cast<uint4*>(dst);
-                    d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    dst = a.out + ((size_t)(g.img * 2 * a.h + oy) * (2 * a.w) + ox) * a.out_cstride + a.out_coff + co;
                 }
+                uint4* d4 = reinterpret_cast<uint4*>(dst);
+                d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
-        }
-        if (MODE == CONV3) {  // per-CTA group sums: warp butterfly, then a fixed order over the 4 warps
-#pragma unroll
-            for (int g = 0; g < GN_MAX_GROUPS; ++g) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s1[g] += __shfl_xor_sync(0xffffffffu, s1[g], o);
-                    s2[g] += __shfl_xor_sync(0xffffffffu, s2[g], o);
-                }
-            }
+            // the accumulator is drained: hand it back to the MMA issuer (one arrival per warp)
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
             if (lane == 0)
-                for (int g = 0; g < GN_MAX_GROUPS; ++g) {
-                    gn_part[q][2 * g] = s1[g];
-                    gn_part[q][2 * g + 1] = s2[g];
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+            if (MODE == CONV3 && a.partials) {
+                // per warp: partials[((img * groups + g) * tpi + t) * 4 + q] = (sum, sum of squares)
+                for (int gg = 0; gg < a.groups; ++gg) {
+                    float v1 = s1[0], v2 = s2[0];
+#pragma unroll
+                    for (int k = 1; k < GN_MAX_GROUPS; ++k)
+                        if (k == gg) {
+                            v1 = s1[k];
+                            v2 = s2[k];
+                        }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                    }
+                    if (lane == 0) {
+                        float* pp = a.partials + ((((size_t)g.img * a.groups + gg) * tpi + g.t) * 4 + q) * 2;
+                        pp[0] = v1;
+                        pp[1] = v2;
+                    }
                 }
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (MODE == CONV3 && a.partials && tid < 2 * a.groups) {
-        // partials[((img * groups + g) * tiles_per_image + t) * 2 + {0: sum, 1: sum of squares}]
-        // (a CONV3 launch has one N tile holding all Cout channels, so local group = global group)
-        const float v = gn_part[0][tid] + gn_part[1][tid] + gn_part[2][tid] + gn_part[3][tid];
-        const int g = tid >> 1, which = tid & 1;
-        a.partials[(((size_t)img * a.groups + g) * tpi + t) * 2 + which] = v;
-    }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -290,6 +328,18 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 namespace {
 
 int conv_kc(int cin) { return cin % 64 == 0 ? 64 : 32; }
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+    }
+    return n;
+}
 
 int conv_nt(int mode, int cout) { return mode == CONV3 ? cout : (4 * cout < 256 ? 4 * cout : 256); }
 
@@ -334,7 +384,7 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     if (ncols % a.nt) return cudaErrorInvalidValue;
     a.stages = conv_stages(a.kc, a.nt);
     a.tmem_cols = 32;
-    while (a.tmem_cols < a.nt) a.tmem_cols <<= 1;
+    while (a.tmem_cols < 2 * a.nt) a.tmem_cols <<= 1;  // two accumulators
     const int BW = a.w < TM ? a.w : TM, BR = TM / BW;
 
     CUtensorMap mA, mB;
@@ -350,7 +400,12 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
 
     const size_t smem = umma_conv_smem_bytes(mode, a.cin, a.cout);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((long long)a.n * a.h * a.w / TM), (unsigned)(ncols / a.nt));
+    const long long tiles = (long long)a.n * a.h * a.w / TM * (ncols / a.nt);
+    int per_sm = (int)((227 * 1024) / (smem + 2048));  // CTAs that fit next to each other on an SM
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+    if (per_sm * a.tmem_cols > 512) per_sm = 512 / a.tmem_cols;
+    const long long slots = (long long)sm_count() * per_sm;
+    cfg.gridDim = dim3((unsigned)(tiles < slots ? tiles : slots));
     cfg.blockDim = dim3(NTHREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;

@@ -350,6 +350,26 @@ __global__ void gn_apply_out_kernel(const uint16_t* __restrict__ x, int n, int h
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Plausibility of a predicted state: every phi and c finite and inside [lo, hi]; flags[img]
+// is set to 1 on a violation (flags are cleared by the caller).
+__global__ void check_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c, int h, int w,
+                             int pitch, float phi_lo, float phi_hi, float c_lo, float c_hi, int* __restrict__ flags)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int img = blockIdx.y;
+    const float* F = phi[img];
+    const float* C = c[img];
+    int bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < h * w; i += gridDim.x * blockDim.x) {
+        const size_t o = (size_t)(i / w) * pitch + i % w;
+        const float f = F[o], cc = C[o];
+        // written so that NaN fails every comparison
+        bad |= !(f >= phi_lo && f <= phi_hi && cc >= c_lo && cc <= c_hi);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags[img], 1);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 cudaLaunchConfig_t cfg_of(dim3 grid, int threads, cudaStream_t s, cudaLaunchAttribute* attr)
 {
     cudaLaunchConfig_t cfg = {};
@@ -430,6 +450,14 @@ cudaError_t launch_gn_out(const uint16_t* x, int n, int h, int w, const float* s
     cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for((long long)n * h * w, 256)), 256, s, attr);
     return cudaLaunchKernelEx(&cfg, gn_apply_out_kernel, x, n, h, w, stats, gamma, beta, phi, c, rho, pitch,
                               rho_top);
+}
+
+cudaError_t launch_check(const float* const* phi, const float* const* c, int n, int h, int w, int pitch, float phi_lo,
+                         float phi_hi, float c_lo, float c_hi, int* flags, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cfg_of(dim3(32, (unsigned)n), 256, s, attr);
+    return cudaLaunchKernelEx(&cfg, check_kernel, phi, c, h, w, pitch, phi_lo, phi_hi, c_lo, c_hi, flags);
 }
 
 }  // namespace pf

@@ -26,4 +26,7 @@ cudaError_t launch_gn_out(const uint16_t* x, int n, int h, int w, const float* s
                           const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
                           float rho_top, cudaStream_t s);
 
+cudaError_t launch_check(const float* const* phi, const float* const* c, int n, int h, int w, int pitch, float phi_lo,
+                         float phi_hi, float c_lo, float c_hi, int* flags, cudaStream_t s);
+
 }  // namespace pf

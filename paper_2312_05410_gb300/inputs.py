@@ -176,3 +176,58 @@ def ensemble_members(n_runs: int = 64, seed: int = 3, v_range=(0.1, 0.9), c_rang
         out.append(dict(nx=side, ny=side, v_mag=float(v), c_inc=float(ci),
                         spec=FilmSpec(side, side, H, seed=seed * 1000 + k, c_inc=float(ci))))
     return out
+
+
+STREAM_HYBRID = 4
+UNET_CHANNELS = (32, 64, 128, 256)
+UNET_FDIM = 128
+
+
+def unet_weights(seed: int = 0) -> dict:
+    """Seeded He-normal weights of the time-conditioned U-Net, FP32 arrays in PyTorch layouts
+    (conv [Cout, Cin, 3, 3], transposed conv [Cin, Cout, 2, 2]) keyed by layer name.  These are
+    untrained random weights: the network is exercised, not fitted."""
+    g = np.random.default_rng(seed)
+    W = {}
+
+    def he(shape, fan_in):
+        return (g.standard_normal(shape) * math.sqrt(2.0 / fan_in)).astype(np.float32)
+
+    W["mlp_w0"] = he((UNET_FDIM, 1), 1)
+    W["mlp_b0"] = (g.standard_normal(UNET_FDIM) * 0.5).astype(np.float32)
+    W["mlp_w1"] = he((UNET_FDIM, UNET_FDIM), UNET_FDIM)
+    W["mlp_b1"] = (g.standard_normal(UNET_FDIM) * 0.1).astype(np.float32)
+    W["mlp_w2"] = he((UNET_FDIM, UNET_FDIM), UNET_FDIM)
+    W["mlp_b2"] = (g.standard_normal(UNET_FDIM) * 0.1).astype(np.float32)
+    for p, c in enumerate(UNET_CHANNELS, 1):
+        W[f"proj{p}"] = (g.standard_normal((c, UNET_FDIM)) / math.sqrt(UNET_FDIM)).astype(np.float32)
+    cin = 3
+    for p, c in enumerate(UNET_CHANNELS, 1):
+        W[f"enc{p}"] = he((c, cin, 3, 3), 9 * cin)
+        cin = c
+    W["dec4"] = he((256, 256, 3, 3), 9 * 256)
+    W["dec3"] = he((128, 256, 3, 3), 9 * 256)
+    W["dec2"] = he((64, 128, 3, 3), 9 * 128)
+    W["dec1"] = he((32, 64, 3, 3), 9 * 64)
+    W["up4"] = he((256, 128, 2, 2), 256)
+    W["up3"] = he((128, 64, 2, 2), 128)
+    W["up2"] = he((64, 32, 2, 2), 64)
+    W["out"] = he((2, 32, 3, 3), 9 * 32)
+    for name, c in (("enc1", 32), ("enc2", 64), ("enc3", 128), ("enc4", 256), ("dec4", 256), ("dec3", 128),
+                    ("dec2", 64), ("dec1", 32), ("out", 2)):
+        W[name + "_gamma"] = (1.0 + 0.1 * g.standard_normal(c)).astype(np.float32)
+        W[name + "_beta"] = (0.1 * g.standard_normal(c)).astype(np.float32)
+    return W
+
+
+def hybrid_members(n_runs: int = 16, side: int = 256, seed: int = 5, v_range=(0.1, 0.9), c_range=(0.3, 0.7),
+                   H: float = 16.0) -> list[dict]:
+    """Runs of the hybrid DNS / U-Net workload: equal grids, seeded deposition rate and composition."""
+    u = uniform01(seed, STREAM_HYBRID, 2 * n_runs).reshape(n_runs, 2)
+    out = []
+    for k in range(n_runs):
+        v = v_range[0] + (v_range[1] - v_range[0]) * u[k, 0]
+        ci = c_range[0] + (c_range[1] - c_range[0]) * u[k, 1]
+        out.append(dict(nx=side, ny=side, v_mag=float(v), c_inc=float(ci),
+                        spec=FilmSpec(side, side, H, seed=seed * 1000 + k, c_inc=float(ci))))
+    return out

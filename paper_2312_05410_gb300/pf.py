@@ -104,6 +104,8 @@ def _load():
     L.pf_unet_jump.argtypes = [vp, C.c_int, pp, pp, pp, C.c_int, C.c_double, C.c_double]
     L.pf_unet_jump.restype = C.c_int
     L.pf_unet_sync.argtypes, L.pf_unet_sync.restype = [vp], C.c_int
+    L.pf_unet_check.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, ip]
+    L.pf_unet_check.restype = C.c_int
     L.pf_unet_buffer.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(C.c_int)]
     L.pf_unet_buffer.restype = C.c_int
     L.pf_unet_destroy.argtypes, L.pf_unet_destroy.restype = [vp], C.c_int
@@ -500,7 +502,7 @@ def conv3x3_bf16(x, w_dev, groups: int, out=None, out_coff: int = 0, partials=No
     if out is None:
         out = torch.empty((n, h, wd, cout), dtype=torch.bfloat16, device=x.device)
     if partials is None:
-        partials = torch.zeros((n, groups, h * wd // 128, 2), dtype=torch.float32, device=x.device)
+        partials = torch.zeros((n, groups, h * wd // 128, 4, 2), dtype=torch.float32, device=x.device)
     if err is None:
         err = torch.zeros(1, dtype=torch.int32, device=x.device)
     s = (stream or torch.cuda.current_stream()).cuda_stream
@@ -563,6 +565,12 @@ class UNet:
 
     def sync(self):
         _ucheck(lib.pf_unet_sync(self.h))
+
+    def check(self, phi_range=(-1.5, 1.5), c_range=(-0.5, 1.5)) -> list[bool]:
+        """Per run: is the last jump's prediction finite and inside the given ranges?  (Synchronises.)"""
+        ok = (C.c_int * self.batch)()
+        _ucheck(lib.pf_unet_check(self.h, phi_range[0], phi_range[1], c_range[0], c_range[1], ok))
+        return [bool(v) for v in ok]
 
     def buffer(self, name: str):
         """Activation buffer `name` (see UNET_BUFFERS) as a BF16 NHWC tensor view of the workspace."""

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 from oracle import unet_ref as U
+from paper_2312_05410_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -64,7 +65,7 @@ def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
     # group sums and sums of squares of the FP32 results, per 128-pixel tile
     p = part.cpu().numpy().astype(np.float64)
     cg = cout // groups
-    tot = p.sum(axis=2)
+    tot = p.sum(axis=(2, 3))
     for i in range(n):
         for gi in range(groups):
             v = ref[i, gi * cg:(gi + 1) * cg]
@@ -113,7 +114,7 @@ def test_unsupported_shapes_are_rejected(pf):
 def _unet_case(pf, n=2, H=128, seed=0, tau=0.5):
     import oracle as O
     from paper_2312_05410_gb300 import inputs as I
-    W = U.init_weights(seed)
+    W = I.unet_weights(seed)
     p = O.with_dt(I.default_params())
     states = [I.film_state(I.FilmSpec(H, H, 40.0 + 10 * k, seed=k), p) for k in range(n)]
     fields = [tuple(pf.device_fields(st)) for st in states]

@@ -13,7 +13,8 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-from oracle import unet_ref as U  # noqa: E402
+from oracle import unet_ref as U
+from paper_2312_05410_gb300 import inputs as I  # noqa: E402
 
 
 def test_bf16_rounding_matches_the_format():
@@ -96,7 +97,7 @@ def test_gelu_is_the_tanh_form_and_close_to_the_erf_form():
 
 
 def test_mlp_basis_matches_a_loop_restatement():
-    W = U.init_weights(5)
+    W = I.unet_weights(5)
     tau = 0.37
     w0, b0, w1, b1, w2, b2 = (W[k].astype(np.float64).tolist() for k in
                               ("mlp_w0", "mlp_b0", "mlp_w1", "mlp_b1", "mlp_w2", "mlp_b2"))
@@ -123,7 +124,7 @@ def _rel(a, b):
 
 
 def test_network_shapes_and_output_normalisation():
-    W = U.init_weights(0)
+    W = I.unet_weights(0)
     W["out_gamma"][:] = 1.0
     W["out_beta"][:] = 0.0
     taps = {}
@@ -137,7 +138,7 @@ def test_network_shapes_and_output_normalisation():
 
 
 def test_network_invariants_of_the_normalisation_and_conditioning():
-    W = U.init_weights(0)
+    W = I.unet_weights(0)
     x = _net_input()
     y = U.forward(W, x, 0.25)
     # the first convolution is linear and GN follows it: an input scale of 2 (exact in BF16) drops out
