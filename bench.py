@@ -334,12 +334,19 @@ class HybridRun:
                 self.fallbacks += 1
 
     def final_diag(self):
+        """[relative L2 of phi, of c, mean relative L2 of the S2 map] of the hybrid final states
+        against the plain-DNS final states (fields restricted to the nx model columns)."""
         self.net.sync()
+        nx = self.net.nx
         err = []
         for q in range(2):
-            num = sum(float(((a[q] - b[q]) ** 2).sum()) for a, b in zip(self.ens.fields, self._dns_runs()))
-            den = sum(float((b[q] ** 2).sum()) for b in self._dns_runs())
+            num = sum(float(((a[q][:, :nx] - b[q][:, :nx]) ** 2).sum()) for a, b in zip(self.ens.fields, self._dns_runs()))
+            den = sum(float((b[q][:, :nx] ** 2).sum()) for b in self._dns_runs())
             err.append((num / den) ** 0.5)
+        s2 = [self.pf.s2_rel_l2(self.pf.s2_counts(b[0], b[1], nx, nx, 32, self.stream),
+                                self.pf.s2_counts(a[0], a[1], nx, nx, 32, self.stream))
+              for a, b in zip(self.ens.fields, self._dns_runs())]
+        err.append(sum(s2) / len(s2))
         return err
 
     def _dns_runs(self):
@@ -468,6 +475,7 @@ def run_native(args):
         line["hybrid"] = {"hybrid_s": hyb_s, "plain_dns_s": R.dns_s, "speedup_vs_dns": R.dns_s / hyb_s,
                           "jumps": R.cycles, "dns_fallbacks": R.fallbacks,
                           "rel_l2_vs_dns": {"phi": final_diag[0], "c": final_diag[1]},
+                          "s2_rel_l2_vs_dns": final_diag[2],
                           "jump_ms": R.jump_s * 1e3, "jump_tflops": jump_tf,
                           "jump_tensor_frac_of_bf16_peak": jump_tf / peaks["bf16_tflops"],
                           "weights": "seeded, untrained (training is not built): jumps that fail the "

@@ -337,6 +337,18 @@ int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels);
 int pf_unet_destroy(pf_unet* u);
 const char* pf_unet_last_error(void);
 
+/*
+ * Two-point autocorrelation of the solid A phase ("Autocorrelations", Results; the
+ * hybrid solver's error metric, "Error metrics", Methods): with I(x) = 1 where
+ * phi > 0 and c > 0.5 (FP32 comparisons), counts[ry + R][rx + R] = sum_x I(x) I(x + r)
+ * over periodic shifts r = (rx, ry), |rx|, |ry| <= R; S2(r) = counts / (nx ny).
+ * phi, c: device FP32 fields with row pitch `pitch`; scratch: device, nx*ny bytes;
+ * counts: device int64 [(2R+1)^2].  R <= 127 and 2R+1 <= min(nx, ny).  Integer
+ * arithmetic (exact).  Asynchronous on `stream`; PF_ERR_ARG / PF_ERR_CUDA.
+ */
+int pf_s2_counts(const float* phi, const float* c, int nx, int ny, int pitch, int R, unsigned char* scratch,
+                 long long* counts, void* stream);
+
 const char* pf_strerror(int code);
 const char* pf_last_error(void);
 

@@ -109,6 +109,8 @@ def _load():
     L.pf_unet_buffer.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(C.c_int)]
     L.pf_unet_buffer.restype = C.c_int
     L.pf_unet_destroy.argtypes, L.pf_unet_destroy.restype = [vp], C.c_int
+    L.pf_s2_counts.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+    L.pf_s2_counts.restype = C.c_int
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
     L.pf_last_error.argtypes, L.pf_last_error.restype = [], C.c_char_p
     return L
@@ -594,3 +596,20 @@ class UNet:
             self.close()
         except Exception:
             pass
+
+
+def s2_counts(phi, c, nx: int, ny: int, R: int, stream=None):
+    """S2 pair counts [2R+1, 2R+1] of the solid A phase of (phi, c) ((ny, pitch) FP32 CUDA tensors)."""
+    import torch
+    scratch = torch.empty(nx * ny, dtype=torch.uint8, device=phi.device)
+    counts = torch.empty((2 * R + 1, 2 * R + 1), dtype=torch.int64, device=phi.device)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib.pf_s2_counts(phi.data_ptr(), c.data_ptr(), nx, ny, phi.shape[1], R, scratch.data_ptr(),
+                            counts.data_ptr(), s))
+    return counts
+
+
+def s2_rel_l2(counts_true, counts_pred) -> float:
+    """Relative L2 distance of two S2 maps (the normalisation by the cell count cancels)."""
+    a = counts_true.double()
+    return float((a - counts_pred.double()).norm() / a.norm())

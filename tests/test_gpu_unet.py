@@ -153,3 +153,16 @@ def test_unet_jump_matches_the_reference_network(pf):
         assert e_phi <= 2e-2 and e_c <= 2e-2
         np.testing.assert_array_equal(rho, (np.float32(1.0) * (np.float32(1.0) - phi.astype(np.float32))) * np.float32(0.5))
     net.close()
+
+
+def test_s2_counts_are_bit_exact(pf):
+    from oracle import s2_ref as S
+    p = None
+    g = np.random.default_rng(3)
+    for (nx, ny, R) in ((256, 256, 32), (96, 40, 7), (33, 65, 16)):
+        phi = np.tanh(g.standard_normal((ny, nx))).astype(np.float32)
+        c = g.random((ny, nx)).astype(np.float32)
+        f = pf.device_fields([phi, c])
+        got = pf.s2_counts(f[0], f[1], nx, ny, R).cpu().numpy()
+        np.testing.assert_array_equal(got, S.s2_counts(phi, c, R))
+    del p
