@@ -272,7 +272,16 @@ class HybridRun:
         self.stream = self.ens.stream
         self.fields = [t for run in self.ens.fields for t in run]
         side = W["side"]
-        self.net = pf.UNet(I.unet_weights(0), W["n_runs"], side, side, stream=self.stream)
+        wpath = W.get("unet_weights")
+        if wpath:
+            with np.load(wpath) as z:
+                weights = {k: z[k] for k in z.files}
+            self.weights_desc = f"trained on GPU-DNS trajectories ({os.path.basename(wpath)})"
+        else:
+            weights = I.unet_weights(0)
+            self.weights_desc = ("seeded, untrained: jumps that fail the plausibility check fall back to DNS "
+                                 "(train with python -m paper_2312_05410_gb300.train_unet, pass --unet-weights)")
+        self.net = pf.UNet(weights, W["n_runs"], side, side, stream=self.stream)
         self.cells = W["n_runs"] * side * side
         self.nsteps = W["steps"]
         self.stretch, self.jump_steps = W["dns_stretch"], W["jump"]
@@ -478,8 +487,7 @@ def run_native(args):
                           "s2_rel_l2_vs_dns": final_diag[2],
                           "jump_ms": R.jump_s * 1e3, "jump_tflops": jump_tf,
                           "jump_tensor_frac_of_bf16_peak": jump_tf / peaks["bf16_tflops"],
-                          "weights": "seeded, untrained (training is not built): jumps that fail the "
-                                     "plausibility check fall back to DNS"}
+                          "weights": R.weights_desc}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -566,6 +574,8 @@ def main():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="paper512")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--unet-weights", default="",
+                    help="hybrid256: weights .npz written by paper_2312_05410_gb300.train_unet")
     ap.add_argument("--timesteps", type=int, default=0,
                     help="override the workload's time steps per run (short runs for profiling only)")
     args = ap.parse_args()
@@ -573,6 +583,8 @@ def main():
         args.warmup = 3
     if args.timesteps > 0:
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], steps=args.timesteps)
+    if args.unet_weights:
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], unet_weights=args.unet_weights)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -291,9 +291,12 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
  *   - encoder z1 = block(x), zp = block(down(z_{p-1})), with block = GELU(GN(conv3x3));
  *   - conditioning zc_p = z_p * (W_p f(tau)), where f is the sin MLP;
  *   - decoder d3 = up(block(zc4)), d2 = up(block(zc3 ++ d3)), d1 = up(block(zc2 ++ d2));
- *   - output (phi, c) = GN(conv3x3(block(zc1 ++ d1))).
- * Channels are 32-64-128-256, with 8 groups in the hidden normalisations and one
- * group per output channel.  Weights and activations are stored as BF16 and
+ *   - output (phi, c) += gamma * conv3x3(block(zc1 ++ d1)) + beta, a per-channel
+ *     affine increment of the input fields.  The paper applies a final group
+ *     normalisation to its single normalised composition field.  Here the two
+ *     predicted fields have a per-sample mean and spread that vary with film
+ *     thickness and incident composition, so the increment form is used instead.
+ * Channels are 32-64-128-256, with 8 groups in the hidden normalisations.  Weights and activations are stored as BF16 and
  * accumulated in FP32; the 3x3 and transposed convolutions of levels 2-4 and of
  * the decoder run on the tensor cores (pf_conv3x3_bf16 / pf_tconv2x2_bf16).
  *
@@ -308,13 +311,14 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
  *   14-17 dec4 [256][256][3][3], dec3 [128][256][3][3], dec2 [64][128][3][3], dec1 [32][64][3][3]
  *   18-20 up4 [256][128][2][2], up3 [128][64][2][2], up2 [64][32][2][2]  ([Cin][Cout][dy][dx])
  *   21    out [2][32][3][3]
- *   22-39 (gamma, beta) of enc1..enc4, dec4..dec1, out.
- *   They are rounded to BF16, except the MLP, projections (FP64) and GN affine
- *   parameters (FP32), and copied into the workspace (synchronises once).
+ *   22-39 (gamma, beta) of enc1..enc4, dec4..dec1 (group normalisation) and of out
+ *   (the output affine).  Convolution weights are rounded to BF16; the MLP and
+ *   projections are kept in FP64 and the affine parameters in FP32.  Everything is
+ *   copied into the workspace (synchronises once).
  *   work: 256-byte aligned.
- * pf_unet_jump: replaces (phi[i], c[i]) of runs i < n (n == batch; device FP32
- *   fields ny x nx with row pitch `pitch` floats) by the prediction for jump
- *   length tau.  It sets rho[i] = rho_top (1 - phi) / 2, the initial-state vapor
+ * pf_unet_jump: advances (phi[i], c[i]) of runs i < n (n == batch; device FP32
+ *   fields ny x nx with row pitch `pitch` floats) in place by the predicted increment
+ *   for jump length tau.  It sets rho[i] = rho_top (1 - phi) / 2, the initial-state vapor
  *   profile; the surrogate does not predict rho.  Asynchronous on the handle's
  *   stream, about 30 kernel launches.
  * pf_unet_sync: synchronise; PF_ERR_TIMEOUT if a tensor-core pipeline wait ran out.
@@ -322,8 +326,8 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
  *   gate for its plain-DNS fallback.  ok[i] (host, n ints) is 1 if every phi and c
  *   of run i is finite and inside [phi_lo, phi_hi] x [c_lo, c_hi], else 0.  Synchronises.
  * pf_unet_buffer: device pointer and channel count of activation buffer `which`
- *   (0-15: pre1, cat1, p1, pre2, cat2, p2, pre3, cat3, p3, pre4, zc4, h4, h3, h2,
- *   h1, pre_out; NHWC BF16 at level resolution), for inspection.
+ *   (0-14: pre1, cat1, p1, pre2, cat2, p2, pre3, cat3, p3, pre4, zc4, h4, h3, h2,
+ *   h1; NHWC BF16 at level resolution), for inspection.
  */
 typedef struct pf_unet pf_unet;
 size_t pf_unet_workspace_size(int batch, int nx, int ny);

@@ -19,7 +19,11 @@ the paper is silent are marked READING):
   encoder    z1 = block(x), zp = block(down(z_{p-1})), p = 2, 3, 4       (unconditioned chain)
   condition  zc_p = z_p * (W_p f(dt))  (per-channel product, p = 1..4)
   decoder    d3 = up(block(zc4)); d2 = up(block(zc3 ++ d3)); d1 = up(block(zc2 ++ d2))
-  output     y  = GN(conv(block(zc1 ++ d1)))   (READING: GN with one group per output channel)
+  output     y  = x_fields + gamma * conv(block(zc1 ++ d1)) + beta
+             (READING: the paper writes GN(conv(...)) for its single normalised composition field; here
+             the network predicts two fields whose per-sample mean and spread vary with the film's
+             thickness and the incident composition, which a final normalisation would pin, so the
+             last convolution instead gives a per-channel affine increment added to the input fields)
 
 Channels 32-64-128-256.  Input x = (phi, c, dt / dt_ref) planes (READING: the two
 fields plus a plane holding the jump length; the paper feeds lb = 3 frames of c).
@@ -131,6 +135,7 @@ def up(x: torch.Tensor, w) -> torch.Tensor:
 def forward(W: dict, x, tau: float, taps: dict | None = None) -> np.ndarray:
     """Network output for x [N, 3, H, W] (float array; rounded to BF16 here); returns [N, 2, H, W] FP64.
     If `taps` is a dict it receives the intermediate tensors by name."""
+    x_fields = _t(np.asarray(x, dtype=np.float32)[:, :OUT_CH])  # the residual adds the FP32 input fields
     x = _rb(_t(x))
     s = [_t(bf16(v)) for v in scales(W, tau)]     # conditioning factors are stored as BF16
     z1 = block(x, W, "enc1")
@@ -142,10 +147,11 @@ def forward(W: dict, x, tau: float, taps: dict | None = None) -> np.ndarray:
     d2 = up(block(torch.cat([zc[2], d3], 1), W, "dec3"), W["up3"])
     d1 = up(block(torch.cat([zc[1], d2], 1), W, "dec2"), W["up2"])
     h1 = block(torch.cat([zc[0], d1], 1), W, "dec1")
-    y = block(h1, W, "out", groups=OUT_CH, act=False)
+    inc = conv3x3(h1, W["out"])
+    y = x_fields + inc * _t(W["out_gamma"])[None, :, None, None] + _t(W["out_beta"])[None, :, None, None]
     if taps is not None:
         taps.update(z1=z1, z2=z2, z3=z3, z4=z4, zc1=zc[0], zc2=zc[1], zc3=zc[2], zc4=zc[3], d3=d3, d2=d2,
-                    d1=d1, h1=h1, y=y)
+                    d1=d1, h1=h1, inc=inc, y=y)
     return y.numpy()
 
 

@@ -132,7 +132,7 @@ UnetLayout unet_layout(int n, int h, int w)
         for (int q = 0; q < 2; ++q) L.gb[k][q] = take(sizeof(float) * gbc[k]);
     const size_t P0 = (size_t)n * h * w, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
     const size_t elems[16] = {P0 * 32, P0 * 64, P1 * 32, P1 * 64, P1 * 128, P2 * 64, P2 * 128, P2 * 256,
-                              P3 * 128, P3 * 256, P3 * 256, P3 * 256, P2 * 128, P1 * 64, P0 * 32, P0 * 2};
+                              P3 * 128, P3 * 256, P3 * 256, P3 * 256, P2 * 128, P1 * 64, P0 * 32, 0};
     for (int k = 0; k < 16; ++k) L.act[k] = take(2 * elems[k]);
     L.partials = take(sizeof(float) * (size_t)n * 8 * (h * (size_t)w / 128) * 4 * 2);
     L.stats = take(sizeof(float) * (size_t)n * 8 * 2);
@@ -367,10 +367,9 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H2), H / 2, W / 2, 64, u->at<uint16_t>(L.wt[2]), 32, act(A_CAT1), 64, 32, false);
     if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT1), H, W, 64, u->at<uint16_t>(L.wc[6]), 32, act(A_PRE1), 32, 0, true);
     ck(pf::launch_gn_dec(act(A_PRE1), n, H, W, 32, G, stats, gam(7), bet(7), act(A_H1), s), "decoder 1");
-    // ---- output: conv 32 -> 2, GN per channel, into the DNS fields
-    ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), act(A_PREO), part, s), "output conv");
-    ck(pf::launch_gn_stats(part, n, 2, H * W / 128, (double)H * W, stats, s), "output statistics");
-    ck(pf::launch_gn_out(act(A_PREO), n, H, W, stats, gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch, (float)rho_top, s),
+    // ---- output: conv 32 -> 2 as an affine increment of the DNS fields (and the vapor reset)
+    ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch,
+                           (float)rho_top, s),
        "output");
     return rc;
 }
@@ -406,7 +405,7 @@ int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double 
 
 int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels)
 {
-    if (!u || !ptr || !channels || which < 0 || which > 15) return ufail(PF_ERR_ARG, "bad buffer query");
+    if (!u || !ptr || !channels || which < 0 || which > 14) return ufail(PF_ERR_ARG, "bad buffer query");
     const int ch[16] = {32, 64, 32, 64, 128, 64, 128, 256, 128, 256, 256, 256, 128, 64, 32, 2};
     *ptr = u->base + u->L.act[which];
     *channels = ch[which];

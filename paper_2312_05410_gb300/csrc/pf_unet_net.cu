@@ -6,10 +6,9 @@
 //                   per-level conditioning factors W_p f(dt), in FP64, stored as BF16 values
 //   in_conv_kernel  the first 3x3 convolution (3 -> 32 channels) straight from the DNS
 //                   fields (phi, c and a plane holding dt / dt_ref), with its group sums
-//   out_conv_kernel the last 3x3 convolution (32 -> 2), with its per-channel sums
+//   out_conv_kernel the last 3x3 convolution (32 -> 2) as an affine increment of the DNS fields
 //   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums, FP64, fixed order
-//   gn_apply_*      GN + GELU (+ conditioning product, + 2x2 max pooling) on stored BF16
-//                   values; the last one writes the predicted phi and c into the DNS fields
+//   gn_apply_*      GN + GELU (+ conditioning product, + 2x2 max pooling) on stored BF16 values
 //
 // Storage follows the precision model of the reference: every stored activation is BF16
 // (round to nearest even), sums are FP32 (FP64 for the statistics), products of BF16 values
@@ -144,13 +143,15 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Last convolution: 3x3, 32 -> 2 channels, from BF16 NHWC [n][h][w][32]; per-channel sums.
+// Output: the last convolution (3x3, 32 -> 2) of BF16 NHWC [n][h][w][32], as a per-channel affine
+// increment added to the FP32 fields in place: phi += g0 conv0 + b0, c += g1 conv1 + b1; the vapor
+// density is reset to its initial-state profile rho_top (1 - phi) / 2.
 __global__ void __launch_bounds__(TPB)
 out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __restrict__ wgt /* [9][32][2] */,
-                uint16_t* __restrict__ out, float* __restrict__ partials)
+                const float* __restrict__ gamma, const float* __restrict__ beta, float* const* __restrict__ phi,
+                float* const* __restrict__ c, float* const* __restrict__ rho, int pitch, float rho_top)
 {
     __shared__ float ws[9 * 32 * 2];
-    __shared__ float red[4];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = threadIdx.x; i < 9 * 32 * 2; i += TPB) ws[i] = wgt[i];
     __syncthreads();
@@ -177,12 +178,11 @@ out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __re
                 }
             }
         }
-    reinterpret_cast<uint32_t*>(out)[(size_t)img * h * w + p] = (uint32_t)to_bf(a0) | ((uint32_t)to_bf(a1) << 16);
-    const float s[4] = {a0, a0 * a0, a1, a1 * a1};
-    for (int k = 0; k < 4; ++k) {
-        const float v = block_sum128(s[k], red);
-        if (threadIdx.x == 0) partials[(((size_t)img * 2 + (k >> 1)) * tpi + t) * 2 + (k & 1)] = v;
-    }
+    const size_t o = (size_t)y * pitch + x;
+    const float f = phi[img][o] + fmaf(gamma[0], a0, beta[0]);
+    c[img][o] = c[img][o] + fmaf(gamma[1], a1, beta[1]);
+    phi[img][o] = f;
+    rho[img][o] = rho_top * (1.0f - f) * 0.5f;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
@@ -324,32 +324,6 @@ __global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pi
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Output: (phi, c) = GN(x) with one group per channel, written as FP32 into the DNS fields; the
-// vapor density is reset to its initial-state profile rho_top (1 - phi) / 2.
-__global__ void gn_apply_out_kernel(const uint16_t* __restrict__ x, int n, int h, int w,
-                                    const float* __restrict__ stats, const float* __restrict__ gamma,
-                                    const float* __restrict__ beta, float* const* __restrict__ phi,
-                                    float* const* __restrict__ c, float* const* __restrict__ rho, int pitch,
-                                    float rho_top)
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const long long total = (long long)n * h * w;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int img = (int)(i / ((long long)h * w));
-        const int p = (int)(i % ((long long)h * w)), yy = p / w, xx = p % w;
-        const uint32_t u = reinterpret_cast<const uint32_t*>(x)[i];
-        const float v0 = bf((uint16_t)(u & 0xffffu)), v1 = bf((uint16_t)(u >> 16));
-        const float f = (v0 - stats[4 * img]) * stats[4 * img + 1] * gamma[0] + beta[0];
-        const float cc = (v1 - stats[4 * img + 2]) * stats[4 * img + 3] * gamma[1] + beta[1];
-        const size_t o = (size_t)yy * pitch + xx;
-        phi[img][o] = f;
-        c[img][o] = cc;
-        rho[img][o] = rho_top * (1.0f - f) * 0.5f;
-    }
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Plausibility of a predicted state: every phi and c finite and inside [lo, hi]; flags[img]
 // is set to 1 on a violation (flags are cleared by the caller).
 __global__ void check_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c, int h, int w,
@@ -406,12 +380,13 @@ cudaError_t launch_in_conv(const float* const* phi, const float* const* c, int p
     return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, pitch, h, w, tau, wgt, out, partials);
 }
 
-cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, uint16_t* out, float* partials,
-                            cudaStream_t s)
+cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, const float* gamma,
+                            const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
+                            float rho_top, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
-    return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, out, partials);
+    return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, gamma, beta, phi, c, rho, pitch, rho_top);
 }
 
 cudaError_t launch_gn_stats(const float* partials, int n, int groups, int tpi, double count, float* stats,
@@ -440,16 +415,6 @@ cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, int gro
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(pixels * (C / 8), 256)), 256, s, attr);
     return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, pixels, C, h * w, groups, stats, gamma, beta, y);
-}
-
-cudaError_t launch_gn_out(const uint16_t* x, int n, int h, int w, const float* stats, const float* gamma,
-                          const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
-                          float rho_top, cudaStream_t s)
-{
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for((long long)n * h * w, 256)), 256, s, attr);
-    return cudaLaunchKernelEx(&cfg, gn_apply_out_kernel, x, n, h, w, stats, gamma, beta, phi, c, rho, pitch,
-                              rho_top);
 }
 
 cudaError_t launch_check(const float* const* phi, const float* const* c, int n, int h, int w, int pitch, float phi_lo,

@@ -533,8 +533,8 @@ UNET_WEIGHT_NAMES = (["mlp_w0", "mlp_b0", "mlp_w1", "mlp_b1", "mlp_w2", "mlp_b2"
                      + [f"{n}_{g}" for n in ("enc1", "enc2", "enc3", "enc4", "dec4", "dec3", "dec2", "dec1", "out")
                         for g in ("gamma", "beta")])
 UNET_BUFFERS = ("pre1", "cat1", "p1", "pre2", "cat2", "p2", "pre3", "cat3", "p3", "pre4", "zc4", "h4", "h3", "h2",
-                "h1", "pre_out")
-_UNET_LEVEL = (0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 2, 1, 0, 0)
+                "h1")
+_UNET_LEVEL = (0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 2, 1, 0)
 
 
 class UNet:

@@ -1,0 +1,163 @@
+"""Train the time-conditioned U-Net on trajectories that the GPU DNS generates.
+
+    python -m paper_2312_05410_gb300.train_unet --out weights.npz [--runs 32] [--budget 300]
+
+This is offline tooling, not the solver's path.
+- **Data.** The batched ensemble kernel advances `runs` seeded films of 256 x 256 cells.
+  A snapshot of (phi, c) is kept every 2000 steps, 50 snapshots per run, like the
+  paper's 50-snapshot trajectories ("Dataset").
+- **Training.** Each pair of consecutive snapshots is a sample with jump length
+  tau = 1 (2000 steps).  The network is the one the inference kernels compute
+  (pf_unet_jump), written a second time with PyTorch operations so that autograd
+  can differentiate it.  Training uses Adam on the relative squared error of both
+  fields ("Training of the network", "Error metrics").
+- **Output.** The weights are written under the names pf.UNet expects.  Prediction
+  with them runs only in the hand-written BF16 tensor-core kernels.
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import time
+
+import numpy as np
+
+from . import inputs as I
+
+CH = I.UNET_CHANNELS
+FDIM = I.UNET_FDIM
+
+
+def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 2000, snapshots: int = 50):
+    """(phi, c) snapshots [snapshots + 1, runs, 2, side, side] on the GPU, from seeded films."""
+    import torch
+
+    ms = []
+    for m in I.hybrid_members(runs, side, seed=seed):
+        p = I.default_params(v_mag=m["v_mag"])
+        p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
+        ms.append((p, *I.film_state(m["spec"], p)))
+    ens = pf.Ensemble(ms)
+    ens.set_tile(0)
+
+    def grab():
+        return torch.stack([torch.stack([run[0][:, :side], run[1][:, :side]]) for run in ens.fields]).clone()
+
+    out = [grab()]
+    for _ in range(snapshots):
+        ens.step(every)
+        out.append(grab())
+    torch.cuda.synchronize()
+    ens.close()
+    return torch.stack(out)
+
+
+def make_model(seed: int = 0):
+    import torch
+    import torch.nn.functional as F
+
+    class Net(torch.nn.Module):
+        def __init__(self):
+            super().__init__()
+            W = I.unet_weights(seed)
+            W["out_gamma"] = np.full(2, 0.1, np.float32)  # start close to the identity jump
+            W["out_beta"] = np.zeros(2, np.float32)
+            self.p = torch.nn.ParameterDict({k: torch.nn.Parameter(torch.from_numpy(v.copy())) for k, v in W.items()})
+
+        def block(self, x, name):
+            y = F.conv2d(x, self.p[name], padding=1)
+            y = F.group_norm(y, 8, self.p[name + "_gamma"], self.p[name + "_beta"], eps=1e-5)
+            return F.gelu(y, approximate="tanh")
+
+        def forward(self, x, tau):
+            p = self.p
+            t = torch.full((1, 1), float(tau), device=x.device)
+            h = torch.sin(t @ p["mlp_w0"].t() + p["mlp_b0"])
+            h = torch.sin(h @ p["mlp_w1"].t() + p["mlp_b1"])
+            f = (h @ p["mlp_w2"].t() + p["mlp_b2"])[0]
+            s = [p[f"proj{k}"] @ f for k in range(1, 5)]
+            z1 = self.block(x, "enc1")
+            z2 = self.block(F.max_pool2d(z1, 2), "enc2")
+            z3 = self.block(F.max_pool2d(z2, 2), "enc3")
+            z4 = self.block(F.max_pool2d(z3, 2), "enc4")
+            zc = [z * sp[None, :, None, None] for z, sp in zip((z1, z2, z3, z4), s)]
+            d3 = F.conv_transpose2d(self.block(zc[3], "dec4"), p["up4"], stride=2)
+            d2 = F.conv_transpose2d(self.block(torch.cat([zc[2], d3], 1), "dec3"), p["up3"], stride=2)
+            d1 = F.conv_transpose2d(self.block(torch.cat([zc[1], d2], 1), "dec2"), p["up2"], stride=2)
+            h1 = self.block(torch.cat([zc[0], d1], 1), "dec1")
+            inc = F.conv2d(h1, p["out"], padding=1)
+            return x[:, :2] + inc * p["out_gamma"][None, :, None, None] + p["out_beta"][None, :, None, None]
+
+    return Net()
+
+
+def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float = 1e-3, seed: int = 0,
+          log=print) -> dict:
+    import torch
+
+    torch.manual_seed(seed)
+    data = generate(pf, runs)                      # [51, runs, 2, H, W]
+    S, R = data.shape[0] - 1, data.shape[1]
+    pairs = [(k, r) for k in range(S) for r in range(R)]
+    val = [(k, r) for (k, r) in pairs if r == R - 1]  # the last run is held out
+    trn = [(k, r) for (k, r) in pairs if r != R - 1]
+    net = make_model(seed).cuda()
+    opt = torch.optim.Adam(net.parameters(), lr=lr)
+    sched_T = None
+
+    def sample(idx):
+        x = torch.stack([torch.cat([data[k, r], torch.ones_like(data[k, r, :1])]) for k, r in idx])
+        y = torch.stack([data[k + 1, r] for k, r in idx])
+        return x, y
+
+    def loss_fn(pred, y):
+        return sum(((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(2))
+
+    g = np.random.default_rng(seed)
+    t0 = time.time()
+    step = 0
+    epoch = 0
+    while time.time() - t0 < budget_s:
+        order = g.permutation(len(trn))
+        for i in range(0, len(order) - batch + 1, batch):
+            frac = min(1.0, (time.time() - t0) / budget_s)
+            for gr in opt.param_groups:
+                gr["lr"] = lr * 0.5 * (1 + math.cos(math.pi * frac))  # cosine decay over the budget
+            x, y = sample([trn[j] for j in order[i:i + batch]])
+            with torch.autocast("cuda", dtype=torch.bfloat16):
+                pred = net(x, 1.0)
+            loss = loss_fn(pred.float(), y)
+            opt.zero_grad(set_to_none=True)
+            loss.backward()
+            opt.step()
+            step += 1
+            if time.time() - t0 > budget_s:
+                break
+        epoch += 1
+        with torch.no_grad(), torch.autocast("cuda", dtype=torch.bfloat16):
+            x, y = sample(val)
+            v = float(loss_fn(net(x, 1.0).float(), y)) / 2
+        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss) / 2:.3e} "
+            f"val rel-sq {v:.3e} (rel L2 {math.sqrt(v):.3e})")
+    del sched_T
+    return {k: v.detach().float().cpu().numpy() for k, v in net.p.items()}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--runs", type=int, default=32)
+    ap.add_argument("--budget", type=float, default=300.0)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args()
+    from . import build as B
+    B.build()
+    from . import pf
+    W = train(pf, args.runs, args.budget, args.batch, args.lr)
+    np.savez(args.out, **W)
+    print(f"wrote {args.out}")
+
+
+if __name__ == "__main__":
+    main()
