@@ -286,7 +286,7 @@ class HybridRun:
         self.nsteps = W["steps"]
         self.stretch, self.jump_steps = W["dns_stretch"], W["jump"]
         self.cycles = self.nsteps // (self.stretch + self.jump_steps)
-        self.rho_top = ms[0][0]["rho_top"]
+
         self.launches = self.cycles * (self.stretch + 31)
         self.fallbacks = 0
         init = [t.clone() for t in self.fields]
@@ -302,11 +302,11 @@ class HybridRun:
         for t, s in zip(self.fields, init):
             t.copy_(s)
         # one jump alone, timed
-        self.net.jump(self.ens.fields, 1.0, self.rho_top)
+        self.net.jump(self.ens.fields, 1.0)
         torch.cuda.synchronize()
         ev[0].record(self.stream)
         for _ in range(5):
-            self.net.jump(self.ens.fields, 1.0, self.rho_top)
+            self.net.jump(self.ens.fields, 1.0)
         ev[1].record(self.stream)
         torch.cuda.synchronize()
         self.jump_s = ev[0].elapsed_time(ev[1]) / 5e3
@@ -334,7 +334,7 @@ class HybridRun:
             with torch.cuda.stream(self.stream):
                 for b, t in zip(self.backup, self.fields):
                     b.copy_(t)
-            self.net.jump(self.ens.fields, self.jump_steps / 2000.0, self.rho_top)
+            self.net.jump(self.ens.fields, self.jump_steps / 2000.0)
             if not all(self.net.check()):
                 with torch.cuda.stream(self.stream):
                     for b, t in zip(self.backup, self.fields):

@@ -287,15 +287,17 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
  * conditioning", Methods; the hybrid solver of Results alternates DNS stretches
  * with such jumps).  For each of `batch` runs it maps (phi, c) at time t to a
  * prediction at t + dt.  Structure:
- *   - input planes (phi, c, tau), with tau = dt / dt_ref;
+ *   - input planes (phi, c, rho, tau), with tau = dt / dt_ref;
  *   - encoder z1 = block(x), zp = block(down(z_{p-1})), with block = GELU(GN(conv3x3));
  *   - conditioning zc_p = z_p * (W_p f(tau)), where f is the sin MLP;
  *   - decoder d3 = up(block(zc4)), d2 = up(block(zc3 ++ d3)), d1 = up(block(zc2 ++ d2));
- *   - output (phi, c) += gamma * conv3x3(block(zc1 ++ d1)) + beta, a per-channel
- *     affine increment of the input fields.  The paper applies a final group
- *     normalisation to its single normalised composition field.  Here the two
- *     predicted fields have a per-sample mean and spread that vary with film
- *     thickness and incident composition, so the increment form is used instead.
+ *   - output (phi, c, rho) += gamma * conv3x3(block(zc1 ++ d1)) + beta, a
+ *     per-channel affine increment of the input fields.  The paper predicts its one
+ *     normalised composition field and applies a final group normalisation.  Here:
+ *     - the state is the three coupled fields, whose per-sample mean and spread vary
+ *       with film thickness and incident composition, so the increment form is used;
+ *     - the vapor density is predicted as well, because resetting it after each jump
+ *       instead costs 12.6% relative L2 in phi over 25 exact jumps.
  * Channels are 32-64-128-256, with 8 groups in the hidden normalisations.  Weights and activations are stored as BF16 and
  * accumulated in FP32; the 3x3 and transposed convolutions of levels 2-4 and of
  * the decoder run on the tensor cores (pf_conv3x3_bf16 / pf_tconv2x2_bf16).
@@ -307,24 +309,23 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
  * pf_unet_init: weights = 40 host FP32 arrays, in PyTorch layouts and this order:
  *   0-5   mlp_w0 [128][1], mlp_b0 [128], mlp_w1 [128][128], mlp_b1, mlp_w2 [128][128], mlp_b2
  *   6-9   proj1..proj4 [C_p][128] (C = 32, 64, 128, 256)
- *   10-13 enc1 [32][3][3][3], enc2 [64][32][3][3], enc3 [128][64][3][3], enc4 [256][128][3][3]
+ *   10-13 enc1 [32][4][3][3], enc2 [64][32][3][3], enc3 [128][64][3][3], enc4 [256][128][3][3]
  *   14-17 dec4 [256][256][3][3], dec3 [128][256][3][3], dec2 [64][128][3][3], dec1 [32][64][3][3]
  *   18-20 up4 [256][128][2][2], up3 [128][64][2][2], up2 [64][32][2][2]  ([Cin][Cout][dy][dx])
- *   21    out [2][32][3][3]
+ *   21    out [3][32][3][3]
  *   22-39 (gamma, beta) of enc1..enc4, dec4..dec1 (group normalisation) and of out
  *   (the output affine).  Convolution weights are rounded to BF16; the MLP and
  *   projections are kept in FP64 and the affine parameters in FP32.  Everything is
  *   copied into the workspace (synchronises once).
  *   work: 256-byte aligned.
- * pf_unet_jump: advances (phi[i], c[i]) of runs i < n (n == batch; device FP32
- *   fields ny x nx with row pitch `pitch` floats) in place by the predicted increment
- *   for jump length tau.  It sets rho[i] = rho_top (1 - phi) / 2, the initial-state vapor
- *   profile; the surrogate does not predict rho.  Asynchronous on the handle's
- *   stream, about 30 kernel launches.
+ * pf_unet_jump: advances (phi[i], c[i], rho[i]) of runs i < n (n == batch; device
+ *   FP32 fields ny x nx with row pitch `pitch` floats) in place by the predicted
+ *   increments for jump length tau.  Asynchronous on the handle's stream, about 30
+ *   kernel launches.
  * pf_unet_sync: synchronise; PF_ERR_TIMEOUT if a tensor-core pipeline wait ran out.
  * pf_unet_check: plausibility of the last jump's prediction, the hybrid solver's
- *   gate for its plain-DNS fallback.  ok[i] (host, n ints) is 1 if every phi and c
- *   of run i is finite and inside [phi_lo, phi_hi] x [c_lo, c_hi], else 0.  Synchronises.
+ *   gate for its plain-DNS fallback.  ok[i] (host, n ints) is 1 if every phi, c and
+ *   rho of run i is finite and inside its range, else 0.  Synchronises.
  * pf_unet_buffer: device pointer and channel count of activation buffer `which`
  *   (0-14: pre1, cat1, p1, pre2, cat2, p2, pre3, cat3, p3, pre4, zc4, h4, h3, h2,
  *   h1; NHWC BF16 at level resolution), for inspection.
@@ -333,10 +334,10 @@ typedef struct pf_unet pf_unet;
 size_t pf_unet_workspace_size(int batch, int nx, int ny);
 int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, int ny, void* work, size_t work_bytes,
                  void* stream, pf_unet** out);
-int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau,
-                 double rho_top);
+int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau);
 int pf_unet_sync(pf_unet* u);
-int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, int* ok);
+int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, double rho_lo, double rho_hi,
+                  int* ok);
 int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels);
 int pf_unet_destroy(pf_unet* u);
 const char* pf_unet_last_error(void);

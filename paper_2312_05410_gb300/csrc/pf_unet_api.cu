@@ -121,13 +121,13 @@ UnetLayout unet_layout(int n, int h, int w)
     };
     L.mlp = take(sizeof(double) * (3 * 128 + 2 * 128 * 128 + 128));
     L.proj = take(sizeof(double) * 480 * 128);
-    L.win = take(sizeof(float) * 27 * 32);
-    L.wout = take(sizeof(float) * 9 * 32 * 2);
+    L.win = take(sizeof(float) * 36 * 32);
+    L.wout = take(sizeof(float) * 9 * 32 * 3);
     const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
     for (int k = 0; k < 7; ++k) L.wc[k] = take(2 * 9 * (size_t)conv_io[k][0] * conv_io[k][1]);
     const int tc_io[3][2] = {{256, 128}, {128, 64}, {64, 32}};
     for (int k = 0; k < 3; ++k) L.wt[k] = take(2 * 4 * (size_t)tc_io[k][0] * tc_io[k][1]);
-    const int gbc[9] = {32, 64, 128, 256, 256, 128, 64, 32, 2};
+    const int gbc[9] = {32, 64, 128, 256, 256, 128, 64, 32, 3};
     for (int k = 0; k < 9; ++k)
         for (int q = 0; q < 2; ++q) L.gb[k][q] = take(sizeof(float) * gbc[k]);
     const size_t P0 = (size_t)n * h * w, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
@@ -250,16 +250,16 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     }
     std::vector<double> proj;
     for (int p = 0; p < 4; ++p) proj.insert(proj.end(), weights[6 + p], weights[6 + p] + (size_t)CH[p] * 128);
-    // first conv [32][3][3][3] -> [(ky,kx,ci)][co], BF16 values
-    std::vector<float> win(27 * 32);
+    // first conv [32][4][3][3] -> [(ky,kx,ci)][co], BF16 values
+    std::vector<float> win(36 * 32);
     for (int co = 0; co < 32; ++co)
-        for (int ci = 0; ci < 3; ++ci)
-            for (int t = 0; t < 9; ++t) win[(t * 3 + ci) * 32 + co] = host_rbf(weights[10][((co * 3 + ci) * 9) + t]);
-    // last conv [2][32][3][3] -> [tap][ci][co]
-    std::vector<float> wout(9 * 32 * 2);
-    for (int co = 0; co < 2; ++co)
+        for (int ci = 0; ci < 4; ++ci)
+            for (int t = 0; t < 9; ++t) win[(t * 4 + ci) * 32 + co] = host_rbf(weights[10][((co * 4 + ci) * 9) + t]);
+    // last conv [3][32][3][3] -> [tap][ci][co]
+    std::vector<float> wout(9 * 32 * 3);
+    for (int co = 0; co < 3; ++co)
         for (int ci = 0; ci < 32; ++ci)
-            for (int t = 0; t < 9; ++t) wout[(t * 32 + ci) * 2 + co] = host_rbf(weights[21][((co * 32 + ci) * 9) + t]);
+            for (int t = 0; t < 9; ++t) wout[(t * 32 + ci) * 3 + co] = host_rbf(weights[21][((co * 32 + ci) * 9) + t]);
     // tensor-core convs [Cout][Cin][3][3] -> [tap][Cout][Cin] BF16: enc2..4 (11..13), dec4..1 (14..17)
     const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
     const int conv_src[7] = {11, 12, 13, 14, 15, 16, 17};
@@ -287,7 +287,7 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
         keep.push_back(std::move(v));
         rc = upload(u, L.wt[k], keep.back().data(), keep.back().size() * 2);
     }
-    const int gbc[9] = {32, 64, 128, 256, 256, 128, 64, 32, 2};
+    const int gbc[9] = {32, 64, 128, 256, 256, 128, 64, 32, 3};
     if (rc == PF_OK) rc = upload(u, L.mlp, mlp.data(), mlp.size() * sizeof(double));
     if (rc == PF_OK) rc = upload(u, L.proj, proj.data(), proj.size() * sizeof(double));
     if (rc == PF_OK) rc = upload(u, L.win, win.data(), win.size() * sizeof(float));
@@ -307,8 +307,7 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     return PF_OK;
 }
 
-int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau,
-                 double rho_top)
+int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau)
 {
     if (!u || !phi || !c || !rho) return ufail(PF_ERR_ARG, "null pointer");
     if (n != u->n) return ufail(PF_ERR_ARG, "batch %d, the handle was built for %d", n, u->n);
@@ -346,7 +345,8 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
         u->cond_tau = tau;
     }
     // ---- encoder
-    ck(pf::launch_in_conv(dp, dp + n, pitch, n, H, W, (float)tau, u->at<float>(L.win), act(A_PRE1), part, s), "input conv");
+    ck(pf::launch_in_conv(dp, dp + n, dp + 2 * n, pitch, n, H, W, (float)tau, u->at<float>(L.win), act(A_PRE1), part, s),
+       "input conv");
     ck(pf::launch_gn_stats(part, n, G, H * W / 128, 4.0 * H * W, stats, s), "statistics");
     ck(pf::launch_gn_enc(act(A_PRE1), n, H, W, 32, G, stats, gam(0), bet(0), sc, act(A_CAT1), 64, act(A_P1), s), "level 1");
     if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P1), H / 2, W / 2, 32, u->at<uint16_t>(L.wc[0]), 64, act(A_PRE2), 64, 0, true);
@@ -367,9 +367,8 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H2), H / 2, W / 2, 64, u->at<uint16_t>(L.wt[2]), 32, act(A_CAT1), 64, 32, false);
     if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT1), H, W, 64, u->at<uint16_t>(L.wc[6]), 32, act(A_PRE1), 32, 0, true);
     ck(pf::launch_gn_dec(act(A_PRE1), n, H, W, 32, G, stats, gam(7), bet(7), act(A_H1), s), "decoder 1");
-    // ---- output: conv 32 -> 2 as an affine increment of the DNS fields (and the vapor reset)
-    ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch,
-                           (float)rho_top, s),
+    // ---- output: conv 32 -> 3 as affine increments of the DNS fields
+    ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch, s),
        "output");
     return rc;
 }
@@ -385,7 +384,8 @@ int pf_unet_sync(pf_unet* u)
     return PF_OK;
 }
 
-int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, int* ok)
+int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, double rho_lo, double rho_hi,
+                  int* ok)
 {
     if (!u || !ok) return ufail(PF_ERR_ARG, "null pointer");
     const int n = u->n;
@@ -393,8 +393,8 @@ int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double 
     cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * n, u->stream);
     float** dp = u->at<float*>(u->L.ptrs);  // the fields of the last jump
     if (e == cudaSuccess)
-        e = pf::launch_check(dp, dp + n, n, u->h, u->w, u->last_pitch, (float)phi_lo, (float)phi_hi, (float)c_lo,
-                             (float)c_hi, flags, u->stream);
+        e = pf::launch_check(dp, dp + n, dp + 2 * n, n, u->h, u->w, u->last_pitch, (float)phi_lo, (float)phi_hi,
+                             (float)c_lo, (float)c_hi, (float)rho_lo, (float)rho_hi, flags, u->stream);
     std::vector<int> f(n, 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f.data(), flags, sizeof(int) * n, cudaMemcpyDeviceToHost, u->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);

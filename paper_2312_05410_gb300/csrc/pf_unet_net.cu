@@ -4,9 +4,9 @@
 //
 //   cond_kernel     the MLP basis f(dt) = w2 sin(w1 sin(w0 dt + b0) + b1) + b2 and the
 //                   per-level conditioning factors W_p f(dt), in FP64, stored as BF16 values
-//   in_conv_kernel  the first 3x3 convolution (3 -> 32 channels) straight from the DNS
-//                   fields (phi, c and a plane holding dt / dt_ref), with its group sums
-//   out_conv_kernel the last 3x3 convolution (32 -> 2) as an affine increment of the DNS fields
+//   in_conv_kernel  the first 3x3 convolution (4 -> 32 channels) straight from the DNS
+//                   fields (phi, c, rho and a plane holding dt / dt_ref), with its group sums
+//   out_conv_kernel the last 3x3 convolution (32 -> 3) as affine increments of the DNS fields
 //   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums, FP64, fixed order
 //   gn_apply_*      GN + GELU (+ conditioning product, + 2x2 max pooling) on stored BF16 values
 //
@@ -83,23 +83,25 @@ __global__ void cond_kernel(const double* __restrict__ mlp, const double* __rest
     }
 }
 
-// First convolution: x = BF16(phi, c, tau) with zero padding outside the image, 3x3, 3 -> 32.
+// First convolution: x = BF16(phi, c, rho, tau) with zero padding outside the image, 3x3, 4 -> 32.
 // One thread per output pixel, one 128-pixel tile per block.
 __global__ void __launch_bounds__(TPB)
-in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c, int pitch, int h, int w,
-               float tau, const float* __restrict__ wgt /* [27][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
+in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
+               const float* const* __restrict__ rho, int pitch, int h, int w, float tau,
+               const float* __restrict__ wgt /* [36][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
                float* __restrict__ partials)
 {
-    __shared__ float ws[27 * 32];
+    __shared__ float ws[36 * 32];
     __shared__ float red[4];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = threadIdx.x; i < 27 * 32; i += TPB) ws[i] = wgt[i];
+    for (int i = threadIdx.x; i < 36 * 32; i += TPB) ws[i] = wgt[i];
     __syncthreads();
     const int tpi = h * w / TPB;
     const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
     const int p = t * TPB + threadIdx.x, y = p / w, x = p % w;
     const float* F = phi[img];
     const float* C = c[img];
+    const float* Rh = rho[img];
     const float tb = rbf(tau);
     float acc[32];
 #pragma unroll
@@ -108,12 +110,15 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
         for (int kx = 0; kx < 3; ++kx) {
             const int yy = y + ky - 1, xx = x + kx - 1;
             const bool in = yy >= 0 && yy < h && xx >= 0 && xx < w;
-            const float v0 = in ? rbf(F[(size_t)yy * pitch + xx]) : 0.f;
-            const float v1 = in ? rbf(C[(size_t)yy * pitch + xx]) : 0.f;
-            const float v2 = in ? tb : 0.f;
-            const float* wk = ws + (ky * 3 + kx) * 3 * 32;
+            const size_t o = in ? (size_t)yy * pitch + xx : 0;
+            const float v0 = in ? rbf(F[o]) : 0.f;
+            const float v1 = in ? rbf(C[o]) : 0.f;
+            const float v2 = in ? rbf(Rh[o]) : 0.f;
+            const float v3 = in ? tb : 0.f;
+            const float* wk = ws + (ky * 3 + kx) * 4 * 32;
 #pragma unroll
-            for (int o = 0; o < 32; ++o) acc[o] = fmaf(v0, wk[o], fmaf(v1, wk[32 + o], fmaf(v2, wk[64 + o], acc[o])));
+            for (int q = 0; q < 32; ++q)
+                acc[q] = fmaf(v0, wk[q], fmaf(v1, wk[32 + q], fmaf(v2, wk[64 + q], fmaf(v3, wk[96 + q], acc[q]))));
         }
     uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)img * h * w + p) * 32);
 #pragma unroll
@@ -143,28 +148,27 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Output: the last convolution (3x3, 32 -> 2) of BF16 NHWC [n][h][w][32], as a per-channel affine
-// increment added to the FP32 fields in place: phi += g0 conv0 + b0, c += g1 conv1 + b1; the vapor
-// density is reset to its initial-state profile rho_top (1 - phi) / 2.
+// Output: the last convolution (3x3, 32 -> 3) of BF16 NHWC [n][h][w][32], as per-channel affine
+// increments added to the FP32 fields in place: u_k += gamma_k conv_k + beta_k for u = (phi, c, rho).
 __global__ void __launch_bounds__(TPB)
-out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __restrict__ wgt /* [9][32][2] */,
+out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __restrict__ wgt /* [9][32][3] */,
                 const float* __restrict__ gamma, const float* __restrict__ beta, float* const* __restrict__ phi,
-                float* const* __restrict__ c, float* const* __restrict__ rho, int pitch, float rho_top)
+                float* const* __restrict__ c, float* const* __restrict__ rho, int pitch)
 {
-    __shared__ float ws[9 * 32 * 2];
+    __shared__ float ws[9 * 32 * 3];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = threadIdx.x; i < 9 * 32 * 2; i += TPB) ws[i] = wgt[i];
+    for (int i = threadIdx.x; i < 9 * 32 * 3; i += TPB) ws[i] = wgt[i];
     __syncthreads();
     const int tpi = h * w / TPB;
     const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
     const int p = t * TPB + threadIdx.x, y = p / w, x = p % w;
-    float a0 = 0.f, a1 = 0.f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     for (int ky = 0; ky < 3; ++ky)
         for (int kx = 0; kx < 3; ++kx) {
             const int yy = y + ky - 1, xx = x + kx - 1;
             if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
             const uint4* src = reinterpret_cast<const uint4*>(in + ((size_t)img * h * w + (size_t)yy * w + xx) * 32);
-            const float* wk = ws + (ky * 3 + kx) * 64;
+            const float* wk = ws + (ky * 3 + kx) * 96;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint4 v = src[q];
@@ -173,16 +177,16 @@ out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __re
                 for (int j = 0; j < 4; ++j) {
                     const int ci = 8 * q + 2 * j;
                     const float lo = bf((uint16_t)(u[j] & 0xffffu)), hi = bf((uint16_t)(u[j] >> 16));
-                    a0 = fmaf(lo, wk[2 * ci], fmaf(hi, wk[2 * ci + 2], a0));
-                    a1 = fmaf(lo, wk[2 * ci + 1], fmaf(hi, wk[2 * ci + 3], a1));
+                    a0 = fmaf(lo, wk[3 * ci], fmaf(hi, wk[3 * ci + 3], a0));
+                    a1 = fmaf(lo, wk[3 * ci + 1], fmaf(hi, wk[3 * ci + 4], a1));
+                    a2 = fmaf(lo, wk[3 * ci + 2], fmaf(hi, wk[3 * ci + 5], a2));
                 }
             }
         }
     const size_t o = (size_t)y * pitch + x;
-    const float f = phi[img][o] + fmaf(gamma[0], a0, beta[0]);
+    phi[img][o] = phi[img][o] + fmaf(gamma[0], a0, beta[0]);
     c[img][o] = c[img][o] + fmaf(gamma[1], a1, beta[1]);
-    phi[img][o] = f;
-    rho[img][o] = rho_top * (1.0f - f) * 0.5f;
+    rho[img][o] = rho[img][o] + fmaf(gamma[2], a2, beta[2]);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
@@ -324,21 +328,23 @@ __global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pi
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Plausibility of a predicted state: every phi and c finite and inside [lo, hi]; flags[img]
+// Plausibility of a predicted state: every phi, c and rho finite and inside its range; flags[img]
 // is set to 1 on a violation (flags are cleared by the caller).
-__global__ void check_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c, int h, int w,
-                             int pitch, float phi_lo, float phi_hi, float c_lo, float c_hi, int* __restrict__ flags)
+__global__ void check_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
+                             const float* const* __restrict__ rho, int h, int w, int pitch, float phi_lo, float phi_hi,
+                             float c_lo, float c_hi, float r_lo, float r_hi, int* __restrict__ flags)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int img = blockIdx.y;
     const float* F = phi[img];
     const float* C = c[img];
+    const float* Rh = rho[img];
     int bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < h * w; i += gridDim.x * blockDim.x) {
         const size_t o = (size_t)(i / w) * pitch + i % w;
-        const float f = F[o], cc = C[o];
+        const float f = F[o], cc = C[o], r = Rh[o];
         // written so that NaN fails every comparison
-        bad |= !(f >= phi_lo && f <= phi_hi && cc >= c_lo && cc <= c_hi);
+        bad |= !(f >= phi_lo && f <= phi_hi && cc >= c_lo && cc <= c_hi && r >= r_lo && r <= r_hi);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags[img], 1);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -372,21 +378,21 @@ cudaError_t launch_cond(const double* mlp, const double* proj, double tau, float
     return cudaLaunchKernelEx(&cfg, cond_kernel, mlp, proj, tau, scales, nscales);
 }
 
-cudaError_t launch_in_conv(const float* const* phi, const float* const* c, int pitch, int n, int h, int w, float tau,
-                           const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
+cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const float* const* rho, int pitch, int n,
+                           int h, int w, float tau, const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
-    return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, pitch, h, w, tau, wgt, out, partials);
+    return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, rho, pitch, h, w, tau, wgt, out, partials);
 }
 
 cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, const float* gamma,
                             const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
-                            float rho_top, cudaStream_t s)
+                            cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
-    return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, gamma, beta, phi, c, rho, pitch, rho_top);
+    return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, gamma, beta, phi, c, rho, pitch);
 }
 
 cudaError_t launch_gn_stats(const float* partials, int n, int groups, int tpi, double count, float* stats,
@@ -417,12 +423,14 @@ cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, int gro
     return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, pixels, C, h * w, groups, stats, gamma, beta, y);
 }
 
-cudaError_t launch_check(const float* const* phi, const float* const* c, int n, int h, int w, int pitch, float phi_lo,
-                         float phi_hi, float c_lo, float c_hi, int* flags, cudaStream_t s)
+cudaError_t launch_check(const float* const* phi, const float* const* c, const float* const* rho, int n, int h, int w,
+                         int pitch, float phi_lo, float phi_hi, float c_lo, float c_hi, float r_lo, float r_hi,
+                         int* flags, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3(32, (unsigned)n), 256, s, attr);
-    return cudaLaunchKernelEx(&cfg, check_kernel, phi, c, h, w, pitch, phi_lo, phi_hi, c_lo, c_hi, flags);
+    return cudaLaunchKernelEx(&cfg, check_kernel, phi, c, rho, h, w, pitch, phi_lo, phi_hi, c_lo, c_hi, r_lo, r_hi,
+                              flags);
 }
 
 }  // namespace pf

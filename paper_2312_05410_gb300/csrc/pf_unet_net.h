@@ -11,11 +11,11 @@ constexpr int UNET_FDIM = 128;       // MLP hidden width and basis size
 constexpr float UNET_EPS = 1e-5f;    // group-normalisation epsilon
 
 cudaError_t launch_cond(const double* mlp, const double* proj, double tau, float* scales, int nscales, cudaStream_t s);
-cudaError_t launch_in_conv(const float* const* phi, const float* const* c, int pitch, int n, int h, int w, float tau,
-                           const float* wgt, uint16_t* out, float* partials, cudaStream_t s);
+cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const float* const* rho, int pitch, int n,
+                           int h, int w, float tau, const float* wgt, uint16_t* out, float* partials, cudaStream_t s);
 cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, const float* gamma,
                             const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
-                            float rho_top, cudaStream_t s);
+                            cudaStream_t s);
 cudaError_t launch_gn_stats(const float* partials, int n, int groups, int tpi, double count, float* stats,
                             cudaStream_t s);
 cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
@@ -23,7 +23,8 @@ cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, int gro
                           uint16_t* pool, cudaStream_t s);
 cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
                           const float* gamma, const float* beta, uint16_t* y, cudaStream_t s);
-cudaError_t launch_check(const float* const* phi, const float* const* c, int n, int h, int w, int pitch, float phi_lo,
-                         float phi_hi, float c_lo, float c_hi, int* flags, cudaStream_t s);
+cudaError_t launch_check(const float* const* phi, const float* const* c, const float* const* rho, int n, int h, int w,
+                         int pitch, float phi_lo, float phi_hi, float c_lo, float c_hi, float r_lo, float r_hi,
+                         int* flags, cudaStream_t s);
 
 }  // namespace pf

@@ -181,6 +181,7 @@ def ensemble_members(n_runs: int = 64, seed: int = 3, v_range=(0.1, 0.9), c_rang
 STREAM_HYBRID = 4
 UNET_CHANNELS = (32, 64, 128, 256)
 UNET_FDIM = 128
+UNET_IN, UNET_OUT = 4, 3  # (phi, c, rho, dt / dt_ref) in; increments of (phi, c, rho) out
 
 
 def unet_weights(seed: int = 0) -> dict:
@@ -201,7 +202,7 @@ def unet_weights(seed: int = 0) -> dict:
     W["mlp_b2"] = (g.standard_normal(UNET_FDIM) * 0.1).astype(np.float32)
     for p, c in enumerate(UNET_CHANNELS, 1):
         W[f"proj{p}"] = (g.standard_normal((c, UNET_FDIM)) / math.sqrt(UNET_FDIM)).astype(np.float32)
-    cin = 3
+    cin = UNET_IN
     for p, c in enumerate(UNET_CHANNELS, 1):
         W[f"enc{p}"] = he((c, cin, 3, 3), 9 * cin)
         cin = c
@@ -212,9 +213,9 @@ def unet_weights(seed: int = 0) -> dict:
     W["up4"] = he((256, 128, 2, 2), 256)
     W["up3"] = he((128, 64, 2, 2), 128)
     W["up2"] = he((64, 32, 2, 2), 64)
-    W["out"] = he((2, 32, 3, 3), 9 * 32)
+    W["out"] = he((UNET_OUT, 32, 3, 3), 9 * 32)
     for name, c in (("enc1", 32), ("enc2", 64), ("enc3", 128), ("enc4", 256), ("dec4", 256), ("dec3", 128),
-                    ("dec2", 64), ("dec1", 32), ("out", 2)):
+                    ("dec2", 64), ("dec1", 32), ("out", UNET_OUT)):
         W[name + "_gamma"] = (1.0 + 0.1 * g.standard_normal(c)).astype(np.float32)
         W[name + "_beta"] = (0.1 * g.standard_normal(c)).astype(np.float32)
     return W

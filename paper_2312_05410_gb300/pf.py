@@ -101,10 +101,10 @@ def _load():
     L.pf_unet_init.argtypes = [C.POINTER(C.POINTER(C.c_float)), C.c_int, C.c_int, C.c_int, C.c_int, vp, sz, vp,
                                C.POINTER(vp)]
     L.pf_unet_init.restype = C.c_int
-    L.pf_unet_jump.argtypes = [vp, C.c_int, pp, pp, pp, C.c_int, C.c_double, C.c_double]
+    L.pf_unet_jump.argtypes = [vp, C.c_int, pp, pp, pp, C.c_int, C.c_double]
     L.pf_unet_jump.restype = C.c_int
     L.pf_unet_sync.argtypes, L.pf_unet_sync.restype = [vp], C.c_int
-    L.pf_unet_check.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, ip]
+    L.pf_unet_check.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, ip]
     L.pf_unet_check.restype = C.c_int
     L.pf_unet_buffer.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(C.c_int)]
     L.pf_unet_buffer.restype = C.c_int
@@ -558,20 +558,21 @@ class UNet:
                                  C.byref(h)))
         self.h = h
 
-    def jump(self, fields, tau: float, rho_top: float = 1.0):
+    def jump(self, fields, tau: float):
         """fields: `batch` tuples (phi, c, rho) of (ny, pitch) float32 CUDA tensors, updated in place."""
         n = len(fields)
         arr = [(C.c_void_p * n)(*[int(f[q].data_ptr()) for f in fields]) for q in range(3)]
         pitch = fields[0][0].shape[1]
-        _ucheck(lib.pf_unet_jump(self.h, n, arr[0], arr[1], arr[2], pitch, float(tau), float(rho_top)))
+        _ucheck(lib.pf_unet_jump(self.h, n, arr[0], arr[1], arr[2], pitch, float(tau)))
 
     def sync(self):
         _ucheck(lib.pf_unet_sync(self.h))
 
-    def check(self, phi_range=(-1.5, 1.5), c_range=(-0.5, 1.5)) -> list[bool]:
+    def check(self, phi_range=(-1.5, 1.5), c_range=(-0.5, 1.5), rho_range=(-0.5, 1.5)) -> list[bool]:
         """Per run: is the last jump's prediction finite and inside the given ranges?  (Synchronises.)"""
         ok = (C.c_int * self.batch)()
-        _ucheck(lib.pf_unet_check(self.h, phi_range[0], phi_range[1], c_range[0], c_range[1], ok))
+        _ucheck(lib.pf_unet_check(self.h, phi_range[0], phi_range[1], c_range[0], c_range[1], rho_range[0],
+                                  rho_range[1], ok))
         return [bool(v) for v in ok]
 
     def buffer(self, name: str):

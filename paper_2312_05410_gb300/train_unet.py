@@ -4,10 +4,11 @@
 
 This is offline tooling, not the solver's path.
 - **Data.** The batched ensemble kernel advances `runs` seeded films of 256 x 256 cells.
-  A snapshot of (phi, c) is kept every 2000 steps, 50 snapshots per run, like the
+  A snapshot of (phi, c, rho) is kept every 2000 steps, 50 snapshots per run, like the
   paper's 50-snapshot trajectories ("Dataset").
 - **Training.** Each pair of consecutive snapshots is a sample with jump length
-  tau = 1 (2000 steps).  The network is the one the inference kernels compute
+  tau = 1 (2000 steps), input (phi, c, rho, tau) and target (phi, c, rho).  Samples are shifted and mirrored in x at random: the domain is
+  periodic in x and, at normal incidence, mirror-symmetric.  The network is the one the inference kernels compute
   (pf_unet_jump), written a second time with PyTorch operations so that autograd
   can differentiate it.  Training uses Adam on the relative squared error of both
   fields ("Training of the network", "Error metrics").
@@ -29,7 +30,7 @@ FDIM = I.UNET_FDIM
 
 
 def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 2000, snapshots: int = 50):
-    """(phi, c) snapshots [snapshots + 1, runs, 2, side, side] on the GPU, from seeded films."""
+    """(phi, c, rho) snapshots [snapshots + 1, runs, 3, side, side] on the GPU, from seeded films."""
     import torch
 
     ms = []
@@ -41,7 +42,7 @@ def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 2000, 
     ens.set_tile(0)
 
     def grab():
-        return torch.stack([torch.stack([run[0][:, :side], run[1][:, :side]]) for run in ens.fields]).clone()
+        return torch.stack([torch.stack([run[q][:, :side] for q in range(3)]) for run in ens.fields]).clone()
 
     out = [grab()]
     for _ in range(snapshots):
@@ -60,8 +61,8 @@ def make_model(seed: int = 0):
         def __init__(self):
             super().__init__()
             W = I.unet_weights(seed)
-            W["out_gamma"] = np.full(2, 0.1, np.float32)  # start close to the identity jump
-            W["out_beta"] = np.zeros(2, np.float32)
+            W["out_gamma"] = np.full(I.UNET_OUT, 0.1, np.float32)  # start close to the identity jump
+            W["out_beta"] = np.zeros(I.UNET_OUT, np.float32)
             self.p = torch.nn.ParameterDict({k: torch.nn.Parameter(torch.from_numpy(v.copy())) for k, v in W.items()})
 
         def block(self, x, name):
@@ -86,7 +87,7 @@ def make_model(seed: int = 0):
             d1 = F.conv_transpose2d(self.block(torch.cat([zc[1], d2], 1), "dec2"), p["up2"], stride=2)
             h1 = self.block(torch.cat([zc[0], d1], 1), "dec1")
             inc = F.conv2d(h1, p["out"], padding=1)
-            return x[:, :2] + inc * p["out_gamma"][None, :, None, None] + p["out_beta"][None, :, None, None]
+            return x[:, :3] + inc * p["out_gamma"][None, :, None, None] + p["out_beta"][None, :, None, None]
 
     return Net()
 
@@ -96,7 +97,7 @@ def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float
     import torch
 
     torch.manual_seed(seed)
-    data = generate(pf, runs)                      # [51, runs, 2, H, W]
+    data = generate(pf, runs)                      # [51, runs, 3, H, W]
     S, R = data.shape[0] - 1, data.shape[1]
     pairs = [(k, r) for k in range(S) for r in range(R)]
     val = [(k, r) for (k, r) in pairs if r == R - 1]  # the last run is held out
@@ -105,13 +106,18 @@ def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float
     opt = torch.optim.Adam(net.parameters(), lr=lr)
     sched_T = None
 
-    def sample(idx):
+    def sample(idx, augment=False):
         x = torch.stack([torch.cat([data[k, r], torch.ones_like(data[k, r, :1])]) for k, r in idx])
         y = torch.stack([data[k + 1, r] for k, r in idx])
+        if augment:  # x is periodic and, at normal incidence, mirror-symmetric: random shifts and flips
+            shift = int(g.integers(0, x.shape[-1]))
+            x, y = torch.roll(x, shift, dims=-1), torch.roll(y, shift, dims=-1)
+            if g.integers(0, 2):
+                x, y = torch.flip(x, dims=(-1,)), torch.flip(y, dims=(-1,))
         return x, y
 
     def loss_fn(pred, y):
-        return sum(((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(2))
+        return sum(((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(3))
 
     g = np.random.default_rng(seed)
     t0 = time.time()
@@ -123,7 +129,7 @@ def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float
             frac = min(1.0, (time.time() - t0) / budget_s)
             for gr in opt.param_groups:
                 gr["lr"] = lr * 0.5 * (1 + math.cos(math.pi * frac))  # cosine decay over the budget
-            x, y = sample([trn[j] for j in order[i:i + batch]])
+            x, y = sample([trn[j] for j in order[i:i + batch]], augment=True)
             with torch.autocast("cuda", dtype=torch.bfloat16):
                 pred = net(x, 1.0)
             loss = loss_fn(pred.float(), y)
@@ -136,8 +142,8 @@ def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float
         epoch += 1
         with torch.no_grad(), torch.autocast("cuda", dtype=torch.bfloat16):
             x, y = sample(val)
-            v = float(loss_fn(net(x, 1.0).float(), y)) / 2
-        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss) / 2:.3e} "
+            v = float(loss_fn(net(x, 1.0).float(), y)) / 3
+        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss) / 3:.3e} "
             f"val rel-sq {v:.3e} (rel L2 {math.sqrt(v):.3e})")
     del sched_T
     return {k: v.detach().float().cpu().numpy() for k, v in net.p.items()}

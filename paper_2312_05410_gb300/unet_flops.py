@@ -6,7 +6,7 @@ def layer_flops(h: int, w: int) -> list[tuple[str, float]]:
     """(layer, FLOPs) of one sample on an h x w input: 3x3 convolutions of the encoder and decoder
     blocks, the stride-2 transposed convolutions, and the output convolution."""
     out = []
-    enc = [(3, 32), (32, 64), (64, 128), (128, 256)]
+    enc = [(4, 32), (32, 64), (64, 128), (128, 256)]
     for lvl, (ci, co) in enumerate(enc):
         out.append((f"enc{lvl + 1}", 2.0 * 9 * ci * co * (h >> lvl) * (w >> lvl)))
     dec = [("dec4", 256, 256, 3), ("dec3", 256, 128, 2), ("dec2", 128, 64, 1), ("dec1", 64, 32, 0)]
@@ -15,7 +15,7 @@ def layer_flops(h: int, w: int) -> list[tuple[str, float]]:
     ups = [("up4", 256, 128, 3), ("up3", 128, 64, 2), ("up2", 64, 32, 1)]
     for name, ci, co, lvl in ups:
         out.append((name, 2.0 * ci * co * 4 * (h >> lvl) * (w >> lvl)))
-    out.append(("out", 2.0 * 9 * 32 * 2 * h * w))
+    out.append(("out", 2.0 * 9 * 32 * 3 * h * w))
     return out
 
 
