@@ -143,10 +143,10 @@ int pf_set_step(pf_handle* h, long step);
  * of 0 makes every wait give up at once, to exercise that path. */
 int pf_set_wait_limit(pf_handle* h, int polls);
 
-/* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids
- * above 2^20 cells, which use the 56 x 24 tile), 0 when every tile uses per-thread
- * asynchronous copies (smaller, L2-resident grids, or a driver without tensor-map
- * support); -1 on NULL. */
+/* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids of
+ * at least 64 columns and one staged window of rows: 16 rows up to 2^20 cells, 32
+ * above), 0 when every tile uses per-thread asynchronous copies (smaller grids, or
+ * a driver without tensor-map support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
 
 /* Clear the sticky device error word (async). */

@@ -322,9 +322,8 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
     h->d = pf::diag_const_of(*p, nx, ny, pitch);
     h->mob = pf::mob_kind_of(*p);
     h->tile = pf::choose_tile(nx, ny);
-    // TMA staging pays off for the large tile (HBM-resident grids); the short tile of small,
-    // L2-resident grids keeps the per-thread asynchronous copies, whose kernel needs fewer registers.
-    h->tma = h->tile == pf::TILE_LARGE &&
+    // interior tiles are staged by TMA whenever the grid holds a full staged window
+    h->tma =
              pf::make_step_maps(h->u[0][0], h->u[0][1], h->u[0][2], nx, ny, pitch, h->tile, &h->maps[0]) &&
              pf::make_step_maps(h->u[1][0], h->u[1][1], h->u[1][2], nx, ny, pitch, h->tile, &h->maps[1]);
     h->gexec = nullptr;

@@ -32,7 +32,11 @@
 // After stage 1, CTAs that touch a boundary write the same ghost rows of u*.
 #include "pf_internal.h"
 
-// Tile heights TY and warps S of the three tile kinds (overridable for sweeps).
+// Tile heights TY and warps S of the three tile kinds (overridable for sweeps), and the
+// register budget of the short tile (resident CTAs per SM).
+#ifndef PF_MINB_SMALL
+#define PF_MINB_SMALL 5
+#endif
 #ifndef PF_SMALL_TY
 #define PF_SMALL_TY 8
 #define PF_SMALL_S 4
@@ -101,11 +105,9 @@ struct Geo {
     static constexpr int PX = LX;             // row pitch (floats)
     static constexpr int PLANE = LY * PX;
     static constexpr int THREADS = 32 * S;    // S warps = S row segments
-#ifndef PF_MINB_SMALL
-#define PF_MINB_SMALL 4
-#define PF_MINB_LARGE 3
-#endif
-    static constexpr int MINB = S <= 4 ? PF_MINB_SMALL : PF_MINB_LARGE;  // resident CTAs per SM the register budget allows
+    // resident CTAs per SM the register budget is sized for: 5 for the short tile of small grids
+    // (102 registers; the TMA-staged kernel there runs best at that cap), else 4 (4 warps) or 3
+    static constexpr int MINB = (TY == PF_SMALL_TY && S == PF_SMALL_S) ? PF_MINB_SMALL : (S <= 4 ? 4 : 3);
     static constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
     static constexpr int L1 = cdiv(TY + 4, S);  // longest stage-1 segment (u* rows)
     static constexpr int L2 = cdiv(TY, S);      // longest stage-2 segment (output rows)
@@ -530,9 +532,9 @@ cudaError_t launch_t(const StepConst& k, const float* f0, const float* c0, const
     using G = Geo<TY, S>;
     const dim3 grid((k.nx + TXO - 1) / TXO, (k.ny + TY - 1) / TY);
     cudaLaunchAttribute attr[1];
-    // TMA staging is built for the large tile only (grids above 2^20 cells); smaller
-    // tiles ignore the maps
-    if constexpr (TY == PF_LARGE_TY && S == PF_LARGE_S) {
+    // TMA staging is built for the short and the large tile; the medium tile (ensembles only)
+    // ignores the maps
+    if constexpr ((TY == PF_LARGE_TY && S == PF_LARGE_S) || (TY == PF_SMALL_TY && S == PF_SMALL_S)) {
         if (maps) {
             auto kern = step_kernel_tma<TY, S, PHI_MODE, MOB>;
             static bool configured = false;
