@@ -177,3 +177,76 @@ def test_plausibility_check_flags_out_of_range_runs(pf):
     fields[0][0][0, 0] = 3.0
     assert net.check() == [False, True]
     net.close()
+
+
+def _hybrid(pf, ens, net, cycles, stretch, jump):
+    """The hybrid loop of bench.py's hybrid workload: DNS stretch, snapshot, jump, plausibility gate."""
+    fields = [t for run in ens.fields for t in run]
+    backup = [t.clone() for t in fields]
+    fallbacks = 0
+    for _ in range(cycles):
+        ens.step(stretch)
+        with torch.cuda.stream(ens.stream):
+            for b, t in zip(backup, fields):
+                b.copy_(t)
+        net.jump(ens.fields, jump / 2000.0)
+        if not all(net.check()):
+            with torch.cuda.stream(ens.stream):
+                for b, t in zip(backup, fields):
+                    t.copy_(b)
+            ens.step(jump)
+            fallbacks += 1
+    torch.cuda.synchronize()
+    return fallbacks
+
+
+def test_hybrid_with_rejected_jumps_is_exactly_the_dns(pf):
+    """Seeded untrained weights make every jump implausible: each one must be undone and replaced by the DNS
+    stretch, so the hybrid result equals plain DNS bit for bit."""
+    import oracle as O
+    from paper_2312_05410_gb300 import inputs as I2
+    ms = []
+    for m in I2.hybrid_members(2, 128, seed=7):
+        p = O.with_dt(I2.default_params(v_mag=m["v_mag"]))
+        ms.append((p, *I2.film_state(m["spec"], p)))
+    ens = pf.Ensemble(ms)
+    ens.set_tile(0)
+    net = pf.UNet(I2.unet_weights(0), 2, 128, 128, stream=ens.stream)
+    assert _hybrid(pf, ens, net, cycles=3, stretch=200, jump=200) == 3
+    hyb = [tuple(t.clone() for t in run) for run in ens.fields]
+    ens.close()
+    ref = pf.Ensemble(ms)
+    ref.set_tile(0)
+    ref.step(1200)
+    for a, b in zip(hyb, ref.fields):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    ref.close()
+    net.close()
+
+
+def test_hybrid_with_identity_jumps_skips_the_jumped_steps(pf):
+    """A zero output affine makes each jump the identity: the hybrid then equals DNS of the stretches only."""
+    import oracle as O
+    from paper_2312_05410_gb300 import inputs as I2
+    ms = []
+    for m in I2.hybrid_members(2, 128, seed=8):
+        p = O.with_dt(I2.default_params(v_mag=m["v_mag"]))
+        ms.append((p, *I2.film_state(m["spec"], p)))
+    W = I2.unet_weights(0)
+    W["out_gamma"][:] = 0.0
+    W["out_beta"][:] = 0.0
+    ens = pf.Ensemble(ms)
+    ens.set_tile(0)
+    net = pf.UNet(W, 2, 128, 128, stream=ens.stream)
+    assert _hybrid(pf, ens, net, cycles=2, stretch=100, jump=300) == 0
+    hyb = [tuple(t.clone() for t in run) for run in ens.fields]
+    ens.close()
+    ref = pf.Ensemble(ms)
+    ref.set_tile(0)
+    ref.step(200)
+    for a, b in zip(hyb, ref.fields):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    ref.close()
+    net.close()
