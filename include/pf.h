@@ -271,8 +271,9 @@ const char* pf_adjoint_last_error(void);
  * pf_tconv2x2_bf16: out[n][2y+dy][2x+dx][out_coff + co] = BF16( sum_ci in[n][y][x][ci]
  *   * wgt[(2 dy + dx) cout + co][ci] ) (stride-2 2x2 transposed convolution, no bias);
  *   out is n x 2h x 2w pixels.
- * Shapes: cin % 32 == 0 (<= 1024), cout % 16 == 0 (conv: <= 256, divisible by
- * groups <= 8), h*w % 128 == 0 and w a multiple or a divisor of 128; pointers
+ * Shapes: cin % 32 == 0 (<= 1024); conv: cout in {32, 64, 128, 256} with groups
+ * = 8 (the U-Net's widths); transposed conv: cout in {16, 32, 64, 128}; h*w % 128
+ * == 0 and w a multiple or a divisor of 128; pointers
  * 16-byte aligned; out_coff and out_cstride multiples of 8.  err_dev: device int;
  * bit 1 is set if a bounded pipeline wait ran out (the kernel then stops early).
  * Asynchronous on `stream`; PF_ERR_ARG / PF_ERR_LAYOUT / PF_ERR_CUDA on errors, with

@@ -39,8 +39,10 @@ int conv_common(int mode, const void* in, int n, int h, int w, int cin, const vo
         return ufail(PF_ERR_ARG, "bad image size %d x %d x %d", n, h, w);
     if (cin < 32 || cin > 1024 || cin % 32 || cout < 16 || cout % 16)
         return ufail(PF_ERR_ARG, "channels cin=%d cout=%d unsupported (cin %% 32, cout %% 16)", cin, cout);
-    if (mode == pf::CONV3 && (cout > 256 || groups < 1 || groups > pf::GN_MAX_GROUPS || cout % groups))
-        return ufail(PF_ERR_ARG, "cout=%d / groups=%d unsupported", cout, groups);
+    if (mode == pf::CONV3 && ((cout != 32 && cout != 64 && cout != 128 && cout != 256) || groups != pf::GN_MAX_GROUPS))
+        return ufail(PF_ERR_ARG, "cout=%d / groups=%d unsupported (cout 32, 64, 128 or 256; 8 groups)", cout, groups);
+    if (mode == pf::TCONV && cout != 16 && cout != 32 && cout != 64 && cout != 128)
+        return ufail(PF_ERR_ARG, "cout=%d unsupported (16, 32, 64 or 128)", cout);
     if ((w % 128) && (128 % w)) return ufail(PF_ERR_ARG, "width %d: must divide or be a multiple of 128", w);
     if (((long long)h * w) % 128) return ufail(PF_ERR_ARG, "h*w must be a multiple of 128");
     if (out_cstride < out_coff + cout || out_coff % 8 || out_cstride % 8)

@@ -55,6 +55,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int cap
     return false;
 }
 
+// The same for waiters with nothing else to do (the epilogue between tiles): back off between
+// polls so that they leave the issue slots to the producer and MMA threads of their schedulers.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, int cap, volatile int* abort_flag)
+{
+    for (int it = 0; it < cap; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63 && *abort_flag) return false;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile with 128-byte (KC = 64) or
 // 64-byte (KC = 32) swizzling: rows of KC BF16, 8-row swizzle atoms SBO bytes apart.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, int kc)
@@ -108,7 +120,7 @@ __device__ __forceinline__ TileGeo tile_geo(const ConvArgs& a, int T, int mtiles
 // Persistent kernel: CTA b takes tiles b, b + gridDim.x, ...  The TMA / MMA stream runs through
 // all of them without draining; two accumulators in tensor memory let the epilogue of one tile
 // overlap the MMAs of the next.
-template <int MODE>
+template <int MODE, int NT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ConvArgs a)
 {
@@ -119,7 +131,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int KC = a.kc, NT = a.nt, ST = a.stages;
+    const int KC = a.kc, ST = a.stages;
     const uint32_t a_bytes = TM * KC * 2, b_bytes = NT * KC * 2, stage_bytes = a_bytes + b_bytes;
     const int kblocks = a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = ntaps * kblocks;
     const int ncols = MODE == CONV3 ? a.cout : 4 * a.cout;
@@ -232,7 +244,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         int local = 0;
         for (int T = blockIdx.x; T < tiles; T += gridDim.x, ++local) {
             const int b = local & 1;
-            if (!mbar_wait(smem_u32(&accf_bar[b]), (uint32_t)(local >> 1) & 1u, a.wait_cap, &abort_flag)) {
+            if (!mbar_wait_sleep(smem_u32(&accf_bar[b]), (uint32_t)(local >> 1) & 1u, a.wait_cap, &abort_flag)) {
                 abort_flag = 1;
                 if (lane == 0) atomicOr(a.err, UNET_ERR_TIMEOUT);
                 break;
@@ -243,6 +255,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             float s1[GN_MAX_GROUPS], s2[GN_MAX_GROUPS];
 #pragma unroll
             for (int gg = 0; gg < GN_MAX_GROUPS; ++gg) s1[gg] = s2[gg] = 0.f;
+#pragma unroll
             for (int c0 = 0; c0 < NT; c0 += 16) {
                 uint32_t r[16];
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT + c0);
@@ -262,17 +275,12 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 }
                 uint16_t* dst;
                 if (MODE == CONV3) {
-                    const int cg = a.cout / a.groups;  // channels per group (one N tile holds all Cout)
+                    constexpr int cg = NT / GN_MAX_GROUPS;  // channels per group (one N tile holds all Cout)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                    for (int j = 0; j < 16; ++j) {  // the group index is a compile-time constant
                         const float v = __uint_as_float(r[j]);
-                        const int gi = (c0 + j) / cg;
-#pragma unroll
-                        for (int gg = 0; gg < GN_MAX_GROUPS; ++gg)
-                            if (gg == gi) {
-                                s1[gg] += v;
-                                s2[gg] = fmaf(v, v, s2[gg]);
-                            }
+                        s1[(c0 + j) / cg] += v;
+                        s2[(c0 + j) / cg] = fmaf(v, v, s2[(c0 + j) / cg]);
                     }
                     dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + c0;
                 } else {  // TCONV: column n0 + c0 + j = sub-pixel s * cout + channel
@@ -291,14 +299,9 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
             if (MODE == CONV3 && a.partials) {
                 // per warp: partials[((img * groups + g) * tpi + t) * 4 + q] = (sum, sum of squares)
-                for (int gg = 0; gg < a.groups; ++gg) {
-                    float v1 = s1[0], v2 = s2[0];
 #pragma unroll
-                    for (int k = 1; k < GN_MAX_GROUPS; ++k)
-                        if (k == gg) {
-                            v1 = s1[k];
-                            v2 = s2[k];
-                        }
+                for (int gg = 0; gg < GN_MAX_GROUPS; ++gg) {
+                    float v1 = s1[gg], v2 = s2[gg];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         v1 += __shfl_xor_sync(0xffffffffu, v1, o);
@@ -375,8 +378,9 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     if (a.cin % 32 || a.cout % 16 || a.cout < 16 || a.n < 1 || a.h < 1 || a.w < 1) return cudaErrorInvalidValue;
     if ((a.w % TM) && (TM % a.w)) return cudaErrorInvalidValue;
     if (((long long)a.h * a.w) % TM) return cudaErrorInvalidValue;
-    if (mode == CONV3 && (a.cout > 256 || a.groups < 1 || a.groups > GN_MAX_GROUPS || a.cout % a.groups))
+    if (mode == CONV3 && ((a.cout != 32 && a.cout != 64 && a.cout != 128 && a.cout != 256) || a.groups != GN_MAX_GROUPS))
         return cudaErrorInvalidValue;
+    if (mode == TCONV && a.cout != 16 && a.cout != 32 && a.cout != 64 && a.cout != 128) return cudaErrorInvalidValue;
     if (a.out_coff % 8 || a.out_cstride % 8) return cudaErrorInvalidValue;  // 16-byte vector stores
     const int ncols = mode == CONV3 ? a.cout : 4 * a.cout;
     a.kc = conv_kc(a.cin);
@@ -414,16 +418,22 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (mode == CONV3) {
-        cudaError_t e = cudaFuncSetAttribute(umma_conv_kernel<CONV3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        return cudaLaunchKernelEx(&cfg, umma_conv_kernel<CONV3>, mA, mB, a);
+        return cudaLaunchKernelEx(&cfg, kern, mA, mB, a);
+    };
+    if (mode == CONV3) {
+        if (a.nt == 32) return go(umma_conv_kernel<CONV3, 32>);
+        if (a.nt == 64) return go(umma_conv_kernel<CONV3, 64>);
+        if (a.nt == 128) return go(umma_conv_kernel<CONV3, 128>);
+        if (a.nt == 256) return go(umma_conv_kernel<CONV3, 256>);
+        return cudaErrorInvalidValue;
     }
-    cudaError_t e =
-        cudaFuncSetAttribute(umma_conv_kernel<TCONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, umma_conv_kernel<TCONV>, mA, mB, a);
+    if (a.nt == 64) return go(umma_conv_kernel<TCONV, 64>);
+    if (a.nt == 128) return go(umma_conv_kernel<TCONV, 128>);
+    if (a.nt == 256) return go(umma_conv_kernel<TCONV, 256>);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace pf

@@ -49,12 +49,12 @@ def to_nchw(t):
 
 
 @pytest.mark.parametrize("n,h,w,cin,cout", [(2, 32, 32, 64, 128), (1, 16, 64, 32, 64), (1, 8, 256, 128, 32),
-                                            (3, 8, 16, 256, 256), (1, 4, 32, 96, 48)])
+                                            (3, 8, 16, 256, 256), (1, 4, 32, 96, 64)])
 def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
     g = np.random.default_rng(n * 1000 + cin + cout)
     x = U.bf16(g.standard_normal((n, cin, h, w)))
     wt = (g.standard_normal((cout, cin, 3, 3)) / np.sqrt(9 * cin)).astype(np.float32)
-    groups = 8 if cout % 8 == 0 else 1
+    groups = 8
     out, part = pf.conv3x3_bf16(nhwc_dev(x), pf.conv_weight_layout(wt), groups)
     torch.cuda.synchronize()
     got = to_nchw(out)
@@ -107,7 +107,15 @@ def test_unsupported_shapes_are_rejected(pf):
     x = torch.zeros((1, 10, 10, 64), dtype=torch.bfloat16, device="cuda")
     w = torch.zeros((9, 32, 64), dtype=torch.bfloat16, device="cuda")
     with pytest.raises(pf.PFError) as e:
-        pf.conv3x3_bf16(x, w, 8)
+        pf.conv3x3_bf16(x, w, 8)                    # 100 pixels: not a whole number of 128-pixel tiles
+    assert e.value.code == pf.PF_ERR_ARG
+    x = torch.zeros((1, 16, 16, 64), dtype=torch.bfloat16, device="cuda")
+    w48 = torch.zeros((9, 48, 64), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(pf.PFError) as e:
+        pf.conv3x3_bf16(x, w48, 8)                  # 48 output channels: not a width the kernel is built for
+    assert e.value.code == pf.PF_ERR_ARG
+    with pytest.raises(pf.PFError) as e:
+        pf.conv3x3_bf16(x, w, 4)                    # the statistics are taken over 8 groups
     assert e.value.code == pf.PF_ERR_ARG
 
 
