@@ -143,10 +143,10 @@ int pf_set_step(pf_handle* h, long step);
  * of 0 makes every wait give up at once, to exercise that path. */
 int pf_set_wait_limit(pf_handle* h, int polls);
 
-/* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids of
- * at least 64 columns and one staged window of rows: 16 rows up to 2^20 cells, 32
- * above), 0 when every tile uses per-thread asynchronous copies (smaller grids, or
- * a driver without tensor-map support); -1 on NULL. */
+/* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids with
+ * at least one interior tile: nx >= 116 and ny >= 20 up to 2^20 cells, ny >= 52
+ * above), 0 when every tile uses per-thread asynchronous copies (smaller grids, or a
+ * driver without tensor-map support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
 
 /* Clear the sticky device error word (async). */

@@ -89,8 +89,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
                     StepMaps* out)
 {
-    const int LY = tile_height(tile) + 8;
-    if (nx < 64 || ny < LY) return false;  // no tile can be interior: the TMA path is never taken
+    const int TY = tile_height(tile), LY = TY + 8;
+    // an interior tile exists only if the second tile column and row keep their whole staged window
+    // inside the grid (x0 = 56, y0 = TY, 4-cell halo); otherwise the TMA path would never be taken
+    if (nx < 56 + 60 || ny < TY + LY - 4) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {cuuint64_t(nx), cuuint64_t(ny)};

@@ -137,7 +137,7 @@ UnetLayout unet_layout(int n, int h, int w)
                               P3 * 128, P3 * 256, P3 * 256, P3 * 256, P2 * 128, P1 * 64, P0 * 32, 0};
     for (int k = 0; k < 16; ++k) L.act[k] = take(2 * elems[k]);
     L.partials = take(sizeof(float) * (size_t)n * 8 * (h * (size_t)w / 128) * 4 * 2);
-    L.stats = take(sizeof(float) * (size_t)n * 8 * 2);
+    L.stats = take(sizeof(float) * (size_t)n * 256 * 2);  // per-channel GN affine (a, b) of the current layer
     L.scales = take(sizeof(float) * 480);
     L.err = take(sizeof(int));
     L.ptrs = take(sizeof(float*) * 3 * (size_t)n);
@@ -170,8 +170,10 @@ int upload(pf_unet* u, size_t off, const void* src, size_t bytes)
     return PF_OK;
 }
 
+// One tensor-core convolution; with gamma/beta, also its group statistics folded into the
+// per-channel affine of the normalisation that follows (in the stats buffer).
 int conv_tc(pf_unet* u, int mode, const uint16_t* in, int h, int w, int cin, const uint16_t* wgt, int cout,
-            uint16_t* out, int cstride, int coff, bool stats_too)
+            uint16_t* out, int cstride, int coff, const float* gamma = nullptr, const float* beta = nullptr)
 {
     pf::ConvArgs a = {};
     a.n = u->n;
@@ -183,6 +185,7 @@ int conv_tc(pf_unet* u, int mode, const uint16_t* in, int h, int w, int cin, con
     a.out = out;
     a.out_cstride = cstride;
     a.out_coff = coff;
+    const bool stats_too = gamma != nullptr;
     a.partials = stats_too ? u->at<float>(u->L.partials) : nullptr;
     a.err = u->at<int>(u->L.err);
     a.wait_cap = 1 << 22;
@@ -190,7 +193,8 @@ int conv_tc(pf_unet* u, int mode, const uint16_t* in, int h, int w, int cin, con
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "tensor-core convolution: %s", cudaGetErrorString(e));
     if (!stats_too) return PF_OK;
     e = pf::launch_gn_stats(u->at<float>(u->L.partials), u->n, pf::GN_MAX_GROUPS, h * w / 128 * 4,
-                            (double)(cout / pf::GN_MAX_GROUPS) * h * w, u->at<float>(u->L.stats), u->stream);
+                            (double)(cout / pf::GN_MAX_GROUPS) * h * w, cout, gamma, beta, u->at<float>(u->L.stats),
+                            u->stream);
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "group statistics: %s", cudaGetErrorString(e));
     return PF_OK;
 }
@@ -336,7 +340,7 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     auto gam = [&](int k) { return u->at<float>(L.gb[k][0]); };
     auto bet = [&](int k) { return u->at<float>(L.gb[k][1]); };
     const int G = pf::GN_MAX_GROUPS;
-    int rc = PF_OK;
+    int rc = PF_OK;  // G: the 8 groups of the first block's statistics
     auto ck = [&](cudaError_t ce, const char* what) {
         if (rc == PF_OK && ce != cudaSuccess) rc = ufail(PF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ce));
     };
@@ -349,26 +353,33 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     // ---- encoder
     ck(pf::launch_in_conv(dp, dp + n, dp + 2 * n, pitch, n, H, W, (float)tau, u->at<float>(L.win), act(A_PRE1), part, s),
        "input conv");
-    ck(pf::launch_gn_stats(part, n, G, H * W / 128, 4.0 * H * W, stats, s), "statistics");
-    ck(pf::launch_gn_enc(act(A_PRE1), n, H, W, 32, G, stats, gam(0), bet(0), sc, act(A_CAT1), 64, act(A_P1), s), "level 1");
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P1), H / 2, W / 2, 32, u->at<uint16_t>(L.wc[0]), 64, act(A_PRE2), 64, 0, true);
-    ck(pf::launch_gn_enc(act(A_PRE2), n, H / 2, W / 2, 64, G, stats, gam(1), bet(1), sc + 32, act(A_CAT2), 128, act(A_P2), s), "level 2");
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P2), H / 4, W / 4, 64, u->at<uint16_t>(L.wc[1]), 128, act(A_PRE3), 128, 0, true);
-    ck(pf::launch_gn_enc(act(A_PRE3), n, H / 4, W / 4, 128, G, stats, gam(2), bet(2), sc + 96, act(A_CAT3), 256, act(A_P3), s), "level 3");
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_P3), H / 8, W / 8, 128, u->at<uint16_t>(L.wc[2]), 256, act(A_PRE4), 256, 0, true);
-    ck(pf::launch_gn_enc(act(A_PRE4), n, H / 8, W / 8, 256, G, stats, gam(3), bet(3), sc + 224, act(A_ZC4), 256, nullptr, s), "level 4");
+    ck(pf::launch_gn_stats(part, n, G, H * W / 128, 4.0 * H * W, 32, gam(0), bet(0), stats, s), "statistics");
+    ck(pf::launch_gn_enc(act(A_PRE1), n, H, W, 32, stats, sc, act(A_CAT1), 64, act(A_P1), s), "level 1");
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_P1), H / 2, W / 2, 32, u->at<uint16_t>(L.wc[0]), 64, act(A_PRE2), 64, 0, gam(1), bet(1));
+    ck(pf::launch_gn_enc(act(A_PRE2), n, H / 2, W / 2, 64, stats, sc + 32, act(A_CAT2), 128, act(A_P2), s), "level 2");
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_P2), H / 4, W / 4, 64, u->at<uint16_t>(L.wc[1]), 128, act(A_PRE3), 128, 0, gam(2), bet(2));
+    ck(pf::launch_gn_enc(act(A_PRE3), n, H / 4, W / 4, 128, stats, sc + 96, act(A_CAT3), 256, act(A_P3), s), "level 3");
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_P3), H / 8, W / 8, 128, u->at<uint16_t>(L.wc[2]), 256, act(A_PRE4), 256, 0, gam(3), bet(3));
+    ck(pf::launch_gn_enc(act(A_PRE4), n, H / 8, W / 8, 256, stats, sc + 224, act(A_ZC4), 256, nullptr, s), "level 4");
     // ---- decoder
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_ZC4), H / 8, W / 8, 256, u->at<uint16_t>(L.wc[3]), 256, act(A_PRE4), 256, 0, true);
-    ck(pf::launch_gn_dec(act(A_PRE4), n, H / 8, W / 8, 256, G, stats, gam(4), bet(4), act(A_H4), s), "decoder 4");
-    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H4), H / 8, W / 8, 256, u->at<uint16_t>(L.wt[0]), 128, act(A_CAT3), 256, 128, false);
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT3), H / 4, W / 4, 256, u->at<uint16_t>(L.wc[4]), 128, act(A_PRE3), 128, 0, true);
-    ck(pf::launch_gn_dec(act(A_PRE3), n, H / 4, W / 4, 128, G, stats, gam(5), bet(5), act(A_H3), s), "decoder 3");
-    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H3), H / 4, W / 4, 128, u->at<uint16_t>(L.wt[1]), 64, act(A_CAT2), 128, 64, false);
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT2), H / 2, W / 2, 128, u->at<uint16_t>(L.wc[5]), 64, act(A_PRE2), 64, 0, true);
-    ck(pf::launch_gn_dec(act(A_PRE2), n, H / 2, W / 2, 64, G, stats, gam(6), bet(6), act(A_H2), s), "decoder 2");
-    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H2), H / 2, W / 2, 64, u->at<uint16_t>(L.wt[2]), 32, act(A_CAT1), 64, 32, false);
-    if (rc == PF_OK) rc = conv_tc(u, pf::CONV3, act(A_CAT1), H, W, 64, u->at<uint16_t>(L.wc[6]), 32, act(A_PRE1), 32, 0, true);
-    ck(pf::launch_gn_dec(act(A_PRE1), n, H, W, 32, G, stats, gam(7), bet(7), act(A_H1), s), "decoder 1");
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_ZC4), H / 8, W / 8, 256, u->at<uint16_t>(L.wc[3]), 256, act(A_PRE4), 256, 0, gam(4), bet(4));
+    ck(pf::launch_gn_dec(act(A_PRE4), n, H / 8, W / 8, 256, stats, act(A_H4), s), "decoder 4");
+    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H4), H / 8, W / 8, 256, u->at<uint16_t>(L.wt[0]), 128, act(A_CAT3), 256, 128);
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_CAT3), H / 4, W / 4, 256, u->at<uint16_t>(L.wc[4]), 128, act(A_PRE3), 128, 0, gam(5), bet(5));
+    ck(pf::launch_gn_dec(act(A_PRE3), n, H / 4, W / 4, 128, stats, act(A_H3), s), "decoder 3");
+    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H3), H / 4, W / 4, 128, u->at<uint16_t>(L.wt[1]), 64, act(A_CAT2), 128, 64);
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_CAT2), H / 2, W / 2, 128, u->at<uint16_t>(L.wc[5]), 64, act(A_PRE2), 64, 0, gam(6), bet(6));
+    ck(pf::launch_gn_dec(act(A_PRE2), n, H / 2, W / 2, 64, stats, act(A_H2), s), "decoder 2");
+    if (rc == PF_OK) rc = conv_tc(u, pf::TCONV, act(A_H2), H / 2, W / 2, 64, u->at<uint16_t>(L.wt[2]), 32, act(A_CAT1), 64, 32);
+    if (rc == PF_OK)
+        rc = conv_tc(u, pf::CONV3, act(A_CAT1), H, W, 64, u->at<uint16_t>(L.wc[6]), 32, act(A_PRE1), 32, 0, gam(7), bet(7));
+    ck(pf::launch_gn_dec(act(A_PRE1), n, H, W, 32, stats, act(A_H1), s), "decoder 1");
     // ---- output: conv 32 -> 3 as affine increments of the DNS fields
     ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch, s),
        "output");

@@ -7,7 +7,8 @@
 //   in_conv_kernel  the first 3x3 convolution (4 -> 32 channels) straight from the DNS
 //                   fields (phi, c, rho and a plane holding dt / dt_ref), with its group sums
 //   out_conv_kernel the last 3x3 convolution (32 -> 3) as affine increments of the DNS fields
-//   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums, FP64, fixed order
+//   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums (FP64, fixed order),
+//                   folded with gamma and beta into a per-channel affine a x + b
 //   gn_apply_*      GN + GELU (+ conditioning product, + 2x2 max pooling) on stored BF16 values
 //
 // Storage follows the precision model of the reference: every stored activation is BF16
@@ -41,18 +42,6 @@ __device__ __forceinline__ float gelu(float u)
     return 0.5f * u * (1.0f + tanhf(0.7978845608028654f * (u + 0.044715f * u * u * u)));
 }
 
-// Sum of `v` over a 128-thread block in a fixed order (warp butterfly, then warps 0..3).
-__device__ __forceinline__ float block_sum128(float v, float* red)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    return red[0] + red[1] + red[2] + red[3];
-}
-
 __global__ void cond_kernel(const double* __restrict__ mlp, const double* __restrict__ proj, double tau,
                             float* __restrict__ scales, int nscales)
 {
@@ -84,7 +73,8 @@ __global__ void cond_kernel(const double* __restrict__ mlp, const double* __rest
 }
 
 // First convolution: x = BF16(phi, c, rho, tau) with zero padding outside the image, 3x3, 4 -> 32.
-// One thread per output pixel, one 128-pixel tile per block.
+// One thread per output pixel, one 128-pixel tile per block (neighbours come through L1: staging
+// the halo in shared memory measured slower).  Group sums: one warp butterfly over all 16 values.
 __global__ void __launch_bounds__(TPB)
 in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
                const float* const* __restrict__ rho, int pitch, int h, int w, float tau,
@@ -92,7 +82,7 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
                float* __restrict__ partials)
 {
     __shared__ float ws[36 * 32];
-    __shared__ float red[4];
+    __shared__ float red[4][16];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = threadIdx.x; i < 36 * 32; i += TPB) ws[i] = wgt[i];
     __syncthreads();
@@ -129,21 +119,30 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
             pk[j] = (uint32_t)to_bf(acc[8 * q + 2 * j]) | ((uint32_t)to_bf(acc[8 * q + 2 * j + 1]) << 16);
         dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
-    // group sums: 8 groups of 4 channels
+    // group sums (8 groups of 4 channels): per thread, then one butterfly per value, then 4 warps
+    float sv[16];
+#pragma unroll
     for (int g = 0; g < 8; ++g) {
         float s1 = 0.f, s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float v = acc[4 * g + j];
-            s1 += v;
-            s2 = fmaf(v, v, s2);
+            s1 += acc[4 * g + j];
+            s2 = fmaf(acc[4 * g + j], acc[4 * g + j], s2);
         }
-        s1 = block_sum128(s1, red);
-        s2 = block_sum128(s2, red);
-        if (threadIdx.x == 0) {
-            partials[(((size_t)img * 8 + g) * tpi + t) * 2 + 0] = s1;
-            partials[(((size_t)img * 8 + g) * tpi + t) * 2 + 1] = s2;
-        }
+        sv[2 * g] = s1;
+        sv[2 * g + 1] = s2;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv[k] += __shfl_xor_sync(0xffffffffu, sv[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) red[threadIdx.x >> 5][k] = sv[k];
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        const int g = threadIdx.x >> 1, which = threadIdx.x & 1;
+        partials[(((size_t)img * 8 + g) * tpi + t) * 2 + which] = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -190,14 +189,20 @@ out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __re
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// (mean, 1/sqrt(var + eps)) per image and group from the per-tile sums, FP64 in a fixed order.
-__global__ void gn_stats_kernel(const float* __restrict__ partials, int tpi, double count, float* __restrict__ stats)
+// Group statistics -> per-channel affine of the normalisation: block (image, group) sums its
+// `entries` partial (sum, sum of squares) pairs in FP64 in a fixed order, and writes for every
+// channel k of the group affine = (a, b) with a = gamma_k / sqrt(var + eps), b = beta_k - mean a,
+// so that GN(x) = a x + b.
+__global__ void gn_stats_kernel(const float* __restrict__ partials, int entries, double count, int C, int groups,
+                                const float* __restrict__ gamma, const float* __restrict__ beta,
+                                float* __restrict__ affine)
 {
     __shared__ double r1[TPB], r2[TPB];
+    __shared__ float mr[2];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const float* p = partials + (size_t)blockIdx.x * tpi * 2;
+    const float* p = partials + (size_t)blockIdx.x * entries * 2;
     double s1 = 0.0, s2 = 0.0;
-    for (int t = threadIdx.x; t < tpi; t += TPB) {
+    for (int t = threadIdx.x; t < entries; t += TPB) {
         s1 += (double)p[2 * t];
         s2 += (double)p[2 * t + 1];
     }
@@ -215,28 +220,35 @@ __global__ void gn_stats_kernel(const float* __restrict__ partials, int tpi, dou
         const double mean = r1[0] / count;
         double var = r2[0] / count - mean * mean;
         var = var < 0.0 ? 0.0 : var;
-        stats[2 * blockIdx.x] = (float)mean;
-        stats[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var + (double)UNET_EPS));
+        mr[0] = (float)mean;
+        mr[1] = (float)(1.0 / sqrt(var + (double)UNET_EPS));
+    }
+    __syncthreads();
+    const int img = blockIdx.x / groups, g = blockIdx.x % groups, cg = C / groups;
+    for (int k = threadIdx.x; k < cg; k += TPB) {
+        const int ch = g * cg + k;
+        const float sc = mr[1] * gamma[ch];
+        affine[((size_t)img * C + ch) * 2] = sc;
+        affine[((size_t)img * C + ch) * 2 + 1] = fmaf(-mr[0], sc, beta[ch]);
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-struct Gn8 {  // GN parameters of 8 consecutive channels
-    float m[8], r[8], g[8], b[8];
+// (a, b) of 8 consecutive channels: four 16-byte loads
+struct Aff8 {
+    float a[8], b[8];
 };
-
-__device__ __forceinline__ Gn8 gn8(const float* stats, const float* gamma, const float* beta, int img, int groups,
-                                   int C, int c0)
+__device__ __forceinline__ Aff8 aff8(const float* affine, int img, int C, int c0)
 {
-    Gn8 q;
-    const int cg = C / groups;
+    Aff8 q;
+    const float4* p = reinterpret_cast<const float4*>(affine + ((size_t)img * C + c0) * 2);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int ch = c0 + j, g = ch / cg;
-        q.m[j] = stats[2 * (img * groups + g)];
-        q.r[j] = stats[2 * (img * groups + g) + 1];
-        q.g[j] = gamma[ch];
-        q.b[j] = beta[ch];
+    for (int k = 0; k < 4; ++k) {
+        const float4 v = p[k];
+        q.a[2 * k] = v.x;
+        q.b[2 * k] = v.y;
+        q.a[2 * k + 1] = v.z;
+        q.b[2 * k + 1] = v.w;
     }
     return q;
 }
@@ -262,9 +274,8 @@ __device__ __forceinline__ uint4 pack8(const float* f)
 // Encoder level: z = BF16(GELU(GN(x))); zc = BF16(z * s) into the skip slice (channels [0, C) of a
 // buffer with cat_stride channels); pool (if not NULL) = 2x2 max of z.  One thread per 8 channels
 // of a 2x2 pixel block (pool) or of one pixel (no pool).
-__global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h, int w, int C, int groups,
-                                    const float* __restrict__ stats, const float* __restrict__ gamma,
-                                    const float* __restrict__ beta, const float* __restrict__ scale,
+__global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h, int w, int C,
+                                    const float* __restrict__ affine, const float* __restrict__ scale,
                                     uint16_t* __restrict__ cat, int cat_stride, uint16_t* __restrict__ pool)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -279,7 +290,7 @@ __global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h
         r /= pw;
         const int py = (int)(r % ph);
         const int img = (int)(r / ph);
-        const Gn8 q = gn8(stats, gamma, beta, img, groups, C, cb * 8);
+        const Aff8 q = aff8(affine, img, C, cb * 8);
         float s[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) s[j] = scale[cb * 8 + j];
@@ -294,7 +305,7 @@ __global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h
             unpack8(reinterpret_cast<const uint4*>(x + pix * C)[cb], v);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                z[j] = rbf(gelu((v[j] - q.m[j]) * q.r[j] * q.g[j] + q.b[j]));
+                z[j] = rbf(gelu(fmaf(v[j], q.a[j], q.b[j])));
                 zc[j] = z[j] * s[j];
                 mx[j] = fmaxf(mx[j], z[j]);
             }
@@ -306,9 +317,8 @@ __global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h
 }
 
 // Decoder level: y = BF16(GELU(GN(x))), NHWC with C channels.
-__global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pixels, int C, int hw, int groups,
-                                    const float* __restrict__ stats, const float* __restrict__ gamma,
-                                    const float* __restrict__ beta, uint16_t* __restrict__ y)
+__global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pixels, int C, int hw,
+                                    const float* __restrict__ affine, uint16_t* __restrict__ y)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int c8 = C / 8;
@@ -318,11 +328,11 @@ __global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pi
         const int cb = (int)(i % c8);
         const long long pix = i / c8;
         const int img = (int)(pix / hw);
-        const Gn8 q = gn8(stats, gamma, beta, img, groups, C, cb * 8);
+        const Aff8 q = aff8(affine, img, C, cb * 8);
         float v[8];
         unpack8(reinterpret_cast<const uint4*>(x + pix * C)[cb], v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = gelu((v[j] - q.m[j]) * q.r[j] * q.g[j] + q.b[j]);
+        for (int j = 0; j < 8; ++j) v[j] = gelu(fmaf(v[j], q.a[j], q.b[j]));
         reinterpret_cast<uint4*>(y + pix * C)[cb] = pack8(v);
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -395,32 +405,30 @@ cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float
     return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, gamma, beta, phi, c, rho, pitch);
 }
 
-cudaError_t launch_gn_stats(const float* partials, int n, int groups, int tpi, double count, float* stats,
-                            cudaStream_t s)
+cudaError_t launch_gn_stats(const float* partials, int n, int groups, int entries, double count, int C,
+                            const float* gamma, const float* beta, float* affine, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * groups)), TPB, s, attr);
-    return cudaLaunchKernelEx(&cfg, gn_stats_kernel, partials, tpi, count, stats);
+    return cudaLaunchKernelEx(&cfg, gn_stats_kernel, partials, entries, count, C, groups, gamma, beta, affine);
 }
 
-cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
-                          const float* gamma, const float* beta, const float* scale, uint16_t* cat, int cat_stride,
-                          uint16_t* pool, cudaStream_t s)
+cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, const float* affine, const float* scale,
+                          uint16_t* cat, int cat_stride, uint16_t* pool, cudaStream_t s)
 {
     const long long items = (long long)n * (pool ? (h / 2) * (w / 2) : h * w) * (C / 8);
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(items, 256)), 256, s, attr);
-    return cudaLaunchKernelEx(&cfg, gn_apply_enc_kernel, x, n, h, w, C, groups, stats, gamma, beta, scale, cat,
-                              cat_stride, pool);
+    return cudaLaunchKernelEx(&cfg, gn_apply_enc_kernel, x, n, h, w, C, affine, scale, cat, cat_stride, pool);
 }
 
-cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
-                          const float* gamma, const float* beta, uint16_t* y, cudaStream_t s)
+cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, const float* affine, uint16_t* y,
+                          cudaStream_t s)
 {
     const long long pixels = (long long)n * h * w;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(pixels * (C / 8), 256)), 256, s, attr);
-    return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, pixels, C, h * w, groups, stats, gamma, beta, y);
+    return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, pixels, C, h * w, affine, y);
 }
 
 cudaError_t launch_check(const float* const* phi, const float* const* c, const float* const* rho, int n, int h, int w,

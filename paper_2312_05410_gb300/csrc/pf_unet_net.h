@@ -16,13 +16,12 @@ cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const
 cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, const float* gamma,
                             const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
                             cudaStream_t s);
-cudaError_t launch_gn_stats(const float* partials, int n, int groups, int tpi, double count, float* stats,
-                            cudaStream_t s);
-cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
-                          const float* gamma, const float* beta, const float* scale, uint16_t* cat, int cat_stride,
-                          uint16_t* pool, cudaStream_t s);
-cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, int groups, const float* stats,
-                          const float* gamma, const float* beta, uint16_t* y, cudaStream_t s);
+cudaError_t launch_gn_stats(const float* partials, int n, int groups, int entries, double count, int C,
+                            const float* gamma, const float* beta, float* affine, cudaStream_t s);
+cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, const float* affine, const float* scale,
+                          uint16_t* cat, int cat_stride, uint16_t* pool, cudaStream_t s);
+cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, const float* affine, uint16_t* y,
+                          cudaStream_t s);
 cudaError_t launch_check(const float* const* phi, const float* const* c, const float* const* rho, int n, int h, int w,
                          int pitch, float phi_lo, float phi_hi, float c_lo, float c_hi, float r_lo, float r_hi,
                          int* flags, cudaStream_t s);

@@ -83,10 +83,10 @@ def test_rough_random_fields(pf):
 
 
 def test_tma_staged_small_tiles_match_oracle(pf):
-    """Grids up to 2^20 cells use the 56 x 8 tile; interior tiles are TMA-staged once the grid holds a 64 x 16
-    window.  Ragged sizes mix both staging paths."""
+    """Grids up to 2^20 cells use the 56 x 8 tile; interior tiles are TMA-staged once the grid has one
+    (nx >= 116, ny >= 20).  Ragged sizes mix both staging paths."""
     p = O.with_dt(I.default_params(v_angle_deg=70.0))
-    for nx, ny in ((64, 16), (130, 70), (200, 64)):
+    for nx, ny in ((116, 20), (130, 70), (200, 64)):
         state = I.film_state(I.FilmSpec(nx, ny, ny / 3.0, seed=nx + ny), p)
         got, _ = run_gpu(pf, p, state, 100)
         assert max_err(got, O.step(p, *state, 100)) <= 1e-5, (nx, ny)
@@ -147,8 +147,8 @@ def test_composition_conserved_long_run(pf):
 
 def test_tma_staging_is_used_where_tiles_fit(pf):
     p = O.with_dt(I.default_params())
-    for (nx, ny), mode in (((2048, 1024), 1), ((1120, 960), 1), ((512, 512), 1), ((64, 16), 1), ((63, 40), 0),
-                           ((96, 15), 0), ((37, 23), 0)):
+    for (nx, ny), mode in (((2048, 1024), 1), ((1120, 960), 1), ((512, 512), 1), ((116, 20), 1), ((115, 40), 0),
+                           ((200, 19), 0), ((64, 64), 0), ((37, 23), 0)):
         sim = pf.Sim(p, *I.film_state(I.FilmSpec(nx, ny, ny / 3.0, seed=1), p))
         assert pf.pf_staging_mode(sim.h) == mode, (nx, ny)
         sim.close()
