@@ -14,15 +14,19 @@
 // accumulator of 128 lanes x N columns in tensor memory.  Four epilogue warps
 // then read it back with tcgen05.ld.
 //
-// Pipeline: warp 0 produces (TMA), warp 1 allocates tensor memory and issues the
-// MMAs, warps 2-5 run the epilogue; ST shared-memory stages with full/empty
-// mbarriers.  Every wait is bounded: a wait that runs out sets the error word,
-// and the CTA drains what it issued (bounded again) and frees its tensor memory.
+// Pipeline: a persistent CTA per SM walks its tiles.  Warp 0 produces (TMA), warp
+// 1 allocates tensor memory and issues the MMAs, warps 2-5 run the epilogue; ST
+// shared-memory stages with full/empty mbarriers carry the stream across tiles
+// without draining, and two accumulators (2 N columns of tensor memory) let the
+// epilogue of one tile overlap the MMAs of the next.  Every wait is bounded: a wait
+// that runs out sets the error word, and the CTA drains what it issued (bounded
+// again) and frees its tensor memory.  The N tile is a template parameter, so the
+// epilogue's loops unroll and its group indices are compile-time constants.
 //
 // Epilogues: CONV3 stores the raw convolution (BF16, into a channel slice of an
-// NHWC buffer) and per-CTA sums of the FP32 values and of their squares per
-// normalisation group; TCONV scatters each input pixel's 4 x Cout outputs to the
-// 2x2 block of output pixels it feeds.
+// NHWC buffer) and, per 32-pixel quarter of each tile, the sums of the FP32
+// values and of their squares per normalisation group; TCONV scatters each input
+// pixel's 4 x Cout outputs to the 2x2 block of output pixels it feeds.
 #include <cstdint>
 #include <cstring>
 
