@@ -120,6 +120,30 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// The passes work on tiles of ATX x ATY cells.  Each block stages, for its tile and a one-cell
+// halo, every operand the stencils read into shared memory.  A halo cell (gj, gi) holds the value
+// at the reflected row and wrapped column, exactly what the forward's ghost rules read there.
+// The rules that are not copies (rho_top above the top, the negated or zero ghosts of the
+// transposes) are applied where the value is used, from the neighbour's global row.
+constexpr int ATX = 32, ATY = ADJ_THREADS / ATX;
+constexpr int AW = ATX + 2, AH = ATY + 2;
+
+// Fill the staged tile of `nf` fields (rows j0-1 .. j0+ATY, columns i0-1 .. i0+ATX); cells
+// beyond the first halo ring outside the grid are never read and hold 0.
+template <int NF>
+__device__ __forceinline__ void stage_tile(float (*S)[AH][AW], const float* const* f, int j0, int i0, int nx, int ny,
+                                           int pitch)
+{
+    for (int e = threadIdx.x; e < AH * AW; e += ADJ_THREADS) {
+        const int r = e / AW, cc = e - r * AW;
+        const int gj = j0 - 1 + r, gi = i0 - 1 + cc;
+        const bool ok = gj >= -1 && gj <= ny && gi >= -1 && gi <= nx;
+        const size_t src = ok ? (size_t)refl(gj, ny) * pitch + wrapx(gi, nx) : 0;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) S[q][r][cc] = ok ? f[q][src] : 0.f;
+    }
+}
+
 // Pass A. x: cotangent (phi, c, rho); v: state. Writes mu_c_bar, M_bar, mu_phi_bar, s_bar
 // and per-block partials {V, m_scale, kappa_c} (FP64, fixed order).
 __global__ void __launch_bounds__(ADJ_THREADS)
@@ -127,26 +151,35 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
              const float* __restrict__ vrho, const float* __restrict__ xphi, const float* __restrict__ xc,
              const float* __restrict__ xrho, const float* __restrict__ muc, const float* __restrict__ Mc,
              float* __restrict__ muc_bar, float* __restrict__ M_bar, float* __restrict__ muf_bar,
-             float* __restrict__ s_bar, double* __restrict__ partials, unsigned* __restrict__ ticket,
-             double pscale, double* __restrict__ acc)
+             float* __restrict__ s_bar, double* __restrict__ partials, double pscale)
 {
+    __shared__ float S[7][AH][AW];  // muc, Mc, xc, xphi, vc, vphi, vrho
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
-    const long long n = (long long)nx * ny;
+    const int ntx = (nx + ATX - 1) / ATX, ntiles = ntx * ((ny + ATY - 1) / ATY);
+    const int tx = threadIdx.x % ATX, ty = threadIdx.x / ATX;
+    const float* const fl[7] = {muc, Mc, xc, xphi, vc, vphi, vrho};
     double accV = 0.0, accM = 0.0, accK = 0.0;
-    for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * ADJ_THREADS) {
-        const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j0 = (tile / ntx) * ATY, i0 = (tile % ntx) * ATX;
+        __syncthreads();  // the previous tile's readers are done
+        stage_tile<7>(S, fl, j0, i0, nx, ny, pitch);
+        __syncthreads();
+        const int j = j0 + ty, i = i0 + tx;
+        if (j >= ny || i >= nx) continue;
         const size_t o = (size_t)j * pitch + i;
-        const int nj[4] = {j, j, j + 1, j - 1}, ni[4] = {i + 1, i - 1, i, i};
-        const float m0 = muc[o], M0 = Mc[o];
-        const float wc = xc[o];
+        const int y = ty + 1, x = tx + 1;  // staged position of (j, i)
+        // staged value of field q at the neighbour (j + dj, i + di)
+        auto at = [&](int q, int dj, int di) { return S[q][y + dj][x + di]; };
+        const int dj4[4] = {0, 0, 1, -1}, di4[4] = {1, -1, 0, 0};
+        const float m0 = at(0, 0, 0), M0 = at(1, 0, 0);
+        const float wc = at(2, 0, 0);
         float mub = 0.f, Mb = 0.f, Rc = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             // a ghost neighbour is the mirror copy: its mu and M equal the boundary cell's
-            const float mn = mirror_at(muc, nj[q], ni[q], nx, ny, pitch), Mn = mirror_at(Mc, nj[q], ni[q], nx, ny, pitch);
-            const float dw = mirror_at(xc, nj[q], ni[q], nx, ny, pitch) - wc;
+            const float mn = at(0, dj4[q], di4[q]), Mn = at(1, dj4[q], di4[q]);
+            const float dw = at(2, dj4[q], di4[q]) - wc;
             mub += (M0 + Mn) * dw;
             Mb -= (mn - m0) * dw;
             Rc += (M0 + Mn) * (mn - m0);
@@ -154,11 +187,10 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
         mub *= a.k.cR;
         Mb *= a.k.cR;
         Rc *= a.k.cR;
-        const float wf = xphi[o], wr = xrho[o];
+        const float wf = at(3, 0, 0), wr = xrho[o];
         float mfb;
         if (a.phi_mode == 0) {
-            const float s = mirror_at(xphi, j, i + 1, nx, ny, pitch) + mirror_at(xphi, j, i - 1, nx, ny, pitch) +
-                            mirror_at(xphi, j + 1, i, nx, ny, pitch) + mirror_at(xphi, j - 1, i, nx, ny, pitch);
+            const float s = at(3, 0, 1) + at(3, 0, -1) + at(3, 1, 0) + at(3, -1, 0);
             mfb = a.k.cF * (s - 4.f * wf);
         } else {
             mfb = a.k.cF * wf;
@@ -169,19 +201,21 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
         muf_bar[o] = mfb;
         s_bar[o] = sb;
         // parameter partials
-        const float c0 = vc[o], r0 = vrho[o];
-        const float Lc = mirror_at(vc, j, i + 1, nx, ny, pitch) + mirror_at(vc, j, i - 1, nx, ny, pitch) +
-                         mirror_at(vc, j + 1, i, nx, ny, pitch) + mirror_at(vc, j - 1, i, nx, ny, pitch) - 4.f * c0;
+        const float c0 = at(4, 0, 0), r0 = at(6, 0, 0);
+        const float Lc = at(4, 0, 1) + at(4, 0, -1) + at(4, 1, 0) + at(4, -1, 0) - 4.f * c0;
         accK -= (double)mub * (double)(Lc * a.idx2);  // d mu_c / d kappa_c = -L(c)
         accM += (double)wc * (double)Rc;
-        const float dfx = mirror_at(vphi, j, i + 1, nx, ny, pitch) - mirror_at(vphi, j, i - 1, nx, ny, pitch);
-        const float dfy = mirror_at(vphi, j + 1, i, nx, ny, pitch) - mirror_at(vphi, j - 1, i, nx, ny, pitch);
-        const float drx = rho_at(vrho, j, i + 1, nx, ny, pitch, a.k.rho_top) -
-                          rho_at(vrho, j, i - 1, nx, ny, pitch, a.k.rho_top);
-        const float dry = rho_at(vrho, j + 1, i, nx, ny, pitch, a.k.rho_top) -
-                          rho_at(vrho, j - 1, i, nx, ny, pitch, a.k.rho_top);
+        const float dfx = at(5, 0, 1) - at(5, 0, -1);
+        const float dfy = at(5, 1, 0) - at(5, -1, 0);
+        // rho above the top is the reservoir value
+        auto rh = [&](int dj, int di) { return j + dj >= ny ? a.k.rho_top : at(6, dj, di); };
+        const float drx = rh(0, 1) - rh(0, -1);
+        const float dry = rh(1, 0) - rh(-1, 0);
         accV += (double)(sb * r0 * (a.cx * dfx + a.cy * dfy)) - (double)(wr * (a.cx * drx + a.cy * dry));
     }
+    // Block sum in a fixed order, added (scaled) to this block's own accumulator slot: the slots
+    // collect every call of the adjoint in the same order whatever the checkpoint interval, and
+    // are summed once, in a fixed order, at the end (adj_sum_kernel).
     __shared__ double red[3][ADJ_THREADS / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     accV = warp_sum(accV);
@@ -193,38 +227,33 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
         red[2][w] = accK;
     }
     __syncthreads();
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 3; ++q) {
-            double s = 0.0;
-            for (int t = 0; t < ADJ_THREADS / 32; ++t) s += red[q][t];
-            partials[(size_t)q * gridDim.x + blockIdx.x] = s;
-        }
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x < 3) {
+        const int q = threadIdx.x;
+        double s = 0.0;
+        for (int t = 0; t < ADJ_THREADS / 32; ++t) s += red[q][t];
+        partials[(size_t)q * gridDim.x + blockIdx.x] += pscale * s;
+    }
+}
+
+// acc[q] = sum over the blocks' accumulator slots (fixed order: strided per thread, then the
+// warp butterfly, then the warps in order).  One block.
+__global__ void __launch_bounds__(ADJ_THREADS) adj_sum_kernel(const double* __restrict__ partials, int nb,
+                                                               double* __restrict__ acc)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    __shared__ double red[3][ADJ_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < 3; ++q) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nb; b += ADJ_THREADS) t += partials[(size_t)q * nb + b];
+        t = warp_sum(t);
+        if (lane == 0) red[q][w] = t;
     }
     __syncthreads();
-    if (last) {
-        // The last block to finish adds scale x (sum of the block partials): every thread
-        // sums a fixed strided subset, then the same fixed-order warp/block reduction.
-        __threadfence();
-        double t3[3] = {0.0, 0.0, 0.0};
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += ADJ_THREADS)
-            for (int q = 0; q < 3; ++q) t3[q] += partials[(size_t)q * gridDim.x + b];
-        __syncthreads();  // red[] is reused
-        for (int q = 0; q < 3; ++q) {
-            t3[q] = warp_sum(t3[q]);
-            if (lane == 0) red[q][w] = t3[q];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 3; ++q) {
-                double t = 0.0;
-                for (int i = 0; i < ADJ_THREADS / 32; ++i) t += red[q][i];
-                acc[q] += pscale * t;
-            }
-            *ticket = 0u;
-        }
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int i = 0; i < ADJ_THREADS / 32; ++i) t += red[threadIdx.x][i];
+        acc[threadIdx.x] = t;
     }
 }
 
@@ -238,14 +267,23 @@ vjp_b_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
              const float* __restrict__ b2rho, float* __restrict__ ophi, float* __restrict__ oc,
              float* __restrict__ orho)
 {
+    __shared__ float S[6][AH][AW];  // muc_bar, muf_bar, vrho, s_bar, vphi, xrho
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
-    const long long n = (long long)nx * ny;
-    for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * ADJ_THREADS) {
-        const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
+    const int ntx = (nx + ATX - 1) / ATX, ntiles = ntx * ((ny + ATY - 1) / ATY);
+    const int tx = threadIdx.x % ATX, ty = threadIdx.x / ATX;
+    const float* const fl[6] = {muc_bar, muf_bar, vrho, s_bar, vphi, xrho};
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int j0 = (tile / ntx) * ATY, i0 = (tile % ntx) * ATX;
+        __syncthreads();  // the previous tile's readers are done
+        stage_tile<6>(S, fl, j0, i0, nx, ny, pitch);
+        __syncthreads();
+        const int j = j0 + ty, i = i0 + tx;
+        if (j >= ny || i >= nx) continue;
         const size_t o = (size_t)j * pitch + i;
-        const float f = vphi[o], cc = vc[o], r = vrho[o];
+        const int y = ty + 1, x = tx + 1;
+        auto at = [&](int q, int dj, int di) { return S[q][y + dj][x + di]; };
+        const float f = at(4, 0, 0), cc = vc[o];
         const float P = 0.25f * (2.f - f) * (1.f + f) * (1.f + f);
         const float dP = 0.75f * (1.f - f * f);
         const float d2P = -1.5f * f;
@@ -261,42 +299,36 @@ vjp_b_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
             dMdf += -2.f * f * a.isig2 * e * (h * a.MAs + (1.f - h) * a.MBs);
             dMdc += e * (a.MAs - a.MBs) * dh;
         }
-        const float mub = muc_bar[o], mfb = muf_bar[o], Mb = M_bar[o];
+        const float mub = at(0, 0, 0), mfb = at(1, 0, 0), Mb = M_bar[o];
         // neighbour sums of the mirrored cotangents (symmetric Laplacians)
-        const float Lmub = mirror_at(muc_bar, j, i + 1, nx, ny, pitch) + mirror_at(muc_bar, j, i - 1, nx, ny, pitch) +
-                           mirror_at(muc_bar, j + 1, i, nx, ny, pitch) + mirror_at(muc_bar, j - 1, i, nx, ny, pitch) -
-                           4.f * mub;
-        const float Lmfb = mirror_at(muf_bar, j, i + 1, nx, ny, pitch) + mirror_at(muf_bar, j, i - 1, nx, ny, pitch) +
-                           mirror_at(muf_bar, j + 1, i, nx, ny, pitch) + mirror_at(muf_bar, j - 1, i, nx, ny, pitch) -
-                           4.f * mfb;
+        const float Lmub = at(0, 0, 1) + at(0, 0, -1) + at(0, 1, 0) + at(0, -1, 0) - 4.f * mub;
+        const float Lmfb = at(1, 0, 1) + at(1, 0, -1) + at(1, 1, 0) + at(1, -1, 0) - 4.f * mfb;
         float cb = a.k.Wc * P * d2g * mub - a.k.kc * Lmub + dP * a.k.Wc * dg * mfb + dMdc * Mb;
         const float fpp = a.k.Wf * (3.f * f * f - 1.f) + d2P * a.k.Wc * g;
         float fb = a.k.Wc * dP * dg * mub + fpp * mfb - a.k.kf * Lmfb + dMdf * Mb;
         // transposed central differences of phi in the source: weights a = (ax, ay) rho s_bar
-        auto aw = [&](int jj, int ii) {  // weight at a neighbour; y-ghosts negated (mirror field)
-            const int jr = refl(jj, ny), ir = wrapx(ii, nx);
-            const size_t q = (size_t)jr * pitch + ir;
-            const float sgn = (jj < 0 || jj >= ny) ? -1.f : 1.f;
-            return sgn * vrho[q] * s_bar[q];
+        auto aw = [&](int dj, int di) {  // weight at a neighbour; y-ghosts negated (mirror field)
+            const float sgn = (j + dj < 0 || j + dj >= ny) ? -1.f : 1.f;
+            return sgn * at(2, dj, di) * at(3, dj, di);
         };
-        fb += a.k.ax * (aw(j, i - 1) - aw(j, i + 1)) + a.k.ay * (aw(j - 1, i) - aw(j + 1, i));
+        fb += a.k.ax * (aw(0, -1) - aw(0, 1)) + a.k.ay * (aw(-1, 0) - aw(1, 0));
         // rho: source factor, diffusion with the transposed boundary rules, transposed advection
-        const float sb = s_bar[o];
-        const float dfx = mirror_at(vphi, j, i + 1, nx, ny, pitch) - mirror_at(vphi, j, i - 1, nx, ny, pitch);
-        const float dfy = mirror_at(vphi, j + 1, i, nx, ny, pitch) - mirror_at(vphi, j - 1, i, nx, ny, pitch);
+        const float sb = at(3, 0, 0);
+        const float dfx = at(4, 0, 1) - at(4, 0, -1);
+        const float dfy = at(4, 1, 0) - at(4, -1, 0);
         float rb = sb * (a.k.ax * dfx + a.k.ay * dfy);
-        auto wr_lap = [&](int jj, int ii) {  // mirrored below, zero above the top
-            if (jj >= ny) return 0.f;
-            return xrho[(size_t)refl(jj, ny) * pitch + wrapx(ii, nx)];
+        auto wr_lap = [&](int dj, int di) {  // mirrored below, zero above the top
+            if (j + dj >= ny) return 0.f;
+            return at(5, dj, di);
         };
-        auto wr_dy = [&](int jj, int ii) {  // negated below, zero above the top
-            if (jj >= ny) return 0.f;
-            const float v = xrho[(size_t)refl(jj, ny) * pitch + wrapx(ii, nx)];
-            return jj < 0 ? -v : v;
+        auto wr_dy = [&](int dj, int di) {  // negated below, zero above the top
+            if (j + dj >= ny) return 0.f;
+            const float v = at(5, dj, di);
+            return j + dj < 0 ? -v : v;
         };
-        const float wr0 = xrho[o];
-        rb += a.k.cD * (wr_lap(j, i + 1) + wr_lap(j, i - 1) + wr_lap(j + 1, i) + wr_lap(j - 1, i) - 4.f * wr0);
-        rb -= a.k.ax * (wr_lap(j, i - 1) - wr_lap(j, i + 1)) + a.k.ay * (wr_dy(j - 1, i) - wr_dy(j + 1, i));
+        const float wr0 = at(5, 0, 0);
+        rb += a.k.cD * (wr_lap(0, 1) + wr_lap(0, -1) + wr_lap(1, 0) + wr_lap(-1, 0) - 4.f * wr0);
+        rb -= a.k.ax * (wr_lap(0, -1) - wr_lap(0, 1)) + a.k.ay * (wr_dy(-1, 0) - wr_dy(1, 0));
         float of = scale * fb, oc_ = scale * cb, orr = scale * rb;
         if (b1phi) {
             of += b1phi[o];
@@ -316,7 +348,8 @@ vjp_b_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
 
 int adj_blocks(int nx, int ny)
 {
-    long long b = ((long long)nx * ny + ADJ_THREADS - 1) / ADJ_THREADS;  // one thread per cell up to the cap
+    // one block per ATX x ATY tile (one thread per cell) up to the cap
+    long long b = (long long)((nx + ATX - 1) / ATX) * ((ny + ATY - 1) / ATY);
     return (int)(b < 1 ? 1 : (b > ADJ_MAX_BLOCKS ? ADJ_MAX_BLOCKS : b));
 }
 
@@ -372,7 +405,7 @@ bool adj_layout(int nx, int ny, int pitch, long nsteps, int K, AdjLayout& L)
     L.partials = off;
     off = a256(off + 3 * size_t(pf::adj_blocks(nx, ny)) * sizeof(double));
     L.acc = off;
-    off = a256(off + 3 * sizeof(double) + sizeof(unsigned));  // accumulators, then the block ticket
+    off = a256(off + 3 * sizeof(double) + sizeof(unsigned));  // the three parameter gradients (+ padding)
     L.total = off;
     return true;
 }
@@ -441,7 +474,6 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
     const int nb = adj_blocks(nx, ny);
     double* partials = reinterpret_cast<double*>(w + L.partials);
     double* acc = reinterpret_cast<double*>(w + L.acc);
-    unsigned* ticket = reinterpret_cast<unsigned*>(acc + 3);
     const long nseg = (nsteps + K - 1) / K;
 
     cudaError_t e = cudaSuccess;
@@ -475,6 +507,7 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
         }
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * sizeof(double) + sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(partials, 0, 3 * size_t(nb) * sizeof(double), s);
     // ---- backward
     std::vector<float*> lamA = planes(L.lam), lamB = planes(L.lam + 3 * L.plane), lamS = planes(L.lam + 6 * L.plane);
     std::vector<float*> us = planes(L.ustar);
@@ -509,8 +542,7 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
         if (e == cudaSuccess)
             e = cudaLaunchKernelEx(&cfg, vjp_a_kernel, ac, (const float*)v[0], (const float*)v[1],
                                    (const float*)v[2], (const float*)x[0], (const float*)x[1], (const float*)x[2],
-                                   (const float*)muc_v, (const float*)M_v, muc_b, M_b, muf_b, s_b, partials, ticket,
-                                   pscale, acc);
+                                   (const float*)muc_v, (const float*)M_v, muc_b, M_b, muf_b, s_b, partials, pscale);
         if (e == cudaSuccess)
             e = cudaLaunchKernelEx(&cfg, vjp_b_kernel, ac, (const float*)v[0], (const float*)v[1],
                                    (const float*)v[2], (const float*)x[2], (const float*)muc_b, (const float*)M_b,
@@ -580,6 +612,18 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
         float* g[3] = {g_phi0, g_c0, g_rho0};
         const float* src[3] = {lam[0], lam[1], lam[2]};
         copy3(g, src);
+    }
+    if (e == cudaSuccess) {
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(1);
+        cfg.blockDim = dim3(ADJ_THREADS);
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, adj_sum_kernel, (const double*)partials, nb, acc);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(g_params, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
