@@ -74,45 +74,6 @@ __device__ __forceinline__ float rho_at(const float* r, int j, int i, int nx, in
     return r[(size_t)refl(j, ny) * pitch + wrapx(i, nx)];
 }
 
-struct Chem {
-    float muc, M;
-};
-
-// mu_c and M_c at (j, i) (ghost rows by reflection, as in the forward)
-__device__ __forceinline__ Chem chem_at(const AdjConst& a, const float* phi, const float* c, int j, int i, int nx,
-                                        int ny, int pitch)
-{
-    const float f = mirror_at(phi, j, i, nx, ny, pitch), cc = mirror_at(c, j, i, nx, ny, pitch);
-    const float sc = mirror_at(c, j, i + 1, nx, ny, pitch) + mirror_at(c, j, i - 1, nx, ny, pitch) +
-                     mirror_at(c, j + 1, i, nx, ny, pitch) + mirror_at(c, j - 1, i, nx, ny, pitch);
-    const float P = 0.25f * (2.f - f) * (1.f + f) * (1.f + f);
-    const float dg = 2.f * cc * (1.f - cc) * (1.f - 2.f * cc);
-    Chem r;
-    r.muc = P * a.k.Wc * dg - a.k.kc * (sc - 4.f * cc);
-    const float h = cc * cc * (3.f - 2.f * cc);
-    r.M = P * (h * a.MAb + (1.f - h) * a.MBb);
-    if (a.MAs != 0.f || a.MBs != 0.f) r.M += expf(-f * f * a.isig2) * (h * a.MAs + (1.f - h) * a.MBs);
-    return r;
-}
-
-// mu_c and M_c of every cell of the state (pass 0 of J_R(v)^T x).
-__global__ void __launch_bounds__(ADJ_THREADS)
-chem_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __restrict__ vc,
-            float* __restrict__ muc, float* __restrict__ Mc)
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
-    const long long n = (long long)nx * ny;
-    for (long long idx = (long long)blockIdx.x * ADJ_THREADS + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * ADJ_THREADS) {
-        const int j = (int)(idx / nx), i = (int)(idx - (long long)j * nx);
-        const Chem C = chem_at(a, vphi, vc, j, i, nx, ny, pitch);
-        const size_t o = (size_t)j * pitch + i;
-        muc[o] = C.muc;
-        Mc[o] = C.M;
-    }
-}
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -144,33 +105,69 @@ __device__ __forceinline__ void stage_tile(float (*S)[AH][AW], const float* cons
     }
 }
 
-// Pass A. x: cotangent (phi, c, rho); v: state. Writes mu_c_bar, M_bar, mu_phi_bar, s_bar
-// and per-block partials {V, m_scale, kappa_c} (FP64, fixed order).
+// Pass A. x: cotangent (phi, c, rho); v: state. Writes mu_c_bar, M_bar, mu_phi_bar, s_bar and
+// adds the block's parameter partials {V, m_scale, kappa_c} (FP64, fixed order) to its slot.
+// The chemical potential and mobility of the state are computed here for the tile and its
+// one-cell halo, from phi and c staged with a two-cell halo: a halo cell beyond the top or
+// bottom takes the value of the cell it mirrors (computed there, with the same stencil and
+// summation order), and one beyond the left or right edge is the periodic translate.
+constexpr int BW2 = ATX + 4, BH2 = ATY + 4;
 __global__ void __launch_bounds__(ADJ_THREADS)
 vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __restrict__ vc,
              const float* __restrict__ vrho, const float* __restrict__ xphi, const float* __restrict__ xc,
-             const float* __restrict__ xrho, const float* __restrict__ muc, const float* __restrict__ Mc,
-             float* __restrict__ muc_bar, float* __restrict__ M_bar, float* __restrict__ muf_bar,
-             float* __restrict__ s_bar, double* __restrict__ partials, double pscale)
+             const float* __restrict__ xrho, float* __restrict__ muc_bar, float* __restrict__ M_bar,
+             float* __restrict__ muf_bar, float* __restrict__ s_bar, double* __restrict__ partials, double pscale)
 {
-    __shared__ float S[7][AH][AW];  // muc, Mc, xc, xphi, vc, vphi, vrho
+    __shared__ float S2[2][BH2][BW2];  // vphi, vc with a two-cell halo
+    __shared__ float S[5][AH][AW];     // muc, Mc (computed), xc, xphi, vrho
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int nx = a.k.nx, ny = a.k.ny, pitch = a.k.pitch;
     const int ntx = (nx + ATX - 1) / ATX, ntiles = ntx * ((ny + ATY - 1) / ATY);
     const int tx = threadIdx.x % ATX, ty = threadIdx.x / ATX;
-    const float* const fl[7] = {muc, Mc, xc, xphi, vc, vphi, vrho};
+    const float* const fl[3] = {xc, xphi, vrho};
     double accV = 0.0, accM = 0.0, accK = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int j0 = (tile / ntx) * ATY, i0 = (tile % ntx) * ATX;
         __syncthreads();  // the previous tile's readers are done
-        stage_tile<7>(S, fl, j0, i0, nx, ny, pitch);
+        for (int e = threadIdx.x; e < BH2 * BW2; e += ADJ_THREADS) {
+            const int r = e / BW2, cc = e - r * BW2;
+            const int gj = j0 - 2 + r, gi = i0 - 2 + cc;
+            const bool ok = gj >= -2 && gj <= ny + 1 && gi >= -2 && gi <= nx + 1;
+            const size_t src = ok ? (size_t)refl(gj, ny) * pitch + wrapx(gi, nx) : 0;
+            S2[0][r][cc] = ok ? vphi[src] : 0.f;
+            S2[1][r][cc] = ok ? vc[src] : 0.f;
+        }
+        {
+            float (*Sx)[AH][AW] = &S[2];
+            stage_tile<3>(Sx, fl, j0, i0, nx, ny, pitch);
+        }
+        __syncthreads();
+        // mu_c and M_c on the tile and its halo (rows j0-1 .. j0+ATY, columns i0-1 .. i0+ATX)
+        for (int e = threadIdx.x; e < AH * AW; e += ADJ_THREADS) {
+            const int r = e / AW, cc = e - r * AW;
+            const int gj = j0 - 1 + r, gi = i0 - 1 + cc;
+            float muc = 0.f, Mc = 0.f;
+            if (gj >= -1 && gj <= ny && gi >= -1 && gi <= nx) {
+                const int y2 = refl(gj, ny) - (j0 - 2), x2 = cc + 1;  // stencil centre in S2
+                const float f = S2[0][y2][x2], c0 = S2[1][y2][x2];
+                const float sc = S2[1][y2][x2 + 1] + S2[1][y2][x2 - 1] + S2[1][y2 + 1][x2] + S2[1][y2 - 1][x2];
+                const float P = 0.25f * (2.f - f) * (1.f + f) * (1.f + f);
+                const float dg = 2.f * c0 * (1.f - c0) * (1.f - 2.f * c0);
+                muc = P * a.k.Wc * dg - a.k.kc * (sc - 4.f * c0);
+                const float h = c0 * c0 * (3.f - 2.f * c0);
+                Mc = P * (h * a.MAb + (1.f - h) * a.MBb);
+                if (a.MAs != 0.f || a.MBs != 0.f) Mc += expf(-f * f * a.isig2) * (h * a.MAs + (1.f - h) * a.MBs);
+            }
+            S[0][r][cc] = muc;
+            S[1][r][cc] = Mc;
+        }
         __syncthreads();
         const int j = j0 + ty, i = i0 + tx;
         if (j >= ny || i >= nx) continue;
         const size_t o = (size_t)j * pitch + i;
         const int y = ty + 1, x = tx + 1;  // staged position of (j, i)
-        // staged value of field q at the neighbour (j + dj, i + di)
         auto at = [&](int q, int dj, int di) { return S[q][y + dj][x + di]; };
+        auto at2 = [&](int q, int dj, int di) { return S2[q][y + 1 + dj][x + 1 + di]; };
         const int dj4[4] = {0, 0, 1, -1}, di4[4] = {1, -1, 0, 0};
         const float m0 = at(0, 0, 0), M0 = at(1, 0, 0);
         const float wc = at(2, 0, 0);
@@ -201,14 +198,14 @@ vjp_a_kernel(const AdjConst a, const float* __restrict__ vphi, const float* __re
         muf_bar[o] = mfb;
         s_bar[o] = sb;
         // parameter partials
-        const float c0 = at(4, 0, 0), r0 = at(6, 0, 0);
-        const float Lc = at(4, 0, 1) + at(4, 0, -1) + at(4, 1, 0) + at(4, -1, 0) - 4.f * c0;
+        const float c0 = at2(1, 0, 0), r0 = at(4, 0, 0);
+        const float Lc = at2(1, 0, 1) + at2(1, 0, -1) + at2(1, 1, 0) + at2(1, -1, 0) - 4.f * c0;
         accK -= (double)mub * (double)(Lc * a.idx2);  // d mu_c / d kappa_c = -L(c)
         accM += (double)wc * (double)Rc;
-        const float dfx = at(5, 0, 1) - at(5, 0, -1);
-        const float dfy = at(5, 1, 0) - at(5, -1, 0);
+        const float dfx = at2(0, 0, 1) - at2(0, 0, -1);
+        const float dfy = at2(0, 1, 0) - at2(0, -1, 0);
         // rho above the top is the reservoir value
-        auto rh = [&](int dj, int di) { return j + dj >= ny ? a.k.rho_top : at(6, dj, di); };
+        auto rh = [&](int dj, int di) { return j + dj >= ny ? a.k.rho_top : at(4, dj, di); };
         const float drx = rh(0, 1) - rh(0, -1);
         const float dry = rh(1, 0) - rh(-1, 0);
         accV += (double)(sb * r0 * (a.cx * dfx + a.cy * dfy)) - (double)(wr * (a.cx * drx + a.cy * dry));
@@ -380,7 +377,7 @@ struct AdjLayout {
     size_t seg;     // K x 3 planes
     size_t lam;     // 3 cotangents x 3 planes
     size_t ustar;   // 3 planes
-    size_t scratch; // 6 planes (mu_c, M, and the four pass-A fields)
+    size_t scratch; // 4 planes (the pass-A fields mu_c_bar, M_bar, mu_phi_bar, s_bar)
     size_t partials, acc, total;
 };
 
@@ -401,7 +398,7 @@ bool adj_layout(int nx, int ny, int pitch, long nsteps, int K, AdjLayout& L)
     L.ustar = off;
     off += 3 * L.plane;
     L.scratch = off;
-    off += 6 * L.plane;
+    off += 4 * L.plane;
     L.partials = off;
     off = a256(off + 3 * size_t(pf::adj_blocks(nx, ny)) * sizeof(double));
     L.acc = off;
@@ -512,8 +509,7 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
     std::vector<float*> lamA = planes(L.lam), lamB = planes(L.lam + 3 * L.plane), lamS = planes(L.lam + 6 * L.plane);
     std::vector<float*> us = planes(L.ustar);
     float* sc = reinterpret_cast<float*>(w + L.scratch);
-    float *muc_b = sc, *M_b = sc + pl, *muf_b = sc + 2 * pl, *s_b = sc + 3 * pl, *muc_v = sc + 4 * pl,
-          *M_v = sc + 5 * pl;
+    float *muc_b = sc, *M_b = sc + pl, *muf_b = sc + 2 * pl, *s_b = sc + 3 * pl;
     // cotangent buffers start at zero (also a zero rho cotangent when none is given)
     if (e == cudaSuccess) e = cudaMemsetAsync(lamA[0], 0, 9 * L.plane, s);
     {
@@ -538,11 +534,9 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         const float* nil = nullptr;
-        e = cudaLaunchKernelEx(&cfg, chem_kernel, ac, (const float*)v[0], (const float*)v[1], muc_v, M_v);
-        if (e == cudaSuccess)
-            e = cudaLaunchKernelEx(&cfg, vjp_a_kernel, ac, (const float*)v[0], (const float*)v[1],
-                                   (const float*)v[2], (const float*)x[0], (const float*)x[1], (const float*)x[2],
-                                   (const float*)muc_v, (const float*)M_v, muc_b, M_b, muf_b, s_b, partials, pscale);
+        e = cudaLaunchKernelEx(&cfg, vjp_a_kernel, ac, (const float*)v[0], (const float*)v[1], (const float*)v[2],
+                               (const float*)x[0], (const float*)x[1], (const float*)x[2], muc_b, M_b, muf_b, s_b,
+                               partials, pscale);
         if (e == cudaSuccess)
             e = cudaLaunchKernelEx(&cfg, vjp_b_kernel, ac, (const float*)v[0], (const float*)v[1],
                                    (const float*)v[2], (const float*)x[2], (const float*)muc_b, (const float*)M_b,
