@@ -229,7 +229,7 @@ class AdjointRun:
         self.stream = torch.cuda.current_stream()
         self.cells = spec.nx * spec.ny
         self.w = [torch.zeros_like(t) for t in self.fields]
-        self.launches = self.nsteps * (1 + 1 + 1 + 6)  # forward + recompute + Euler + two (A, sum, B) passes
+        self.launches = self.nsteps * (1 + 1 + 1 + 4) + 1  # forward, recompute, Euler, two (A, B) passes; final sum
         self.config = {"nx": spec.nx, "ny": spec.ny, "timesteps_per_run": self.nsteps, "checkpoint_every": self.K,
                        "loss": "sum (phi_N - phi_T)^2 + (c_N - c_T)^2, target deposited 1.3x faster",
                        "launch": "pf_adjoint: forward with checkpoints, segment recompute, adjoint passes"}
