@@ -504,6 +504,9 @@ def oracle_problem(W):
         return m["spec"], O.with_dt(I.default_params(v_mag=m["v_mag"])), "run 0 of the ensemble"
     if W.get("kind") == "adjoint":
         return W["spec"], O.with_dt(I.default_params(**W["params"])), "forward steps only, on the"
+    if W.get("kind") == "hybrid":
+        m = I.hybrid_members(W["n_runs"], W["side"], seed=W["seed"])[0]
+        return m["spec"], O.with_dt(I.default_params(v_mag=m["v_mag"])), "plain DNS of run 0 of the hybrid batch, the"
     return W["spec"], O.with_dt(I.default_params(**W["params"])), "the"
 
 
