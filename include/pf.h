@@ -284,6 +284,15 @@ int pf_conv3x3_bf16(const void* in, int n, int h, int w, int cin, const void* wg
 int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* wgt, int cout, void* out,
                      int out_cstride, int out_coff, int* err_dev, void* stream);
 /*
+ * pf_conv_halo: selects how pf_conv3x3_bf16 (and the U-Net's convolutions) stage a tile
+ * with cin == 64, cout <= 64 and w a multiple of 128.  on = 1 (the default): one copy of
+ * the tile's three input rows of 130 pixels serves all nine taps, and the weights of
+ * all taps stay in shared memory.  on = 0: one copy per tap, like every other shape.
+ * Both give the same sums.  A process-wide setting (not thread-safe against
+ * concurrent launches); returns the previous setting.
+ */
+int pf_conv_halo(int on);
+/*
  * The time-conditioned U-Net surrogate and its jump ("U-Net with temporal
  * conditioning", Methods; the hybrid solver of Results alternates DNS stretches
  * with such jumps).  For each of `batch` runs it maps (phi, c) at time t to a

@@ -216,6 +216,8 @@ int pf_tconv2x2_bf16(const void* in, int n, int h, int w, int cin, const void* w
                        stream);
 }
 
+int pf_conv_halo(int on) { return pf::set_conv_halo(on); }
+
 size_t pf_unet_workspace_size(int batch, int nx, int ny)
 {
     if (!shape_ok(batch, ny, nx)) return 0;

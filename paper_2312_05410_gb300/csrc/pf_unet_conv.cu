@@ -36,7 +36,8 @@ namespace pf {
 namespace {
 
 constexpr int TM = 128;          // pixels per tile (MMA M)
-constexpr int NTHREADS = 192;    // 6 warps
+constexpr int EPI_WARPS = 4;     // epilogue warps: EPI_WARPS / 4 per TMEM lane quarter, each on a share of the N columns
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // producer warp, MMA warp, epilogue warps
 constexpr int MAX_ST = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -86,6 +87,16 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, int kc)
     return d;
 }
 
+// Halo mode (CONV3, 64 input channels, rows of at least 128 pixels): a tile's three input rows of
+// 130 pixels (the 128 of the tile and one on each side) arrive in ONE box; tap (dy, dx) is the
+// 128-row window starting at row (dy + 1) * 130 + dx + 1 of it.  TMA and the MMA both apply the
+// 128-byte swizzle as a function of the absolute shared-memory address (the copy starts on a
+// 1024-byte boundary), so a window that starts at any 128-byte row takes a plain descriptor with
+// base offset 0.  The weights of all taps stay resident in shared memory for the whole launch.
+constexpr int HALO_W = TM + 2;
+constexpr uint32_t HALO_BOX = 3u * HALO_W * 128u;               // bytes copied per tile
+constexpr uint32_t HALO_STAGE = (HALO_BOX + 1023u) & ~1023u;   // stage stride (swizzle-atom aligned)
+
 // Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
 __device__ __forceinline__ uint32_t umma_idesc(int n)
 {
@@ -94,29 +105,64 @@ __device__ __forceinline__ uint32_t umma_idesc(int n)
 
 
 // Round to nearest even, as the oracle's format definition does.
-__device__ __forceinline__ uint16_t f_to_bf16(float f)
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
-    uint32_t u = __float_as_uint(f);
-    if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40);  // NaN stays NaN
-    u += 0x7fffu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
+    uint32_t d;  // one conversion instruction: hi to bits 16-31, lo to bits 0-15, both rounded to nearest even
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
+
+// Quotient and remainder of a non-negative int by a positive divisor through a reciprocal
+// computed once: the FP64 product is within 2^-52 relative of x / d, so the truncated
+// quotient is off by at most one, and one correction step makes it exact.
+struct FastDiv {
+    int d;
+    double inv;
+};
+
+__device__ __forceinline__ FastDiv make_fastdiv(int d) { return {d, 1.0 / (double)d}; }
+
+__device__ __forceinline__ int fast_divmod(int x, const FastDiv& f, int& r)
+{
+    int q = __double2int_rz((double)x * f.inv);
+    r = x - q * f.d;
+    if (r < 0) {
+        --q;
+        r += f.d;
+    } else if (r >= f.d) {
+        ++q;
+        r -= f.d;
+    }
+    return q;
+}
+
+static_assert(EPI_WARPS == 4 || EPI_WARPS == 8, "one or two epilogue warps per TMEM lane quarter");
+static_assert(GN_MAX_GROUPS % (EPI_WARPS / 4) == 0, "the column shares split the normalisation groups");
 
 // Tile geometry: tile T of a launch -> image, first pixel (x0, y0) and first GEMM column n0.
 struct TileGeo {
     int img, t, x0, y0, n0;
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const ConvArgs& a, int T, int mtiles, int NT)
+struct TileDivs {
+    FastDiv mtiles, tpi, tiles_per_row;
+    int BW, BR;
+};
+
+__device__ __forceinline__ TileDivs tile_divs(const ConvArgs& a, int mtiles)
+{
+    const int BW = a.w < TM ? a.w : TM;
+    return {make_fastdiv(mtiles), make_fastdiv((a.h * a.w) / TM), make_fastdiv(a.w / BW), BW, TM / BW};
+}
+
+__device__ __forceinline__ TileGeo tile_geo(const TileDivs& v, int T, int NT)
 {
     TileGeo g;
-    const int mt = T % mtiles, nt = T / mtiles;
-    const int tpi = (a.h * a.w) / TM;
-    const int BW = a.w < TM ? a.w : TM, BR = TM / BW, tiles_per_row = a.w / BW;
-    g.img = mt / tpi;
-    g.t = mt % tpi;
-    g.y0 = (g.t / tiles_per_row) * BR;
-    g.x0 = (g.t % tiles_per_row) * BW;
+    int mt, r;
+    const int nt = fast_divmod(T, v.mtiles, mt);
+    g.img = fast_divmod(mt, v.tpi, g.t);
+    g.y0 = fast_divmod(g.t, v.tiles_per_row, r) * v.BR;
+    g.x0 = r * v.BW;
     g.n0 = nt * NT;
     return g;
 }
@@ -124,24 +170,29 @@ __device__ __forceinline__ TileGeo tile_geo(const ConvArgs& a, int T, int mtiles
 // Persistent kernel: CTA b takes tiles b, b + gridDim.x, ...  The TMA / MMA stream runs through
 // all of them without draining; two accumulators in tensor memory let the epilogue of one tile
 // overlap the MMAs of the next.
-template <int MODE, int NT>
+template <int MODE, int NT, bool HALO = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
 umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ConvArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smraw[];
-    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[MAX_ST], empty_bar[MAX_ST], accf_bar[2], acce_bar[2];
+    uint8_t* const sm0 = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    // halo mode: resident weights (9 taps x NT rows x 128 bytes) first, then the stage ring
+    constexpr uint32_t BRES = HALO ? 9u * NT * 128u : 0u;
+    uint8_t* const sm = sm0 + BRES;
+    __shared__ __align__(8) uint64_t full_bar[MAX_ST], empty_bar[MAX_ST], accf_bar[2], acce_bar[2], bres_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KC = a.kc, ST = a.stages;
-    const uint32_t a_bytes = TM * KC * 2, b_bytes = NT * KC * 2, stage_bytes = a_bytes + b_bytes;
-    const int kblocks = a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = ntaps * kblocks;
+    const uint32_t a_bytes = HALO ? HALO_STAGE : TM * KC * 2, b_bytes = HALO ? 0u : NT * KC * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const int kblocks = a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = HALO ? 1 : ntaps * kblocks;
     const int ncols = MODE == CONV3 ? a.cout : 4 * a.cout;
     const int mtiles = a.n * ((a.h * a.w) / TM), tiles = mtiles * (ncols / NT);
     const int tpi = (a.h * a.w) / TM;
     const int BW = a.w < TM ? a.w : TM;
+    const TileDivs divs = tile_divs(a, mtiles);
 
     if (tid == 0) {
         abort_flag = 0;
@@ -151,8 +202,10 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar[b])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce_bar[b])), "n"(EPI_WARPS)
+                         : "memory");
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bres_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {  // the whole warp allocates both accumulators (2 NT columns)
@@ -170,12 +223,34 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         if (lane == 0) {  // ---- producer: a continuous stream of (tile, tap, channel block) stages
             int it = 0;  // stage counter over all tiles
             bool ok = true;
+            if constexpr (HALO) {  // all 9 taps' weights, once: one 64 x NT x 9 box
+                const uint32_t bb = smem_u32(&bres_bar);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(BRES) : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sm0)),
+                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(0), "r"(0), "r"(0), "r"(bb)
+                    : "memory");
+            }
             for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x) {
-                const TileGeo g = tile_geo(a, T, mtiles, NT);
+                const TileGeo g = tile_geo(divs, T, NT);
                 for (int k = 0; k < iters && ok; ++k, ++it) {
                     const int s = it % ST;
                     ok = mbar_wait(smem_u32(&empty_bar[s]), ((uint32_t)(it / ST) & 1u) ^ 1u, a.wait_cap, &abort_flag);
                     if (!ok) break;
+                    if constexpr (HALO) {  // rows y0-1 .. y0+1, columns x0-1 .. x0+128 of all 64 channels
+                        const uint32_t fb = smem_u32(&full_bar[s]);
+                        const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                     "r"(HALO_BOX) : "memory");
+                        asm volatile(
+                            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                            " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
+                            "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(0), "r"(g.x0 - 1), "r"(g.y0 - 1), "r"(g.img),
+                            "r"(fb)
+                            : "memory");
+                        continue;
+                    }
                     const int tap = k / kblocks, kb = k % kblocks;
                     const int dy = MODE == CONV3 ? tap / 3 - 1 : 0, dx = MODE == CONV3 ? tap % 3 - 1 : 0;
                     const uint32_t fb = smem_u32(&full_bar[s]);
@@ -201,6 +276,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 // let the copies already issued land before the CTA leaves (bounded)
                 for (int j = (it > ST ? it - ST : 0); j < it; ++j)
                     mbar_wait(smem_u32(&full_bar[j % ST]), (uint32_t)(j / ST) & 1u, a.wait_cap, &abort_flag);
+                if constexpr (HALO) mbar_wait(smem_u32(&bres_bar), 0u, a.wait_cap, &abort_flag);
             }
         }
     } else if (warp == 1) {
@@ -208,6 +284,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const uint32_t idesc = umma_idesc(NT);
             int it = 0, local = 0;
             bool ok = true;
+            if constexpr (HALO) ok = mbar_wait(smem_u32(&bres_bar), 0u, a.wait_cap, &abort_flag);
             for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x, ++local) {
                 const int b = local & 1;
                 // the epilogue must have drained this accumulator (its previous use)
@@ -221,14 +298,30 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
-                    for (int kk = 0; kk < KC / 16; ++kk) {
-                        const uint64_t ad = umma_desc(sa + kk * 32, KC), bd = umma_desc(sb + kk * 32, KC);
-                        const uint32_t acc = (k | kk) ? 1u : 0u;
-                        asm volatile(
-                            "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
-                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                            : "memory");
+                    if constexpr (HALO) {
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const uint32_t at = sa + (uint32_t)(((tap / 3) * HALO_W + tap % 3) * 128);
+                            const uint32_t bt = smem_u32(sm0) + (uint32_t)(tap * NT * 128);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = umma_desc(at + kk * 32, 64), bd = umma_desc(bt + kk * 32, 64);
+                                const uint32_t acc = (tap | kk) ? 1u : 0u;
+                                asm volatile(
+                                    "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+                                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                    : "memory");
+                            }
+                        }
+                    } else {
+                        for (int kk = 0; kk < KC / 16; ++kk) {
+                            const uint64_t ad = umma_desc(sa + kk * 32, KC), bd = umma_desc(sb + kk * 32, KC);
+                            const uint32_t acc = (k | kk) ? 1u : 0u;
+                            asm volatile(
+                                "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                : "memory");
+                        }
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                                  ::"r"(smem_u32(&empty_bar[s])) : "memory");
@@ -242,9 +335,13 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 atomicOr(a.err, UNET_ERR_TIMEOUT);
             }
         }
-    } else {  // ---- epilogue, warps 2..5: TMEM lanes 32 (warp % 4) ... + 31
+    } else {  // ---- epilogue, warps 2 .. 2 + EPI_WARPS - 1: TMEM lanes 32 (warp % 4) ... + 31
+        constexpr int SHARES = EPI_WARPS / 4;      // warps per lane quarter
+        constexpr int NS = NT / SHARES;            // columns per warp
         const int q = warp & 3;
-        const int row = q * 32 + lane;  // pixel within the tile
+        const int half = (warp - 2) / 4;           // columns [half NS, (half + 1) NS)
+        const int row = q * 32 + lane;             // pixel within the tile
+        constexpr int HG = GN_MAX_GROUPS / SHARES; // groups per warp (CONV3: one N tile holds all Cout)
         int local = 0;
         for (int T = blockIdx.x; T < tiles; T += gridDim.x, ++local) {
             const int b = local & 1;
@@ -254,13 +351,14 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const TileGeo g = tile_geo(a, T, mtiles, NT);
+            const TileGeo g = tile_geo(divs, T, NT);
             const int py = g.y0 + row / BW, px = g.x0 + row % BW;
-            float s1[GN_MAX_GROUPS], s2[GN_MAX_GROUPS];
+            float s1[HG], s2[HG];
 #pragma unroll
-            for (int gg = 0; gg < GN_MAX_GROUPS; ++gg) s1[gg] = s2[gg] = 0.f;
+            for (int gg = 0; gg < HG; ++gg) s1[gg] = s2[gg] = 0.f;
 #pragma unroll
-            for (int c0 = 0; c0 < NT; c0 += 16) {
+            for (int k0 = 0; k0 < NS; k0 += 16) {
+                const int c0 = half * NS + k0;
                 uint32_t r[16];
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT + c0);
                 asm volatile(
@@ -275,16 +373,16 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float v0 = __uint_as_float(r[2 * j]), v1 = __uint_as_float(r[2 * j + 1]);
-                    pk[j] = (uint32_t)f_to_bf16(v0) | ((uint32_t)f_to_bf16(v1) << 16);
+                    pk[j] = pack_bf16x2(v0, v1);
                 }
                 uint16_t* dst;
                 if (MODE == CONV3) {
-                    constexpr int cg = NT / GN_MAX_GROUPS;  // channels per group (one N tile holds all Cout)
+                    constexpr int cg = NT / GN_MAX_GROUPS;  // channels per group; NS = HG groups
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {  // the group index is a compile-time constant
+                    for (int j = 0; j < 16; ++j) {  // the group index within the share is a compile-time constant
                         const float v = __uint_as_float(r[j]);
-                        s1[(c0 + j) / cg] += v;
-                        s2[(c0 + j) / cg] = fmaf(v, v, s2[(c0 + j) / cg]);
+                        s1[(k0 + j) / cg] += v;
+                        s2[(k0 + j) / cg] = fmaf(v, v, s2[(k0 + j) / cg]);
                     }
                     dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + c0;
                 } else {  // TCONV: column n0 + c0 + j = sub-pixel s * cout + channel
@@ -302,20 +400,19 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             if (lane == 0)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
             if (MODE == CONV3 && a.partials) {
-                // per warp: partials[((img * groups + g) * tpi + t) * 4 + q] = (sum, sum of squares)
+                // per warp: partials[((img * groups + g) * tpi + t) * 4 + q] = (sum, sum of squares) of its
+                // HG groups; lane (32 / 2 HG) i holds value i: statistic i / HG of group half HG + i % HG
+                float v[2 * HG];
 #pragma unroll
-                for (int gg = 0; gg < GN_MAX_GROUPS; ++gg) {
-                    float v1 = s1[gg], v2 = s2[gg];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-                        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-                    }
-                    if (lane == 0) {
-                        float* pp = a.partials + ((((size_t)g.img * a.groups + gg) * tpi + g.t) * 4 + q) * 2;
-                        pp[0] = v1;
-                        pp[1] = v2;
-                    }
+                for (int gg = 0; gg < HG; ++gg) {
+                    v[gg] = s1[gg];
+                    v[HG + gg] = s2[gg];
+                }
+                const float tot = warp_sum_scatter<2 * HG>(v, lane);
+                constexpr int LS = 32 / (2 * HG);
+                if (lane % LS == 0) {
+                    const int i = lane / LS, gg = half * HG + i % HG, st = i / HG;
+                    a.partials[((((size_t)g.img * a.groups + gg) * tpi + g.t) * 4 + q) * 2 + st] = tot;
                 }
             }
         }
@@ -335,6 +432,8 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 namespace {
 
 int conv_kc(int cin) { return cin % 64 == 0 ? 64 : 32; }
+
+bool g_halo_enabled = true;
 
 int sm_count()
 {
@@ -369,12 +468,32 @@ bool encode(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, 
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
+// Halo mode applies to 3x3 convolutions of 64 channels into at most 64, on rows that are whole tiles.
+bool halo_applies(int mode, const ConvArgs& a)
+{
+    return g_halo_enabled && mode == CONV3 && a.cin == 64 && a.nt <= 64 && a.w % TM == 0;
+}
 
-size_t umma_conv_smem_bytes(int mode, int cin, int cout)
+int halo_stages(int nt)
+{
+    const int st = (int)((200u * 1024u - 9u * nt * 128u) / HALO_STAGE);
+    return st < 2 ? 2 : (st > MAX_ST ? MAX_ST : st);
+}
+
+size_t conv_smem_bytes(int mode, int cin, int cout, bool halo)
 {
     const int kc = conv_kc(cin), nt = conv_nt(mode, cout);
+    if (halo) return 9u * nt * 128u + (size_t)halo_stages(nt) * HALO_STAGE + 1024;
     return (size_t)conv_stages(kc, nt) * (size_t)(TM * kc * 2 + nt * kc * 2) + 1024;
+}
+
+}  // namespace
+
+int set_conv_halo(int on)
+{
+    const int prev = g_halo_enabled ? 1 : 0;
+    g_halo_enabled = on != 0;
+    return prev;
 }
 
 cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, ConvArgs a, cudaStream_t s)
@@ -390,7 +509,8 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     a.kc = conv_kc(a.cin);
     a.nt = conv_nt(mode, a.cout);
     if (ncols % a.nt) return cudaErrorInvalidValue;
-    a.stages = conv_stages(a.kc, a.nt);
+    const bool halo = halo_applies(mode, a);
+    a.stages = halo ? halo_stages(a.nt) : conv_stages(a.kc, a.nt);
     a.tmem_cols = 32;
     while (a.tmem_cols < 2 * a.nt) a.tmem_cols <<= 1;  // two accumulators
     const int BW = a.w < TM ? a.w : TM, BR = TM / BW;
@@ -398,22 +518,21 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     CUtensorMap mA, mB;
     const cuuint64_t dA[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)a.n};
     const cuuint64_t sA[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.w * a.cin * 2, (cuuint64_t)a.h * a.w * a.cin * 2};
-    const cuuint32_t bA[4] = {(cuuint32_t)a.kc, (cuuint32_t)BW, (cuuint32_t)BR, 1u};
+    // halo mode: three rows of 130 pixels per box, and all nine taps of the weights in one box
+    const cuuint32_t bA[4] = {(cuuint32_t)a.kc, (cuuint32_t)(halo ? HALO_W : BW), (cuuint32_t)(halo ? 3 : BR), 1u};
     const int taps = mode == CONV3 ? 9 : 1;
     const cuuint64_t dB[3] = {(cuuint64_t)a.cin, (cuuint64_t)ncols, (cuuint64_t)taps};
     const cuuint64_t sB[2] = {(cuuint64_t)a.cin * 2, (cuuint64_t)ncols * a.cin * 2};
-    const cuuint32_t bB[3] = {(cuuint32_t)a.kc, (cuuint32_t)a.nt, 1u};
+    const cuuint32_t bB[3] = {(cuuint32_t)a.kc, (cuuint32_t)a.nt, halo ? 9u : 1u};
     if (!encode(&mA, in, 4, dA, sA, bA, a.kc) || !encode(&mB, wgt, 3, dB, sB, bB, a.kc))
         return cudaErrorInvalidValue;
 
-    const size_t smem = umma_conv_smem_bytes(mode, a.cin, a.cout);
+    const size_t smem = conv_smem_bytes(mode, a.cin, a.cout, halo);
     cudaLaunchConfig_t cfg = {};
     const long long tiles = (long long)a.n * a.h * a.w / TM * (ncols / a.nt);
     int per_sm = (int)((227 * 1024) / (smem + 2048));  // CTAs that fit next to each other on an SM
     per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
     if (per_sm * a.tmem_cols > 512) per_sm = 512 / a.tmem_cols;
-    const long long slots = (long long)sm_count() * per_sm;
-    cfg.gridDim = dim3((unsigned)(tiles < slots ? tiles : slots));
     cfg.blockDim = dim3(NTHREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -425,8 +544,20 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        // every CTA of the persistent grid must be resident at once: cap by registers as well
+        int fit = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, NTHREADS, smem);
+        if (e != cudaSuccess) return e;
+        const int ps = fit < 1 ? 1 : (fit < per_sm ? fit : per_sm);
+        const long long slots = (long long)sm_count() * ps;
+        cfg.gridDim = dim3((unsigned)(tiles < slots ? tiles : slots));
         return cudaLaunchKernelEx(&cfg, kern, mA, mB, a);
     };
+    if (halo) {
+        if (a.nt == 32) return go(umma_conv_kernel<CONV3, 32, true>);
+        if (a.nt == 64) return go(umma_conv_kernel<CONV3, 64, true>);
+        return cudaErrorInvalidValue;
+    }
     if (mode == CONV3) {
         if (a.nt == 32) return go(umma_conv_kernel<CONV3, 32>);
         if (a.nt == 64) return go(umma_conv_kernel<CONV3, 64>);

@@ -16,6 +16,33 @@ enum ConvMode { CONV3 = 0, TCONV = 1 };
 constexpr int GN_MAX_GROUPS = 8;        // group normalisation groups of the hidden layers
 constexpr int UNET_ERR_TIMEOUT = 2;     // error-word bit: a bounded wait of a tensor-core kernel ran out
 
+#ifdef __CUDACC__
+// Sum over the warp of V values per lane (V = 2^b <= 32) by recursive halving: each exchange
+// step, with offsets 16, 8, ... down to 32 / V, sends half of the remaining values to the partner
+// lane and keeps the other half, so that lane l ends with value (l >> (5 - b)) & (V - 1) summed
+// over the lanes that agree with l in their low 5 - b bits; full exchanges at the remaining
+// offsets complete the sum over all 32 lanes.  V + 4 - b shuffles instead of 5 V.
+template <int V>
+__device__ __forceinline__ float warp_sum_scatter(float (&v)[V], int lane)
+{
+    static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+#pragma unroll
+    for (int h = V / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            const float send = up ? v[j] : v[j + h];
+            const float keep = up ? v[j + h] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    float s = v[0];
+#pragma unroll
+    for (int o = 16 / V; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+#endif
+
 // Arguments of one implicit-GEMM convolution launch (see pf_unet_conv.cu).
 struct ConvArgs {
     int n, h, w;           // images and input size
@@ -37,6 +64,7 @@ struct ConvArgs {
 // cout % 16 == 0, and (h * w) % 128 == 0 with w % 128 == 0 or 128 % w == 0.
 // Returns cudaErrorInvalidValue for shapes outside these rules.
 cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, ConvArgs a, cudaStream_t s);
-size_t umma_conv_smem_bytes(int mode, int cin, int cout);
+// Enables (1) or disables (0) the halo form of the 3x3 convolution; returns the previous setting.
+int set_conv_halo(int on);
 
 }  // namespace pf

@@ -26,12 +26,19 @@ constexpr int TPB = 128;  // one 128-pixel tile per block in the tile-shaped ker
 
 __device__ __forceinline__ float bf(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
+// FP32 -> BF16, round to nearest even: one conversion instruction each
 __device__ __forceinline__ uint16_t to_bf(float f)
 {
-    uint32_t u = __float_as_uint(f);
-    if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40);
-    u += 0x7fffu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
+    uint16_t h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return h;
+}
+
+__device__ __forceinline__ uint32_t to_bf2(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 __device__ __forceinline__ float rbf(float f) { return bf(to_bf(f)); }
@@ -72,16 +79,28 @@ __global__ void cond_kernel(const double* __restrict__ mlp, const double* __rest
     }
 }
 
+// eight BF16 values (one 16-byte load) to FP32
+__device__ __forceinline__ void unpack8(const uint4 v, float* f)
+{
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f[2 * j] = bf((uint16_t)(u[j] & 0xffffu));
+        f[2 * j + 1] = bf((uint16_t)(u[j] >> 16));
+    }
+}
+
 // First convolution: x = BF16(phi, c, rho, tau) with zero padding outside the image, 3x3, 4 -> 32.
 // One thread per output pixel, one 128-pixel tile per block (neighbours come through L1: staging
-// the halo in shared memory measured slower).  Group sums: one warp butterfly over all 16 values.
+// the halo in shared memory measured slower).  The 32 outputs are 16 pairs updated by packed FP32x2
+// FMAs (each half runs the scalar chain unchanged); group sums: one scatter-halving per warp.
 __global__ void __launch_bounds__(TPB)
 in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
                const float* const* __restrict__ rho, int pitch, int h, int w, float tau,
                const float* __restrict__ wgt /* [36][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
                float* __restrict__ partials)
 {
-    __shared__ float ws[36 * 32];
+    __shared__ __align__(16) float ws[36 * 32];
     __shared__ float red[4][16];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = threadIdx.x; i < 36 * 32; i += TPB) ws[i] = wgt[i];
@@ -93,52 +112,41 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     const float* C = c[img];
     const float* Rh = rho[img];
     const float tb = rbf(tau);
-    float acc[32];
+    const float2* ws2 = reinterpret_cast<const float2*>(ws);
+    float2 acc[16];
 #pragma unroll
-    for (int o = 0; o < 32; ++o) acc[o] = 0.f;
+    for (int o = 0; o < 16; ++o) acc[o] = make_float2(0.f, 0.f);
     for (int ky = 0; ky < 3; ++ky)
         for (int kx = 0; kx < 3; ++kx) {
             const int yy = y + ky - 1, xx = x + kx - 1;
             const bool in = yy >= 0 && yy < h && xx >= 0 && xx < w;
             const size_t o = in ? (size_t)yy * pitch + xx : 0;
-            const float v0 = in ? rbf(F[o]) : 0.f;
-            const float v1 = in ? rbf(C[o]) : 0.f;
-            const float v2 = in ? rbf(Rh[o]) : 0.f;
-            const float v3 = in ? tb : 0.f;
-            const float* wk = ws + (ky * 3 + kx) * 4 * 32;
+            const float v0 = in ? rbf(F[o]) : 0.f, v1 = in ? rbf(C[o]) : 0.f;
+            const float v2 = in ? rbf(Rh[o]) : 0.f, v3 = in ? tb : 0.f;
+            const float2 b0 = make_float2(v0, v0), b1 = make_float2(v1, v1);
+            const float2 b2 = make_float2(v2, v2), b3 = make_float2(v3, v3);
+            const float2* wk = ws2 + (ky * 3 + kx) * 4 * 16;
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-                acc[q] = fmaf(v0, wk[q], fmaf(v1, wk[32 + q], fmaf(v2, wk[64 + q], fmaf(v3, wk[96 + q], acc[q]))));
+            for (int q = 0; q < 16; ++q)
+                acc[q] = __ffma2_rn(b0, wk[q], __ffma2_rn(b1, wk[16 + q],
+                                   __ffma2_rn(b2, wk[32 + q], __ffma2_rn(b3, wk[48 + q], acc[q]))));
         }
     uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)img * h * w + p) * 32);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            pk[j] = (uint32_t)to_bf(acc[8 * q + 2 * j]) | ((uint32_t)to_bf(acc[8 * q + 2 * j + 1]) << 16);
-        dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
-    // group sums (8 groups of 4 channels): per thread, then one butterfly per value, then 4 warps
+    for (int q = 0; q < 4; ++q)
+        dst[q] = make_uint4(to_bf2(acc[4 * q].x, acc[4 * q].y), to_bf2(acc[4 * q + 1].x, acc[4 * q + 1].y),
+                            to_bf2(acc[4 * q + 2].x, acc[4 * q + 2].y), to_bf2(acc[4 * q + 3].x, acc[4 * q + 3].y));
+    // group sums (8 groups of 4 channels): value 2 g + k is the sum (k = 0) or the sum of squares (k = 1)
     float sv[16];
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
-        float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            s1 += acc[4 * g + j];
-            s2 = fmaf(acc[4 * g + j], acc[4 * g + j], s2);
-        }
-        sv[2 * g] = s1;
-        sv[2 * g + 1] = s2;
+        const float2 a0 = acc[2 * g], a1 = acc[2 * g + 1];
+        sv[2 * g] = (a0.x + a0.y) + (a1.x + a1.y);
+        sv[2 * g + 1] = fmaf(a1.y, a1.y, fmaf(a1.x, a1.x, fmaf(a0.y, a0.y, a0.x * a0.x)));
     }
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sv[k] += __shfl_xor_sync(0xffffffffu, sv[k], o);
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int k = 0; k < 16; ++k) red[threadIdx.x >> 5][k] = sv[k];
+    const int lane = threadIdx.x & 31;
+    const float tot = warp_sum_scatter<16>(sv, lane);  // even lane l: value l / 2
+    if (!(lane & 1)) red[threadIdx.x >> 5][lane >> 1] = tot;
     __syncthreads();
     if (threadIdx.x < 16) {
         const int g = threadIdx.x >> 1, which = threadIdx.x & 1;
@@ -149,43 +157,83 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
 
 // Output: the last convolution (3x3, 32 -> 3) of BF16 NHWC [n][h][w][32], as per-channel affine
 // increments added to the FP32 fields in place: u_k += gamma_k conv_k + beta_k for u = (phi, c, rho).
+// One 128-pixel tile per block, 32 pixels per warp.  Lane l reads the 8 channels 8 (l % 4) .. + 7 of
+// pixels l / 4 + 8 g (g = 0..3), so that each 16-byte load of the warp covers 512 contiguous bytes
+// (8 whole pixels); the four partial sums of a pixel meet in two shuffle-halving steps, after which
+// lane l holds the three outputs of pixel l / 4 + 8 (l % 4).
 __global__ void __launch_bounds__(TPB)
 out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __restrict__ wgt /* [9][32][3] */,
                 const float* __restrict__ gamma, const float* __restrict__ beta, float* const* __restrict__ phi,
                 float* const* __restrict__ c, float* const* __restrict__ rho, int pitch)
 {
-    __shared__ float ws[9 * 32 * 3];
+    __shared__ __align__(16) float ws[9 * 32 * 3];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = threadIdx.x; i < 9 * 32 * 3; i += TPB) ws[i] = wgt[i];
     __syncthreads();
     const int tpi = h * w / TPB;
     const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
-    const int p = t * TPB + threadIdx.x, y = p / w, x = p % w;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    const int lane = threadIdx.x & 31, cq = lane & 3, ps = lane >> 2;
+    const int p0 = t * TPB + (threadIdx.x >> 5) * 32;
+    const uint16_t* src = in + (size_t)img * h * w * 32 + cq * 8;
+    int py[4], px[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int p = p0 + 8 * g + ps;
+        py[g] = p / w;
+        px[g] = p - py[g] * w;
+    }
+    float acc[12];  // [g][output]
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.f;
     for (int ky = 0; ky < 3; ++ky)
         for (int kx = 0; kx < 3; ++kx) {
-            const int yy = y + ky - 1, xx = x + kx - 1;
-            if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
-            const uint4* src = reinterpret_cast<const uint4*>(in + ((size_t)img * h * w + (size_t)yy * w + xx) * 32);
-            const float* wk = ws + (ky * 3 + kx) * 96;
+            float wv[24];  // this lane's 8 channels x 3 outputs of the tap
+            const float4* wq = reinterpret_cast<const float4*>(ws + ((ky * 3 + kx) * 32 + cq * 8) * 3);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 v = src[q];
-                const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+            for (int k = 0; k < 6; ++k) {
+                const float4 v = wq[k];
+                wv[4 * k] = v.x;
+                wv[4 * k + 1] = v.y;
+                wv[4 * k + 2] = v.z;
+                wv[4 * k + 3] = v.w;
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int ci = 8 * q + 2 * j;
-                    const float lo = bf((uint16_t)(u[j] & 0xffffu)), hi = bf((uint16_t)(u[j] >> 16));
-                    a0 = fmaf(lo, wk[3 * ci], fmaf(hi, wk[3 * ci + 3], a0));
-                    a1 = fmaf(lo, wk[3 * ci + 1], fmaf(hi, wk[3 * ci + 4], a1));
-                    a2 = fmaf(lo, wk[3 * ci + 2], fmaf(hi, wk[3 * ci + 5], a2));
+            for (int g = 0; g < 4; ++g) {
+                const int yy = py[g] + ky - 1, xx = px[g] + kx - 1;
+                if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                float f[8];
+                unpack8(*reinterpret_cast<const uint4*>(src + ((size_t)yy * w + xx) * 32), f);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    acc[3 * g] = fmaf(f[j], wv[3 * j], acc[3 * g]);
+                    acc[3 * g + 1] = fmaf(f[j], wv[3 * j + 1], acc[3 * g + 1]);
+                    acc[3 * g + 2] = fmaf(f[j], wv[3 * j + 2], acc[3 * g + 2]);
                 }
             }
         }
+    // halving over the 4 lanes of a pixel: offset 2 splits g in {0,1} | {2,3}, offset 1 splits g even | odd
+    {
+        const bool up = lane & 2;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float send = up ? acc[k] : acc[k + 6], keep = up ? acc[k + 6] : acc[k];
+            acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        }
+    }
+    {
+        const bool up = lane & 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float send = up ? acc[k] : acc[k + 3], keep = up ? acc[k + 3] : acc[k];
+            acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+    }
+    const int g = cq;  // lane bits 1, 0 chose the upper halves: this lane now holds pixel ps + 8 cq
+    const int p = p0 + 8 * g + ps, y = p / w, x = p - y * w;
     const size_t o = (size_t)y * pitch + x;
-    phi[img][o] = phi[img][o] + fmaf(gamma[0], a0, beta[0]);
-    c[img][o] = c[img][o] + fmaf(gamma[1], a1, beta[1]);
-    rho[img][o] = rho[img][o] + fmaf(gamma[2], a2, beta[2]);
+    phi[img][o] = phi[img][o] + fmaf(gamma[0], acc[0], beta[0]);
+    c[img][o] = c[img][o] + fmaf(gamma[1], acc[1], beta[1]);
+    rho[img][o] = rho[img][o] + fmaf(gamma[2], acc[2], beta[2]);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
@@ -253,43 +301,29 @@ __device__ __forceinline__ Aff8 aff8(const float* affine, int img, int C, int c0
     return q;
 }
 
-__device__ __forceinline__ void unpack8(const uint4 v, float* f)
-{
-    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        f[2 * j] = bf((uint16_t)(u[j] & 0xffffu));
-        f[2 * j + 1] = bf((uint16_t)(u[j] >> 16));
-    }
-}
-
 __device__ __forceinline__ uint4 pack8(const float* f)
 {
     uint32_t u[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) u[j] = (uint32_t)to_bf(f[2 * j]) | ((uint32_t)to_bf(f[2 * j + 1]) << 16);
+    for (int j = 0; j < 4; ++j) u[j] = to_bf2(f[2 * j], f[2 * j + 1]);
     return make_uint4(u[0], u[1], u[2], u[3]);
 }
 
 // Encoder level: z = BF16(GELU(GN(x))); zc = BF16(z * s) into the skip slice (channels [0, C) of a
 // buffer with cat_stride channels); pool (if not NULL) = 2x2 max of z.  One thread per 8 channels
-// of a 2x2 pixel block (pool) or of one pixel (no pool).
-__global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h, int w, int C,
+// of a 2x2 pixel block (pool) or of one pixel (no pool).  Blocks in y walk the rows of (pooled)
+// pixels, blocks in x the (pixel, 8-channel block) items of a row; C / 8 = 1 << lc8.
+__global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h, int w, int C, int lc8,
                                     const float* __restrict__ affine, const float* __restrict__ scale,
                                     uint16_t* __restrict__ cat, int cat_stride, uint16_t* __restrict__ pool)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int c8 = C / 8;
     const int ph = pool ? h / 2 : h, pw = pool ? w / 2 : w;
-    const long long total = (long long)n * ph * pw * c8;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int cb = (int)(i % c8);
-        long long r = i / c8;
-        const int px = (int)(r % pw);
-        r /= pw;
-        const int py = (int)(r % ph);
-        const int img = (int)(r / ph);
+    const int rows = n * ph, per_row = pw << lc8;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per_row; i += gridDim.x * blockDim.x) {
+        const int img = row / ph, py = row - img * ph;
+        const int cb = i & ((1 << lc8) - 1), px = i >> lc8;
         const Aff8 q = aff8(affine, img, C, cb * 8);
         float s[8];
 #pragma unroll
@@ -316,18 +350,17 @@ __global__ void gn_apply_enc_kernel(const uint16_t* __restrict__ x, int n, int h
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Decoder level: y = BF16(GELU(GN(x))), NHWC with C channels.
-__global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, long long pixels, int C, int hw,
+// Decoder level: y = BF16(GELU(GN(x))), NHWC with C channels; rows and items as in the encoder.
+__global__ void gn_apply_dec_kernel(const uint16_t* __restrict__ x, int n, int h, int w, int C, int lc8,
                                     const float* __restrict__ affine, uint16_t* __restrict__ y)
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int c8 = C / 8;
-    const long long total = pixels * c8;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int cb = (int)(i % c8);
-        const long long pix = i / c8;
-        const int img = (int)(pix / hw);
+    const int rows = n * h, per_row = w << lc8;
+    for (int row = blockIdx.y; row < rows; row += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per_row; i += gridDim.x * blockDim.x) {
+        const int img = row / h;
+        const int cb = i & ((1 << lc8) - 1);
+        const size_t pix = (size_t)row * w + (i >> lc8);
         const Aff8 q = aff8(affine, img, C, cb * 8);
         float v[8];
         unpack8(reinterpret_cast<const uint4*>(x + pix * C)[cb], v);
@@ -373,10 +406,20 @@ cudaLaunchConfig_t cfg_of(dim3 grid, int threads, cudaStream_t s, cudaLaunchAttr
     return cfg;
 }
 
-unsigned grid_for(long long items, int threads)
+// Row-wise grid of the normalisation kernels: x covers one row's items, y the rows (at most 65535).
+dim3 row_grid(int rows, long long per_row, int threads)
 {
-    long long b = (items + threads - 1) / threads;
-    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+    const long long bx = (per_row + threads - 1) / threads;
+    return dim3((unsigned)(bx < 1 ? 1 : (bx > 1024 ? 1024 : bx)), (unsigned)(rows < 65535 ? rows : 65535));
+}
+
+// log2 of C / 8, or -1 unless C / 8 is a power of two
+int log2_c8(int C)
+{
+    if (C < 8 || C % 8) return -1;
+    int l = 0;
+    while ((8 << l) < C) ++l;
+    return (8 << l) == C ? l : -1;
 }
 
 }  // namespace
@@ -416,19 +459,22 @@ cudaError_t launch_gn_stats(const float* partials, int n, int groups, int entrie
 cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, const float* affine, const float* scale,
                           uint16_t* cat, int cat_stride, uint16_t* pool, cudaStream_t s)
 {
-    const long long items = (long long)n * (pool ? (h / 2) * (w / 2) : h * w) * (C / 8);
+    const int lc8 = log2_c8(C);
+    if (lc8 < 0) return cudaErrorInvalidValue;
+    const int rows = n * (pool ? h / 2 : h), per_row = (pool ? w / 2 : w) << lc8;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(items, 256)), 256, s, attr);
-    return cudaLaunchKernelEx(&cfg, gn_apply_enc_kernel, x, n, h, w, C, affine, scale, cat, cat_stride, pool);
+    cudaLaunchConfig_t cfg = cfg_of(row_grid(rows, per_row, 256), 256, s, attr);
+    return cudaLaunchKernelEx(&cfg, gn_apply_enc_kernel, x, n, h, w, C, lc8, affine, scale, cat, cat_stride, pool);
 }
 
 cudaError_t launch_gn_dec(const uint16_t* x, int n, int h, int w, int C, const float* affine, uint16_t* y,
                           cudaStream_t s)
 {
-    const long long pixels = (long long)n * h * w;
+    const int lc8 = log2_c8(C);
+    if (lc8 < 0) return cudaErrorInvalidValue;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cfg_of(dim3(grid_for(pixels * (C / 8), 256)), 256, s, attr);
-    return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, pixels, C, h * w, affine, y);
+    cudaLaunchConfig_t cfg = cfg_of(row_grid(n * h, (long long)w << lc8, 256), 256, s, attr);
+    return cudaLaunchKernelEx(&cfg, gn_apply_dec_kernel, x, n, h, w, C, lc8, affine, y);
 }
 
 cudaError_t launch_check(const float* const* phi, const float* const* c, const float* const* rho, int n, int h, int w,

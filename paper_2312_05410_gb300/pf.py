@@ -96,6 +96,7 @@ def _load():
     L.pf_tconv2x2_bf16.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int,
                                    vp, vp]
     L.pf_tconv2x2_bf16.restype = C.c_int
+    L.pf_conv_halo.argtypes, L.pf_conv_halo.restype = [C.c_int], C.c_int
     L.pf_unet_last_error.argtypes, L.pf_unet_last_error.restype = [], C.c_char_p
     L.pf_unet_workspace_size.argtypes, L.pf_unet_workspace_size.restype = [C.c_int, C.c_int, C.c_int], sz
     L.pf_unet_init.argtypes = [C.POINTER(C.POINTER(C.c_float)), C.c_int, C.c_int, C.c_int, C.c_int, vp, sz, vp,
@@ -511,6 +512,11 @@ def conv3x3_bf16(x, w_dev, groups: int, out=None, out_coff: int = 0, partials=No
     _ucheck(lib.pf_conv3x3_bf16(x.data_ptr(), n, h, wd, cin, w_dev.data_ptr(), cout, out.data_ptr(), out.shape[3],
                                 out_coff, groups, partials.data_ptr(), err.data_ptr(), s))
     return out, partials
+
+
+def conv_halo(on: bool) -> bool:
+    """Select the halo staging of 64-channel 3x3 convolutions (default on); returns the previous setting."""
+    return bool(lib.pf_conv_halo(1 if on else 0))
 
 
 def tconv2x2_bf16(x, w_dev, out=None, out_coff: int = 0, err=None, stream=None):
