@@ -144,22 +144,30 @@ struct TileGeo {
     int img, t, x0, y0, n0;
 };
 
+// Tiles are numbered column-tile-major (T = nt mtiles + mt), or, with `inter` (the halo form, whose
+// CTAs keep the weights of one column tile), column-tile-minor (T = mt nsplit + nt): there a grid
+// that is a multiple of nsplit gives every CTA a single column tile.
 struct TileDivs {
-    FastDiv mtiles, tpi, tiles_per_row;
+    FastDiv mtiles, nsplit, tpi, tiles_per_row;
     int BW, BR;
+    bool inter;
 };
 
-__device__ __forceinline__ TileDivs tile_divs(const ConvArgs& a, int mtiles)
+__device__ __forceinline__ TileDivs tile_divs(const ConvArgs& a, int mtiles, int nsplit, bool inter)
 {
     const int BW = a.w < TM ? a.w : TM;
-    return {make_fastdiv(mtiles), make_fastdiv((a.h * a.w) / TM), make_fastdiv(a.w / BW), BW, TM / BW};
+    return {make_fastdiv(mtiles), make_fastdiv(nsplit), make_fastdiv((a.h * a.w) / TM), make_fastdiv(a.w / BW),
+            BW, TM / BW, inter};
 }
 
 __device__ __forceinline__ TileGeo tile_geo(const TileDivs& v, int T, int NT)
 {
     TileGeo g;
-    int mt, r;
-    const int nt = fast_divmod(T, v.mtiles, mt);
+    int mt, nt, r;
+    if (v.inter)
+        mt = fast_divmod(T, v.nsplit, nt);
+    else
+        nt = fast_divmod(T, v.mtiles, mt);
     g.img = fast_divmod(mt, v.tpi, g.t);
     g.y0 = fast_divmod(g.t, v.tiles_per_row, r) * v.BR;
     g.x0 = r * v.BW;
@@ -170,15 +178,32 @@ __device__ __forceinline__ TileGeo tile_geo(const TileDivs& v, int T, int NT)
 // Persistent kernel: CTA b takes tiles b, b + gridDim.x, ...  The TMA / MMA stream runs through
 // all of them without draining; two accumulators in tensor memory let the epilogue of one tile
 // overlap the MMAs of the next.
-template <int MODE, int NT, bool HALO = false>
+// Position in a stage ring: stage, phase parity and stages passed, advanced without divisions.
+struct Ring {
+    int s = 0, it = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int st)
+    {
+        ++it;
+        if (++s == st) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
+// GPT: normalisation groups per column tile (all 8 unless the halo form splits Cout over two tiles);
+// HKB: channel blocks of 64 per tile in the halo form (its input channels / 64).
+template <int MODE, int NT, bool HALO = false, int GPT = GN_MAX_GROUPS, int HKB = 1>
 __global__ void __launch_bounds__(NTHREADS, 1)
 umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ConvArgs a)
 {
+    static_assert(GPT >= EPI_WARPS / 4 && GPT % (EPI_WARPS / 4) == 0 && NT % GPT == 0, "group split");
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t* const sm0 = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    // halo mode: resident weights (9 taps x NT rows x 128 bytes) first, then the stage ring
-    constexpr uint32_t BRES = HALO ? 9u * NT * 128u : 0u;
-    uint8_t* const sm = sm0 + BRES;
+    // halo mode: resident weights ([channel block][9 taps][NT rows][128 bytes]) first, then the stage ring
+    constexpr uint32_t bres = HALO ? (uint32_t)HKB * 9u * NT * 128u : 0u;
+    uint8_t* const sm = sm0 + bres;
     __shared__ __align__(8) uint64_t full_bar[MAX_ST], empty_bar[MAX_ST], accf_bar[2], acce_bar[2], bres_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
@@ -187,12 +212,13 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const int KC = a.kc, ST = a.stages;
     const uint32_t a_bytes = HALO ? HALO_STAGE : TM * KC * 2, b_bytes = HALO ? 0u : NT * KC * 2;
     const uint32_t stage_bytes = a_bytes + b_bytes;
-    const int kblocks = a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = HALO ? 1 : ntaps * kblocks;
+    const int kblocks = HALO ? HKB : a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = HALO ? HKB : ntaps * kblocks;
     const int ncols = MODE == CONV3 ? a.cout : 4 * a.cout;
-    const int mtiles = a.n * ((a.h * a.w) / TM), tiles = mtiles * (ncols / NT);
+    const int nsplit = ncols / NT;
+    const int mtiles = a.n * ((a.h * a.w) / TM), tiles = mtiles * nsplit;
     const int tpi = (a.h * a.w) / TM;
     const int BW = a.w < TM ? a.w : TM;
-    const TileDivs divs = tile_divs(a, mtiles);
+    const TileDivs divs = tile_divs(a, mtiles, nsplit, HALO);
 
     if (tid == 0) {
         abort_flag = 0;
@@ -221,59 +247,60 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 
     if (warp == 0) {
         if (lane == 0) {  // ---- producer: a continuous stream of (tile, tap, channel block) stages
-            int it = 0;  // stage counter over all tiles
+            Ring r;
             bool ok = true;
-            if constexpr (HALO) {  // all 9 taps' weights, once: one 64 x NT x 9 box
+            if constexpr (HALO) {  // this CTA's column tile, all 9 taps, once: one 64 x NT x 9 box per channel block
                 const uint32_t bb = smem_u32(&bres_bar);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(BRES) : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sm0)),
-                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(0), "r"(0), "r"(0), "r"(bb)
-                    : "memory");
+                const int ntc = (int)blockIdx.x % nsplit;  // the grid is a multiple of nsplit
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(bres) : "memory");
+#pragma unroll
+                for (int kb = 0; kb < HKB; ++kb)
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sm0 + (size_t)kb * 9 * NT * 128)),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * 64), "r"(ntc * NT), "r"(0), "r"(bb)
+                        : "memory");
             }
             for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x) {
                 const TileGeo g = tile_geo(divs, T, NT);
-                for (int k = 0; k < iters && ok; ++k, ++it) {
-                    const int s = it % ST;
-                    ok = mbar_wait(smem_u32(&empty_bar[s]), ((uint32_t)(it / ST) & 1u) ^ 1u, a.wait_cap, &abort_flag);
-                    if (!ok) break;
-                    if constexpr (HALO) {  // rows y0-1 .. y0+1, columns x0-1 .. x0+128 of all 64 channels
-                        const uint32_t fb = smem_u32(&full_bar[s]);
-                        const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes);
-                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                     "r"(HALO_BOX) : "memory");
-                        asm volatile(
-                            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                            " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
-                            "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(0), "r"(g.x0 - 1), "r"(g.y0 - 1), "r"(g.img),
-                            "r"(fb)
-                            : "memory");
-                        continue;
+                for (int tap = 0; tap < (HALO ? 1 : ntaps) && ok; ++tap)
+                    for (int kb = 0; kb < kblocks && ok; ++kb, r.next(ST)) {
+                        ok = mbar_wait(smem_u32(&empty_bar[r.s]), r.ph ^ 1u, a.wait_cap, &abort_flag);
+                        if (!ok) break;
+                        const uint32_t fb = smem_u32(&full_bar[r.s]);
+                        const uint32_t sa = smem_u32(sm + (size_t)r.s * stage_bytes), sb = sa + a_bytes;
+                        if constexpr (HALO) {  // rows y0-1 .. y0+1, columns x0-1 .. x0+128 of channel block kb
+                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                         "r"(HALO_BOX) : "memory");
+                            asm volatile(
+                                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
+                                "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * 64), "r"(g.x0 - 1), "r"(g.y0 - 1),
+                                "r"(g.img), "r"(fb)
+                                : "memory");
+                        } else {
+                            const int dy = MODE == CONV3 ? tap / 3 - 1 : 0, dx = MODE == CONV3 ? tap % 3 - 1 : 0;
+                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                         "r"(stage_bytes) : "memory");
+                            asm volatile(
+                                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
+                                "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * KC), "r"(g.x0 + dx), "r"(g.y0 + dy),
+                                "r"(g.img), "r"(fb)
+                                : "memory");
+                            asm volatile(
+                                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sb),
+                                "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * KC), "r"(g.n0), "r"(tap), "r"(fb)
+                                : "memory");
+                        }
                     }
-                    const int tap = k / kblocks, kb = k % kblocks;
-                    const int dy = MODE == CONV3 ? tap / 3 - 1 : 0, dx = MODE == CONV3 ? tap % 3 - 1 : 0;
-                    const uint32_t fb = smem_u32(&full_bar[s]);
-                    const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_bytes)
-                                 : "memory");
-                    asm volatile(
-                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
-                        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * KC), "r"(g.x0 + dx), "r"(g.y0 + dy),
-                        "r"(g.img), "r"(fb)
-                        : "memory");
-                    asm volatile(
-                        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sb),
-                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * KC), "r"(g.n0), "r"(tap), "r"(fb)
-                        : "memory");
-                }
             }
             if (!ok) {
                 abort_flag = 1;
                 atomicOr(a.err, UNET_ERR_TIMEOUT);
                 // let the copies already issued land before the CTA leaves (bounded)
+                const int it = r.it;
                 for (int j = (it > ST ? it - ST : 0); j < it; ++j)
                     mbar_wait(smem_u32(&full_bar[j % ST]), (uint32_t)(j / ST) & 1u, a.wait_cap, &abort_flag);
                 if constexpr (HALO) mbar_wait(smem_u32(&bres_bar), 0u, a.wait_cap, &abort_flag);
@@ -282,7 +309,8 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     } else if (warp == 1) {
         if (lane == 0) {  // ---- MMA issuer
             const uint32_t idesc = umma_idesc(NT);
-            int it = 0, local = 0;
+            Ring r;
+            int local = 0;
             bool ok = true;
             if constexpr (HALO) ok = mbar_wait(smem_u32(&bres_bar), 0u, a.wait_cap, &abort_flag);
             for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x, ++local) {
@@ -292,29 +320,50 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(b * NT);
-                for (int k = 0; k < iters && ok; ++k, ++it) {
-                    const int s = it % ST;
-                    ok = mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(it / ST) & 1u, a.wait_cap, &abort_flag);
+                if constexpr (HALO) {
+                    // all channel blocks of the tile first, then tap by tap: the per-tap form's order of sums
+                    int ss[HKB];
+#pragma unroll
+                    for (int kb = 0; kb < HKB; ++kb, r.next(ST)) {
+                        ss[kb] = r.s;
+                        if (ok) ok = mbar_wait(smem_u32(&full_bar[r.s]), r.ph, a.wait_cap, &abort_flag);
+                    }
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = smem_u32(sm + (size_t)s * stage_bytes), sb = sa + a_bytes;
-                    if constexpr (HALO) {
-                        for (int tap = 0; tap < 9; ++tap) {
-                            const uint32_t at = sa + (uint32_t)(((tap / 3) * HALO_W + tap % 3) * 128);
-                            const uint32_t bt = smem_u32(sm0) + (uint32_t)(tap * NT * 128);
+                    // descriptors of the stage and weight bases; a window or K step adds its byte offset / 16
+                    // to the start-address field (every address stays below 2^18)
+                    uint64_t adesc[HKB];
+#pragma unroll
+                    for (int kb = 0; kb < HKB; ++kb) adesc[kb] = umma_desc(smem_u32(sm + (size_t)ss[kb] * stage_bytes), 64);
+                    const uint64_t bdesc = umma_desc(smem_u32(sm0), 64);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                        for (int kb = 0; kb < HKB; ++kb)
+#pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = umma_desc(at + kk * 32, 64), bd = umma_desc(bt + kk * 32, 64);
-                                const uint32_t acc = (tap | kk) ? 1u : 0u;
+                                const uint64_t ad = adesc[kb] + (uint64_t)((((tap / 3) * HALO_W + tap % 3) * 128 + kk * 32) >> 4);
+                                const uint64_t bd = bdesc + (uint64_t)(((kb * 9 + tap) * NT * 128 + kk * 32) >> 4);
+                                const uint32_t acc = (tap | kb | kk) ? 1u : 0u;
                                 asm volatile(
                                     "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
                                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                                     : "memory");
                             }
-                        }
-                    } else {
+#pragma unroll
+                    for (int kb = 0; kb < HKB; ++kb)
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     ::"r"(smem_u32(&empty_bar[ss[kb]])) : "memory");
+                } else {
+                    for (int k = 0; k < iters && ok; ++k, r.next(ST)) {
+                        ok = mbar_wait(smem_u32(&full_bar[r.s]), r.ph, a.wait_cap, &abort_flag);
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t sa = smem_u32(sm + (size_t)r.s * stage_bytes), sb = sa + a_bytes;
+                        const uint64_t ad0 = umma_desc(sa, KC), bd0 = umma_desc(sb, KC);
                         for (int kk = 0; kk < KC / 16; ++kk) {
-                            const uint64_t ad = umma_desc(sa + kk * 32, KC), bd = umma_desc(sb + kk * 32, KC);
+                            const uint64_t ad = ad0 + (uint64_t)(2 * kk), bd = bd0 + (uint64_t)(2 * kk);  // + 32 B
                             const uint32_t acc = (k | kk) ? 1u : 0u;
                             asm volatile(
                                 "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
@@ -322,9 +371,9 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                                 : "memory");
                         }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     ::"r"(smem_u32(&empty_bar[r.s])) : "memory");
                     }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 ::"r"(smem_u32(&empty_bar[s])) : "memory");
                 }
                 if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -341,7 +390,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         const int q = warp & 3;
         const int half = (warp - 2) / 4;           // columns [half NS, (half + 1) NS)
         const int row = q * 32 + lane;             // pixel within the tile
-        constexpr int HG = GN_MAX_GROUPS / SHARES; // groups per warp (CONV3: one N tile holds all Cout)
+        constexpr int HG = GPT / SHARES;           // groups per warp (CONV3: GPT groups per column tile)
         int local = 0;
         for (int T = blockIdx.x; T < tiles; T += gridDim.x, ++local) {
             const int b = local & 1;
@@ -377,14 +426,14 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 }
                 uint16_t* dst;
                 if (MODE == CONV3) {
-                    constexpr int cg = NT / GN_MAX_GROUPS;  // channels per group; NS = HG groups
+                    constexpr int cg = NT / GPT;  // channels per group; NS = HG groups
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {  // the group index within the share is a compile-time constant
                         const float v = __uint_as_float(r[j]);
                         s1[(k0 + j) / cg] += v;
                         s2[(k0 + j) / cg] = fmaf(v, v, s2[(k0 + j) / cg]);
                     }
-                    dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + c0;
+                    dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + g.n0 + c0;
                 } else {  // TCONV: column n0 + c0 + j = sub-pixel s * cout + channel
                     const int col = g.n0 + c0, s = col / a.cout, co = col % a.cout;
                     const int oy = 2 * py + (s >> 1), ox = 2 * px + (s & 1);
@@ -411,7 +460,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 const float tot = warp_sum_scatter<2 * HG>(v, lane);
                 constexpr int LS = 32 / (2 * HG);
                 if (lane % LS == 0) {
-                    const int i = lane / LS, gg = half * HG + i % HG, st = i / HG;
+                    const int i = lane / LS, gg = (g.n0 / NT) * GPT + half * HG + i % HG, st = i / HG;
                     a.partials[((((size_t)g.img * a.groups + gg) * tpi + g.t) * 4 + q) * 2 + st] = tot;
                 }
             }
@@ -468,23 +517,28 @@ bool encode(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, 
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Halo mode applies to 3x3 convolutions of 64 channels into at most 64, on rows that are whole tiles.
-bool halo_applies(int mode, const ConvArgs& a)
+// Column tile of the halo form, or 0 where it does not apply: 3x3 convolutions of 64 or 128 channels
+// into at most 64, on rows that are whole 128-pixel tiles.  The weights of a column tile must fit
+// next to three stages: 64 -> N keeps all N columns, 128 -> N keeps 32 (two column tiles for N = 64).
+int halo_nt(int mode, const ConvArgs& a)
 {
-    return g_halo_enabled && mode == CONV3 && a.cin == 64 && a.nt <= 64 && a.w % TM == 0;
+    if (!g_halo_enabled || mode != CONV3 || a.w % TM || a.cout > 64) return 0;
+    return a.cin == 64 ? a.cout : (a.cin == 128 ? 32 : 0);
 }
 
-int halo_stages(int nt)
+constexpr size_t HALO_SMEM = 225 * 1024;  // weights + stage ring (plus 1 KB of alignment slack)
+
+int halo_stages(int kblocks, int nt)
 {
-    const int st = (int)((200u * 1024u - 9u * nt * 128u) / HALO_STAGE);
-    return st < 2 ? 2 : (st > MAX_ST ? MAX_ST : st);
+    const int st = (int)((HALO_SMEM - (size_t)kblocks * 9 * nt * 128) / HALO_STAGE);
+    return st > MAX_ST ? MAX_ST : st;
 }
 
-size_t conv_smem_bytes(int mode, int cin, int cout, bool halo)
+size_t conv_smem_bytes(int mode, int cin, int nt, bool halo, int stages)
 {
-    const int kc = conv_kc(cin), nt = conv_nt(mode, cout);
-    if (halo) return 9u * nt * 128u + (size_t)halo_stages(nt) * HALO_STAGE + 1024;
-    return (size_t)conv_stages(kc, nt) * (size_t)(TM * kc * 2 + nt * kc * 2) + 1024;
+    if (halo) return (size_t)(cin / 64) * 9 * nt * 128 + (size_t)stages * HALO_STAGE + 1024;
+    const int kc = conv_kc(cin);
+    return (size_t)stages * (size_t)(TM * kc * 2 + nt * kc * 2) + 1024;
 }
 
 }  // namespace
@@ -507,10 +561,13 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     if (a.out_coff % 8 || a.out_cstride % 8) return cudaErrorInvalidValue;  // 16-byte vector stores
     const int ncols = mode == CONV3 ? a.cout : 4 * a.cout;
     a.kc = conv_kc(a.cin);
-    a.nt = conv_nt(mode, a.cout);
+    const int hnt = halo_nt(mode, a);
+    const bool halo = hnt > 0 && halo_stages(a.cin / 64, hnt) >= 2;
+    a.nt = halo ? hnt : conv_nt(mode, a.cout);
     if (ncols % a.nt) return cudaErrorInvalidValue;
-    const bool halo = halo_applies(mode, a);
-    a.stages = halo ? halo_stages(a.nt) : conv_stages(a.kc, a.nt);
+    const int nsplit = ncols / a.nt;
+    a.stages = halo ? halo_stages(a.cin / 64, a.nt) : conv_stages(a.kc, a.nt);
+    if (halo && a.stages < a.cin / 64) return cudaErrorInvalidValue;  // a tile's channel blocks are resident together
     a.tmem_cols = 32;
     while (a.tmem_cols < 2 * a.nt) a.tmem_cols <<= 1;  // two accumulators
     const int BW = a.w < TM ? a.w : TM, BR = TM / BW;
@@ -527,7 +584,7 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     if (!encode(&mA, in, 4, dA, sA, bA, a.kc) || !encode(&mB, wgt, 3, dB, sB, bB, a.kc))
         return cudaErrorInvalidValue;
 
-    const size_t smem = conv_smem_bytes(mode, a.cin, a.cout, halo);
+    const size_t smem = conv_smem_bytes(mode, a.cin, a.nt, halo, a.stages);
     cudaLaunchConfig_t cfg = {};
     const long long tiles = (long long)a.n * a.h * a.w / TM * (ncols / a.nt);
     int per_sm = (int)((227 * 1024) / (smem + 2048));  // CTAs that fit next to each other on an SM
@@ -544,18 +601,28 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        // every CTA of the persistent grid must be resident at once: cap by registers as well
-        int fit = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, NTHREADS, smem);
+        // two CTAs of a small-stage configuration share an SM: ask for the largest shared-memory carveout,
+        // and cap the CTAs per SM by their registers as well
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
-        const int ps = fit < 1 ? 1 : (fit < per_sm ? fit : per_sm);
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kern);
+        if (e != cudaSuccess) return e;
+        const int regs_cta = NTHREADS * ((fa.numRegs + 7) & ~7);
+        const int by_regs = regs_cta > 0 ? 65536 / regs_cta : 1;
+        const int ps = by_regs < 1 ? 1 : (by_regs < per_sm ? by_regs : per_sm);
         const long long slots = (long long)sm_count() * ps;
-        cfg.gridDim = dim3((unsigned)(tiles < slots ? tiles : slots));
+        long long grid = tiles < slots ? tiles : slots;
+        if (halo) grid = grid < nsplit ? nsplit : grid - grid % nsplit;  // each CTA keeps one column tile's weights
+        cfg.gridDim = dim3((unsigned)grid);
         return cudaLaunchKernelEx(&cfg, kern, mA, mB, a);
     };
     if (halo) {
-        if (a.nt == 32) return go(umma_conv_kernel<CONV3, 32, true>);
-        if (a.nt == 64) return go(umma_conv_kernel<CONV3, 64, true>);
+        const int kb = a.cin / 64;
+        if (a.nt == 32 && nsplit == 1 && kb == 1) return go(umma_conv_kernel<CONV3, 32, true, GN_MAX_GROUPS, 1>);
+        if (a.nt == 32 && nsplit == 1 && kb == 2) return go(umma_conv_kernel<CONV3, 32, true, GN_MAX_GROUPS, 2>);
+        if (a.nt == 32 && nsplit == 2 && kb == 2) return go(umma_conv_kernel<CONV3, 32, true, GN_MAX_GROUPS / 2, 2>);
+        if (a.nt == 64 && nsplit == 1 && kb == 1) return go(umma_conv_kernel<CONV3, 64, true, GN_MAX_GROUPS, 1>);
         return cudaErrorInvalidValue;
     }
     if (mode == CONV3) {

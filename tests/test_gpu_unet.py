@@ -50,7 +50,8 @@ def to_nchw(t):
 
 @pytest.mark.parametrize("n,h,w,cin,cout", [(2, 32, 32, 64, 128), (1, 16, 64, 32, 64), (1, 8, 256, 128, 32),
                                             (3, 8, 16, 256, 256), (1, 4, 32, 96, 64),
-                                            (2, 8, 256, 64, 32), (1, 6, 384, 64, 64), (1, 1, 128, 64, 32)])
+                                            (2, 8, 256, 64, 32), (1, 6, 384, 64, 64), (1, 1, 128, 64, 32),
+                                            (2, 8, 128, 128, 64), (1, 3, 256, 128, 32)])
 def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
     g = np.random.default_rng(n * 1000 + cin + cout)
     x = U.bf16(g.standard_normal((n, cin, h, w)))
@@ -74,13 +75,15 @@ def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
             np.testing.assert_allclose(tot[i, gi, 1], (v * v).sum(), rtol=1e-4)
 
 
-@pytest.mark.parametrize("n,h,w,cout", [(2, 16, 256, 32), (1, 5, 128, 64), (3, 2, 512, 32)])
-def test_halo_staging_gives_the_same_sums_as_per_tap_staging(pf, n, h, w, cout):
-    """64-channel tiles on 128-pixel rows take the halo path by default; the per-tap path adds the
-    same products in the same order (tap by tap, 16 channels at a time), so the two agree bit for bit."""
-    g = np.random.default_rng(h * w + cout)
-    x = nhwc_dev(U.bf16(g.standard_normal((n, 64, h, w))))
-    wd = pf.conv_weight_layout((g.standard_normal((cout, 64, 3, 3)) / 24).astype(np.float32))
+@pytest.mark.parametrize("n,h,w,cin,cout", [(2, 16, 256, 64, 32), (1, 5, 128, 64, 64), (3, 2, 512, 64, 32),
+                                            (2, 8, 128, 128, 64), (1, 4, 256, 128, 32)])
+def test_halo_staging_gives_the_same_sums_as_per_tap_staging(pf, n, h, w, cin, cout):
+    """64- and 128-channel tiles on 128-pixel rows take the halo path by default (128 -> 64 as two
+    column tiles of 32); the per-tap path adds the same products in the same order (tap by tap, then
+    channel block, 16 channels at a time), so the two agree bit for bit, group sums included."""
+    g = np.random.default_rng(h * w + cin + cout)
+    x = nhwc_dev(U.bf16(g.standard_normal((n, cin, h, w))))
+    wd = pf.conv_weight_layout((g.standard_normal((cout, cin, 3, 3)) / (3 * np.sqrt(cin))).astype(np.float32))
     assert pf.conv_halo(True) is True
     a, pa = pf.conv3x3_bf16(x, wd, 8)
     prev = pf.conv_halo(False)
