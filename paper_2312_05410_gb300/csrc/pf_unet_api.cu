@@ -124,7 +124,7 @@ UnetLayout unet_layout(int n, int h, int w)
     L.mlp = take(sizeof(double) * (3 * 128 + 2 * 128 * 128 + 128));
     L.proj = take(sizeof(double) * 480 * 128);
     L.win = take(sizeof(float) * 36 * 32);
-    L.wout = take(sizeof(float) * 9 * 32 * 3);
+    L.wout = take(2 * 9 * 16 * 32);  // output conv as one 16-column tensor-core tile: [tap][16][32] BF16, rows 3.. zero
     const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
     for (int k = 0; k < 7; ++k) L.wc[k] = take(2 * 9 * (size_t)conv_io[k][0] * conv_io[k][1]);
     const int tc_io[3][2] = {{256, 128}, {128, 64}, {64, 32}};
@@ -263,11 +263,11 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     for (int co = 0; co < 32; ++co)
         for (int ci = 0; ci < 4; ++ci)
             for (int t = 0; t < 9; ++t) win[(t * 4 + ci) * 32 + co] = host_rbf(weights[10][((co * 4 + ci) * 9) + t]);
-    // last conv [3][32][3][3] -> [tap][ci][co]
-    std::vector<float> wout(9 * 32 * 3);
+    // last conv [3][32][3][3] -> [tap][16][32] BF16 (output columns 3..15 zero)
+    std::vector<uint16_t> wout(9 * 16 * 32, 0);
     for (int co = 0; co < 3; ++co)
         for (int ci = 0; ci < 32; ++ci)
-            for (int t = 0; t < 9; ++t) wout[(t * 32 + ci) * 3 + co] = host_rbf(weights[21][((co * 32 + ci) * 9) + t]);
+            for (int t = 0; t < 9; ++t) wout[(t * 16 + co) * 32 + ci] = host_bf16(weights[21][((co * 32 + ci) * 9) + t]);
     // tensor-core convs [Cout][Cin][3][3] -> [tap][Cout][Cin] BF16: enc2..4 (11..13), dec4..1 (14..17)
     const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
     const int conv_src[7] = {11, 12, 13, 14, 15, 16, 17};
@@ -299,7 +299,7 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     if (rc == PF_OK) rc = upload(u, L.mlp, mlp.data(), mlp.size() * sizeof(double));
     if (rc == PF_OK) rc = upload(u, L.proj, proj.data(), proj.size() * sizeof(double));
     if (rc == PF_OK) rc = upload(u, L.win, win.data(), win.size() * sizeof(float));
-    if (rc == PF_OK) rc = upload(u, L.wout, wout.data(), wout.size() * sizeof(float));
+    if (rc == PF_OK) rc = upload(u, L.wout, wout.data(), wout.size() * sizeof(uint16_t));
     for (int k = 0; k < 9 && rc == PF_OK; ++k)
         for (int q = 0; q < 2 && rc == PF_OK; ++q) rc = upload(u, L.gb[k][q], weights[22 + 2 * k + q], gbc[k] * sizeof(float));
     if (rc == PF_OK) {
@@ -382,9 +382,23 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     if (rc == PF_OK)
         rc = conv_tc(u, pf::CONV3, act(A_CAT1), H, W, 64, u->at<uint16_t>(L.wc[6]), 32, act(A_PRE1), 32, 0, gam(7), bet(7));
     ck(pf::launch_gn_dec(act(A_PRE1), n, H, W, 32, stats, act(A_H1), s), "decoder 1");
-    // ---- output: conv 32 -> 3 as affine increments of the DNS fields
-    ck(pf::launch_out_conv(act(A_H1), n, H, W, u->at<float>(L.wout), gam(8), bet(8), dp, dp + n, dp + 2 * n, pitch, s),
-       "output");
+    // ---- output: conv 32 -> 3 on the tensor cores, added as affine increments to the DNS fields
+    if (rc == PF_OK) {
+        pf::ConvArgs a = {};
+        a.n = n;
+        a.h = H;
+        a.w = W;
+        a.cin = 32;
+        a.cout = 16;
+        a.groups = G;
+        a.err = u->at<int>(L.err);
+        a.wait_cap = 1 << 22;
+        a.fields = dp;
+        a.fpitch = pitch;
+        a.ogamma = gam(8);
+        a.obeta = bet(8);
+        ck(pf::launch_umma_conv(pf::OUT3, act(A_H1), u->at<uint16_t>(L.wout), a, s), "output");
+    }
     return rc;
 }
 

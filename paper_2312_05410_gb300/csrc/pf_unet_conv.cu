@@ -94,8 +94,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, int kc)
 // 1024-byte boundary), so a window that starts at any 128-byte row takes a plain descriptor with
 // base offset 0.  The weights of all taps stay resident in shared memory for the whole launch.
 constexpr int HALO_W = TM + 2;
-constexpr uint32_t HALO_BOX = 3u * HALO_W * 128u;               // bytes copied per tile
-constexpr uint32_t HALO_STAGE = (HALO_BOX + 1023u) & ~1023u;   // stage stride (swizzle-atom aligned)
+// Bytes of a tile's box with channel blocks of kc (rows of 2 kc bytes), and the stage stride
+// (1024-byte aligned, a whole number of swizzle atoms of either width).
+__host__ __device__ constexpr uint32_t halo_box(int kc) { return 3u * HALO_W * 2u * (uint32_t)kc; }
+__host__ __device__ constexpr uint32_t halo_stage(int kc) { return (halo_box(kc) + 1023u) & ~1023u; }
 
 // Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
 __device__ __forceinline__ uint32_t umma_idesc(int n)
@@ -193,8 +195,9 @@ struct Ring {
 };
 
 // GPT: normalisation groups per column tile (all 8 unless the halo form splits Cout over two tiles);
-// HKB: channel blocks of 64 per tile in the halo form (its input channels / 64).
-template <int MODE, int NT, bool HALO = false, int GPT = GN_MAX_GROUPS, int HKB = 1>
+// HKB, HKC: channel blocks per tile in the halo form, and channels per block (64: 128-byte swizzle,
+// 32: 64-byte swizzle).
+template <int MODE, int NT, bool HALO = false, int GPT = GN_MAX_GROUPS, int HKB = 1, int HKC = 64>
 __global__ void __launch_bounds__(NTHREADS, 1)
 umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ConvArgs a)
 {
@@ -202,7 +205,8 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t* const sm0 = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     // halo mode: resident weights ([channel block][9 taps][NT rows][128 bytes]) first, then the stage ring
-    constexpr uint32_t bres = HALO ? (uint32_t)HKB * 9u * NT * 128u : 0u;
+    constexpr uint32_t RB = 2u * HKC;  // halo form: bytes per pixel row of a channel block
+    constexpr uint32_t bres = HALO ? (uint32_t)HKB * 9u * NT * RB : 0u;
     uint8_t* const sm = sm0 + bres;
     __shared__ __align__(8) uint64_t full_bar[MAX_ST], empty_bar[MAX_ST], accf_bar[2], acce_bar[2], bres_bar;
     __shared__ uint32_t tmem_slot;
@@ -210,10 +214,10 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KC = a.kc, ST = a.stages;
-    const uint32_t a_bytes = HALO ? HALO_STAGE : TM * KC * 2, b_bytes = HALO ? 0u : NT * KC * 2;
+    const uint32_t a_bytes = HALO ? halo_stage(HKC) : TM * KC * 2, b_bytes = HALO ? 0u : NT * KC * 2;
     const uint32_t stage_bytes = a_bytes + b_bytes;
-    const int kblocks = HALO ? HKB : a.cin / KC, ntaps = MODE == CONV3 ? 9 : 1, iters = HALO ? HKB : ntaps * kblocks;
-    const int ncols = MODE == CONV3 ? a.cout : 4 * a.cout;
+    const int kblocks = HALO ? HKB : a.cin / KC, ntaps = MODE == TCONV ? 1 : 9, iters = HALO ? HKB : ntaps * kblocks;
+    const int ncols = MODE == TCONV ? 4 * a.cout : a.cout;
     const int nsplit = ncols / NT;
     const int mtiles = a.n * ((a.h * a.w) / TM), tiles = mtiles * nsplit;
     const int tpi = (a.h * a.w) / TM;
@@ -257,8 +261,8 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 for (int kb = 0; kb < HKB; ++kb)
                     asm volatile(
                         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sm0 + (size_t)kb * 9 * NT * 128)),
-                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * 64), "r"(ntc * NT), "r"(0), "r"(bb)
+                        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sm0 + (size_t)kb * 9 * NT * RB)),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(kb * HKC), "r"(ntc * NT), "r"(0), "r"(bb)
                         : "memory");
             }
             for (int T = blockIdx.x; T < tiles && ok; T += gridDim.x) {
@@ -271,15 +275,15 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                         const uint32_t sa = smem_u32(sm + (size_t)r.s * stage_bytes), sb = sa + a_bytes;
                         if constexpr (HALO) {  // rows y0-1 .. y0+1, columns x0-1 .. x0+128 of channel block kb
                             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                         "r"(HALO_BOX) : "memory");
+                                         "r"(halo_box(HKC)) : "memory");
                             asm volatile(
                                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(sa),
-                                "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * 64), "r"(g.x0 - 1), "r"(g.y0 - 1),
+                                "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(kb * HKC), "r"(g.x0 - 1), "r"(g.y0 - 1),
                                 "r"(g.img), "r"(fb)
                                 : "memory");
                         } else {
-                            const int dy = MODE == CONV3 ? tap / 3 - 1 : 0, dx = MODE == CONV3 ? tap % 3 - 1 : 0;
+                            const int dy = MODE == TCONV ? 0 : tap / 3 - 1, dx = MODE == TCONV ? 0 : tap % 3 - 1;
                             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                                          "r"(stage_bytes) : "memory");
                             asm volatile(
@@ -334,16 +338,16 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     // to the start-address field (every address stays below 2^18)
                     uint64_t adesc[HKB];
 #pragma unroll
-                    for (int kb = 0; kb < HKB; ++kb) adesc[kb] = umma_desc(smem_u32(sm + (size_t)ss[kb] * stage_bytes), 64);
-                    const uint64_t bdesc = umma_desc(smem_u32(sm0), 64);
+                    for (int kb = 0; kb < HKB; ++kb) adesc[kb] = umma_desc(smem_u32(sm + (size_t)ss[kb] * stage_bytes), HKC);
+                    const uint64_t bdesc = umma_desc(smem_u32(sm0), HKC);
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
                         for (int kb = 0; kb < HKB; ++kb)
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = adesc[kb] + (uint64_t)((((tap / 3) * HALO_W + tap % 3) * 128 + kk * 32) >> 4);
-                                const uint64_t bd = bdesc + (uint64_t)(((kb * 9 + tap) * NT * 128 + kk * 32) >> 4);
+                            for (int kk = 0; kk < HKC / 16; ++kk) {
+                                const uint64_t ad = adesc[kb] + (uint64_t)((((tap / 3) * HALO_W + tap % 3) * RB + kk * 32) >> 4);
+                                const uint64_t bd = bdesc + (uint64_t)(((kb * 9 + tap) * NT * RB + kk * 32) >> 4);
                                 const uint32_t acc = (tap | kb | kk) ? 1u : 0u;
                                 asm volatile(
                                     "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
@@ -391,6 +395,62 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         const int half = (warp - 2) / 4;           // columns [half NS, (half + 1) NS)
         const int row = q * 32 + lane;             // pixel within the tile
         constexpr int HG = GPT / SHARES;           // groups per warp (CONV3: GPT groups per column tile)
+        static_assert(MODE != OUT3 || (NT == 16 && SHARES == 1), "the output layer is one 16-column tile");
+        if constexpr (MODE == OUT3) {
+            // u += gamma conv + beta for u = phi, c, rho.  The fields of the next PD tiles are loaded
+            // ahead, so that the read-modify-write of a tile does not wait for its loads.
+            constexpr int PD = 4;
+            float og[3], ob[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                og[f] = a.ogamma[f];
+                ob[f] = a.obeta[f];
+            }
+            float pv[PD][3];
+            float* pp[PD][3];
+            auto fetch = [&](int T, int d) {
+                if (T < tiles) {
+                    const TileGeo g = tile_geo(divs, T, NT);
+                    const size_t o = (size_t)(g.y0 + row / BW) * a.fpitch + g.x0 + row % BW;
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        pp[d][f] = a.fields[f * a.n + g.img] + o;
+                        pv[d][f] = *pp[d][f];
+                    }
+                }
+            };
+#pragma unroll
+            for (int d = 0; d < PD; ++d) fetch((int)blockIdx.x + d * (int)gridDim.x, d);
+            int local = 0;
+            for (int T = blockIdx.x; T < tiles; T += gridDim.x, ++local) {
+                const int b = local & 1;
+                if (!mbar_wait_sleep(smem_u32(&accf_bar[b]), (uint32_t)(local >> 1) & 1u, a.wait_cap, &abort_flag)) {
+                    abort_flag = 1;
+                    if (lane == 0) atomicOr(a.err, UNET_ERR_TIMEOUT);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint32_t r[4];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                             : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * NT)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[b])) : "memory");
+#pragma unroll
+                for (int f = 0; f < 3; ++f) *pp[0][f] = pv[0][f] + fmaf(og[f], __uint_as_float(r[f]), ob[f]);
+#pragma unroll
+                for (int d = 0; d + 1 < PD; ++d)
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) {
+                        pv[d][f] = pv[d + 1][f];
+                        pp[d][f] = pp[d + 1][f];
+                    }
+                fetch(T + PD * (int)gridDim.x, PD - 1);
+            }
+        } else {
         int local = 0;
         for (int T = blockIdx.x; T < tiles; T += gridDim.x, ++local) {
             const int b = local & 1;
@@ -418,30 +478,32 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                       "=r"(r[14]), "=r"(r[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                uint32_t pk[8];
+                {
+                    uint32_t pk[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float v0 = __uint_as_float(r[2 * j]), v1 = __uint_as_float(r[2 * j + 1]);
-                    pk[j] = pack_bf16x2(v0, v1);
-                }
-                uint16_t* dst;
-                if (MODE == CONV3) {
-                    constexpr int cg = NT / GPT;  // channels per group; NS = HG groups
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {  // the group index within the share is a compile-time constant
-                        const float v = __uint_as_float(r[j]);
-                        s1[(k0 + j) / cg] += v;
-                        s2[(k0 + j) / cg] = fmaf(v, v, s2[(k0 + j) / cg]);
+                    for (int j = 0; j < 8; ++j) {
+                        const float v0 = __uint_as_float(r[2 * j]), v1 = __uint_as_float(r[2 * j + 1]);
+                        pk[j] = pack_bf16x2(v0, v1);
                     }
-                    dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + g.n0 + c0;
-                } else {  // TCONV: column n0 + c0 + j = sub-pixel s * cout + channel
-                    const int col = g.n0 + c0, s = col / a.cout, co = col % a.cout;
-                    const int oy = 2 * py + (s >> 1), ox = 2 * px + (s & 1);
-                    dst = a.out + ((size_t)(g.img * 2 * a.h + oy) * (2 * a.w) + ox) * a.out_cstride + a.out_coff + co;
+                    uint16_t* dst;
+                    if (MODE == CONV3) {
+                        constexpr int cg = NT / GPT;  // channels per group; NS = HG groups
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {  // the group index within the share is a compile-time constant
+                            const float v = __uint_as_float(r[j]);
+                            s1[(k0 + j) / cg] += v;
+                            s2[(k0 + j) / cg] = fmaf(v, v, s2[(k0 + j) / cg]);
+                        }
+                        dst = a.out + ((size_t)(g.img * a.h + py) * a.w + px) * a.out_cstride + a.out_coff + g.n0 + c0;
+                    } else {  // TCONV: column n0 + c0 + j = sub-pixel s * cout + channel
+                        const int col = g.n0 + c0, s = col / a.cout, co = col % a.cout;
+                        const int oy = 2 * py + (s >> 1), ox = 2 * px + (s & 1);
+                        dst = a.out + ((size_t)(g.img * 2 * a.h + oy) * (2 * a.w) + ox) * a.out_cstride + a.out_coff + co;
+                    }
+                    uint4* d4 = reinterpret_cast<uint4*>(dst);
+                    d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
-                uint4* d4 = reinterpret_cast<uint4*>(dst);
-                d4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                d4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
             // the accumulator is drained: hand it back to the MMA issuer (one arrival per warp)
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -464,6 +526,7 @@ umma_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     a.partials[((((size_t)g.img * a.groups + gg) * tpi + g.t) * 4 + q) * 2 + st] = tot;
                 }
             }
+        }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -496,7 +559,7 @@ int sm_count()
     return n;
 }
 
-int conv_nt(int mode, int cout) { return mode == CONV3 ? cout : (4 * cout < 256 ? 4 * cout : 256); }
+int conv_nt(int mode, int cout) { return mode == TCONV ? (4 * cout < 256 ? 4 * cout : 256) : cout; }
 
 int conv_stages(int kc, int nt)
 {
@@ -517,26 +580,31 @@ bool encode(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, 
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Column tile of the halo form, or 0 where it does not apply: 3x3 convolutions of 64 or 128 channels
-// into at most 64, on rows that are whole 128-pixel tiles.  The weights of a column tile must fit
-// next to three stages: 64 -> N keeps all N columns, 128 -> N keeps 32 (two column tiles for N = 64).
+// Column tile of the halo form, or 0 where it does not apply: 3x3 convolutions of 32, 64 or 128
+// channels into at most 64, on rows that are whole 128-pixel tiles.  The weights of a column tile
+// must fit next to the stages: 32 or 64 -> N keeps all N columns, 128 -> N keeps 32 (two column
+// tiles for N = 64).  Channel blocks: one of 32 or 64 channels, or two of 64.
 int halo_nt(int mode, const ConvArgs& a)
 {
-    if (!g_halo_enabled || mode != CONV3 || a.w % TM || a.cout > 64) return 0;
-    return a.cin == 64 ? a.cout : (a.cin == 128 ? 32 : 0);
+    if (!g_halo_enabled || mode == TCONV || a.w % TM || a.cout > 64) return 0;
+    if (mode == OUT3) return a.cin == 32 ? a.cout : 0;
+    return (a.cin == 32 || a.cin == 64) ? a.cout : (a.cin == 128 ? 32 : 0);
 }
+
+int halo_kc(int cin) { return cin == 32 ? 32 : 64; }
 
 constexpr size_t HALO_SMEM = 225 * 1024;  // weights + stage ring (plus 1 KB of alignment slack)
 
-int halo_stages(int kblocks, int nt)
+int halo_stages(int cin, int nt)
 {
-    const int st = (int)((HALO_SMEM - (size_t)kblocks * 9 * nt * 128) / HALO_STAGE);
+    const int kc = halo_kc(cin);
+    const int st = (int)((HALO_SMEM - (size_t)cin * 2 * 9 * nt) / halo_stage(kc));
     return st > MAX_ST ? MAX_ST : st;
 }
 
 size_t conv_smem_bytes(int mode, int cin, int nt, bool halo, int stages)
 {
-    if (halo) return (size_t)(cin / 64) * 9 * nt * 128 + (size_t)stages * HALO_STAGE + 1024;
+    if (halo) return (size_t)cin * 2 * 9 * nt + (size_t)stages * halo_stage(halo_kc(cin)) + 1024;
     const int kc = conv_kc(cin);
     return (size_t)stages * (size_t)(TM * kc * 2 + nt * kc * 2) + 1024;
 }
@@ -558,16 +626,19 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     if (mode == CONV3 && ((a.cout != 32 && a.cout != 64 && a.cout != 128 && a.cout != 256) || a.groups != GN_MAX_GROUPS))
         return cudaErrorInvalidValue;
     if (mode == TCONV && a.cout != 16 && a.cout != 32 && a.cout != 64 && a.cout != 128) return cudaErrorInvalidValue;
+    if (mode == OUT3 && (a.cout != 16 || a.cin != 32 || !a.fields || !a.ogamma || !a.obeta || a.fpitch < a.w))
+        return cudaErrorInvalidValue;
+    if (mode == OUT3) a.partials = nullptr;
     if (a.out_coff % 8 || a.out_cstride % 8) return cudaErrorInvalidValue;  // 16-byte vector stores
-    const int ncols = mode == CONV3 ? a.cout : 4 * a.cout;
+    const int ncols = mode == TCONV ? 4 * a.cout : a.cout;
     a.kc = conv_kc(a.cin);
     const int hnt = halo_nt(mode, a);
-    const bool halo = hnt > 0 && halo_stages(a.cin / 64, hnt) >= 2;
+    const bool halo = hnt > 0 && halo_stages(a.cin, hnt) >= 2;
     a.nt = halo ? hnt : conv_nt(mode, a.cout);
     if (ncols % a.nt) return cudaErrorInvalidValue;
     const int nsplit = ncols / a.nt;
-    a.stages = halo ? halo_stages(a.cin / 64, a.nt) : conv_stages(a.kc, a.nt);
-    if (halo && a.stages < a.cin / 64) return cudaErrorInvalidValue;  // a tile's channel blocks are resident together
+    a.stages = halo ? halo_stages(a.cin, a.nt) : conv_stages(a.kc, a.nt);
+    if (halo && a.stages < a.cin / a.kc) return cudaErrorInvalidValue;  // a tile's channel blocks are resident together
     a.tmem_cols = 32;
     while (a.tmem_cols < 2 * a.nt) a.tmem_cols <<= 1;  // two accumulators
     const int BW = a.w < TM ? a.w : TM, BR = TM / BW;
@@ -577,7 +648,7 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     const cuuint64_t sA[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.w * a.cin * 2, (cuuint64_t)a.h * a.w * a.cin * 2};
     // halo mode: three rows of 130 pixels per box, and all nine taps of the weights in one box
     const cuuint32_t bA[4] = {(cuuint32_t)a.kc, (cuuint32_t)(halo ? HALO_W : BW), (cuuint32_t)(halo ? 3 : BR), 1u};
-    const int taps = mode == CONV3 ? 9 : 1;
+    const int taps = mode == TCONV ? 1 : 9;
     const cuuint64_t dB[3] = {(cuuint64_t)a.cin, (cuuint64_t)ncols, (cuuint64_t)taps};
     const cuuint64_t sB[2] = {(cuuint64_t)a.cin * 2, (cuuint64_t)ncols * a.cin * 2};
     const cuuint32_t bB[3] = {(cuuint32_t)a.kc, (cuuint32_t)a.nt, halo ? 9u : 1u};
@@ -617,6 +688,15 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
         cfg.gridDim = dim3((unsigned)grid);
         return cudaLaunchKernelEx(&cfg, kern, mA, mB, a);
     };
+    if (mode == OUT3) {
+        if (halo) return go(umma_conv_kernel<OUT3, 16, true, GN_MAX_GROUPS, 1, 32>);
+        return go(umma_conv_kernel<OUT3, 16>);
+    }
+    if (halo && a.cin == 32) {
+        if (a.nt == 32) return go(umma_conv_kernel<CONV3, 32, true, GN_MAX_GROUPS, 1, 32>);
+        if (a.nt == 64) return go(umma_conv_kernel<CONV3, 64, true, GN_MAX_GROUPS, 1, 32>);
+        return cudaErrorInvalidValue;
+    }
     if (halo) {
         const int kb = a.cin / 64;
         if (a.nt == 32 && nsplit == 1 && kb == 1) return go(umma_conv_kernel<CONV3, 32, true, GN_MAX_GROUPS, 1>);

@@ -12,7 +12,10 @@ namespace pf {
 // cuTensorMapEncodeTiled through the runtime's driver entry point (NULL if unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
-enum ConvMode { CONV3 = 0, TCONV = 1 };
+// CONV3: 3x3 convolution into BF16 channels (with group sums); TCONV: 2x2 stride-2 transposed
+// convolution; OUT3: 3x3 convolution whose first three output columns are added, through a
+// per-output affine (gamma, beta), to three FP32 fields in place (the U-Net's output layer).
+enum ConvMode { CONV3 = 0, TCONV = 1, OUT3 = 2 };
 constexpr int GN_MAX_GROUPS = 8;        // group normalisation groups of the hidden layers
 constexpr int UNET_ERR_TIMEOUT = 2;     // error-word bit: a bounded wait of a tensor-core kernel ran out
 
@@ -56,6 +59,10 @@ struct ConvArgs {
     float* partials;       // CONV3: per-tile group sums [n][groups][h*w/128][2], or NULL
     int* err;              // error word (UNET_ERR_TIMEOUT)
     int wait_cap;          // polls of a bounded mbarrier wait
+    float* const* fields;  // OUT3: device table of 3 n field pointers (phi of each image, then c, then rho)
+    int fpitch;            // OUT3: row pitch of the fields (floats)
+    const float* ogamma;   // OUT3: device, 3 values
+    const float* obeta;    // OUT3: device, 3 values
 };
 
 // Encode the tensor maps and launch.  in: BF16 NHWC [n][h][w][cin]; wgt: BF16

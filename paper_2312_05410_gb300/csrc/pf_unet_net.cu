@@ -155,88 +155,6 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Output: the last convolution (3x3, 32 -> 3) of BF16 NHWC [n][h][w][32], as per-channel affine
-// increments added to the FP32 fields in place: u_k += gamma_k conv_k + beta_k for u = (phi, c, rho).
-// One 128-pixel tile per block, 32 pixels per warp.  Lane l reads the 8 channels 8 (l % 4) .. + 7 of
-// pixels l / 4 + 8 g (g = 0..3), so that each 16-byte load of the warp covers 512 contiguous bytes
-// (8 whole pixels); the four partial sums of a pixel meet in two shuffle-halving steps, after which
-// lane l holds the three outputs of pixel l / 4 + 8 (l % 4).
-__global__ void __launch_bounds__(TPB)
-out_conv_kernel(const uint16_t* __restrict__ in, int h, int w, const float* __restrict__ wgt /* [9][32][3] */,
-                const float* __restrict__ gamma, const float* __restrict__ beta, float* const* __restrict__ phi,
-                float* const* __restrict__ c, float* const* __restrict__ rho, int pitch)
-{
-    __shared__ __align__(16) float ws[9 * 32 * 3];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = threadIdx.x; i < 9 * 32 * 3; i += TPB) ws[i] = wgt[i];
-    __syncthreads();
-    const int tpi = h * w / TPB;
-    const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
-    const int lane = threadIdx.x & 31, cq = lane & 3, ps = lane >> 2;
-    const int p0 = t * TPB + (threadIdx.x >> 5) * 32;
-    const uint16_t* src = in + (size_t)img * h * w * 32 + cq * 8;
-    int py[4], px[4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const int p = p0 + 8 * g + ps;
-        py[g] = p / w;
-        px[g] = p - py[g] * w;
-    }
-    float acc[12];  // [g][output]
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = 0.f;
-    for (int ky = 0; ky < 3; ++ky)
-        for (int kx = 0; kx < 3; ++kx) {
-            float wv[24];  // this lane's 8 channels x 3 outputs of the tap
-            const float4* wq = reinterpret_cast<const float4*>(ws + ((ky * 3 + kx) * 32 + cq * 8) * 3);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float4 v = wq[k];
-                wv[4 * k] = v.x;
-                wv[4 * k + 1] = v.y;
-                wv[4 * k + 2] = v.z;
-                wv[4 * k + 3] = v.w;
-            }
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                const int yy = py[g] + ky - 1, xx = px[g] + kx - 1;
-                if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
-                float f[8];
-                unpack8(*reinterpret_cast<const uint4*>(src + ((size_t)yy * w + xx) * 32), f);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    acc[3 * g] = fmaf(f[j], wv[3 * j], acc[3 * g]);
-                    acc[3 * g + 1] = fmaf(f[j], wv[3 * j + 1], acc[3 * g + 1]);
-                    acc[3 * g + 2] = fmaf(f[j], wv[3 * j + 2], acc[3 * g + 2]);
-                }
-            }
-        }
-    // halving over the 4 lanes of a pixel: offset 2 splits g in {0,1} | {2,3}, offset 1 splits g even | odd
-    {
-        const bool up = lane & 2;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float send = up ? acc[k] : acc[k + 6], keep = up ? acc[k + 6] : acc[k];
-            acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-        }
-    }
-    {
-        const bool up = lane & 1;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float send = up ? acc[k] : acc[k + 3], keep = up ? acc[k + 3] : acc[k];
-            acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-        }
-    }
-    const int g = cq;  // lane bits 1, 0 chose the upper halves: this lane now holds pixel ps + 8 cq
-    const int p = p0 + 8 * g + ps, y = p / w, x = p - y * w;
-    const size_t o = (size_t)y * pitch + x;
-    phi[img][o] = phi[img][o] + fmaf(gamma[0], acc[0], beta[0]);
-    c[img][o] = c[img][o] + fmaf(gamma[1], acc[1], beta[1]);
-    rho[img][o] = rho[img][o] + fmaf(gamma[2], acc[2], beta[2]);
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Group statistics -> per-channel affine of the normalisation: block (image, group) sums its
 // `entries` partial (sum, sum of squares) pairs in FP64 in a fixed order, and writes for every
 // channel k of the group affine = (a, b) with a = gamma_k / sqrt(var + eps), b = beta_k - mean a,
@@ -437,15 +355,6 @@ cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
     return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, rho, pitch, h, w, tau, wgt, out, partials);
-}
-
-cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, const float* gamma,
-                            const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
-                            cudaStream_t s)
-{
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
-    return cudaLaunchKernelEx(&cfg, out_conv_kernel, in, h, w, wgt, gamma, beta, phi, c, rho, pitch);
 }
 
 cudaError_t launch_gn_stats(const float* partials, int n, int groups, int entries, double count, int C,

@@ -13,9 +13,6 @@ constexpr float UNET_EPS = 1e-5f;    // group-normalisation epsilon
 cudaError_t launch_cond(const double* mlp, const double* proj, double tau, float* scales, int nscales, cudaStream_t s);
 cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const float* const* rho, int pitch, int n,
                            int h, int w, float tau, const float* wgt, uint16_t* out, float* partials, cudaStream_t s);
-cudaError_t launch_out_conv(const uint16_t* in, int n, int h, int w, const float* wgt, const float* gamma,
-                            const float* beta, float* const* phi, float* const* c, float* const* rho, int pitch,
-                            cudaStream_t s);
 cudaError_t launch_gn_stats(const float* partials, int n, int groups, int entries, double count, int C,
                             const float* gamma, const float* beta, float* affine, cudaStream_t s);
 cudaError_t launch_gn_enc(const uint16_t* x, int n, int h, int w, int C, const float* affine, const float* scale,

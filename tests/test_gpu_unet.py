@@ -51,7 +51,7 @@ def to_nchw(t):
 @pytest.mark.parametrize("n,h,w,cin,cout", [(2, 32, 32, 64, 128), (1, 16, 64, 32, 64), (1, 8, 256, 128, 32),
                                             (3, 8, 16, 256, 256), (1, 4, 32, 96, 64),
                                             (2, 8, 256, 64, 32), (1, 6, 384, 64, 64), (1, 1, 128, 64, 32),
-                                            (2, 8, 128, 128, 64), (1, 3, 256, 128, 32)])
+                                            (2, 8, 128, 128, 64), (1, 3, 256, 128, 32), (2, 8, 128, 32, 64)])
 def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
     g = np.random.default_rng(n * 1000 + cin + cout)
     x = U.bf16(g.standard_normal((n, cin, h, w)))
@@ -76,9 +76,10 @@ def test_conv3x3_within_one_bf16_ulp_of_the_fp64_sum(pf, n, h, w, cin, cout):
 
 
 @pytest.mark.parametrize("n,h,w,cin,cout", [(2, 16, 256, 64, 32), (1, 5, 128, 64, 64), (3, 2, 512, 64, 32),
-                                            (2, 8, 128, 128, 64), (1, 4, 256, 128, 32)])
+                                            (2, 8, 128, 128, 64), (1, 4, 256, 128, 32), (2, 6, 128, 32, 64),
+                                            (1, 3, 256, 32, 32)])
 def test_halo_staging_gives_the_same_sums_as_per_tap_staging(pf, n, h, w, cin, cout):
-    """64- and 128-channel tiles on 128-pixel rows take the halo path by default (128 -> 64 as two
+    """32-, 64- and 128-channel tiles on 128-pixel rows take the halo path by default (128 -> 64 as two
     column tiles of 32); the per-tap path adds the same products in the same order (tap by tap, then
     channel block, 16 channels at a time), so the two agree bit for bit, group sums included."""
     g = np.random.default_rng(h * w + cin + cout)
