@@ -91,9 +91,11 @@ __device__ __forceinline__ void unpack8(const uint4 v, float* f)
 }
 
 // First convolution: x = BF16(phi, c, rho, tau) with zero padding outside the image, 3x3, 4 -> 32.
-// One thread per output pixel, one 128-pixel tile per block (neighbours come through L1: staging
-// the halo in shared memory measured slower).  The 32 outputs are 16 pairs updated by packed FP32x2
-// FMAs (each half runs the scalar chain unchanged); group sums: one scatter-halving per warp.
+// A block covers two consecutive 128-pixel tiles of one image; thread t computes pixel t of each
+// (neighbours come through L1: staging the halo in shared memory measured slower).  The 32 outputs
+// are 16 pairs updated by packed FP32x2 FMAs (each half runs the scalar chain unchanged), and each
+// weight pair read from shared memory serves both pixels.  Group sums: one scatter-halving per warp
+// and tile.
 __global__ void __launch_bounds__(TPB)
 in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
                const float* const* __restrict__ rho, int pitch, int h, int w, float tau,
@@ -101,56 +103,94 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
                float* __restrict__ partials)
 {
     __shared__ __align__(16) float ws[36 * 32];
-    __shared__ float red[4][16];
+    __shared__ float red[2][4][16];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = threadIdx.x; i < 36 * 32; i += TPB) ws[i] = wgt[i];
     __syncthreads();
-    const int tpi = h * w / TPB;
-    const int img = blockIdx.x / tpi, t = blockIdx.x % tpi;
-    const int p = t * TPB + threadIdx.x, y = p / w, x = p % w;
+    const int tpi = h * w / TPB, bpi = (tpi + 1) / 2;  // tiles and blocks per image
+    const int img = blockIdx.x / bpi, t0 = 2 * (blockIdx.x % bpi);
+    const bool two = t0 + 1 < tpi;
     const float* F = phi[img];
     const float* C = c[img];
     const float* Rh = rho[img];
     const float tb = rbf(tau);
-    const float2* ws2 = reinterpret_cast<const float2*>(ws);
-    float2 acc[16];
+    int y[2], x[2];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) acc[o] = make_float2(0.f, 0.f);
+    for (int k = 0; k < 2; ++k) {
+        const int p = (t0 + k) * TPB + threadIdx.x;
+        y[k] = p / w;
+        x[k] = p % w;
+    }
+    const float2* ws2 = reinterpret_cast<const float2*>(ws);
+    float2 acc[2][16];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[k][o] = make_float2(0.f, 0.f);
     for (int ky = 0; ky < 3; ++ky)
         for (int kx = 0; kx < 3; ++kx) {
-            const int yy = y + ky - 1, xx = x + kx - 1;
-            const bool in = yy >= 0 && yy < h && xx >= 0 && xx < w;
-            const size_t o = in ? (size_t)yy * pitch + xx : 0;
-            const float v0 = in ? rbf(F[o]) : 0.f, v1 = in ? rbf(C[o]) : 0.f;
-            const float v2 = in ? rbf(Rh[o]) : 0.f, v3 = in ? tb : 0.f;
-            const float2 b0 = make_float2(v0, v0), b1 = make_float2(v1, v1);
-            const float2 b2 = make_float2(v2, v2), b3 = make_float2(v3, v3);
-            const float2* wk = ws2 + (ky * 3 + kx) * 4 * 16;
+            float2 b[2][4];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-                acc[q] = __ffma2_rn(b0, wk[q], __ffma2_rn(b1, wk[16 + q],
-                                   __ffma2_rn(b2, wk[32 + q], __ffma2_rn(b3, wk[48 + q], acc[q]))));
+            for (int k = 0; k < 2; ++k) {
+                const int yy = y[k] + ky - 1, xx = x[k] + kx - 1;
+                const bool in = (k == 0 || two) && yy >= 0 && yy < h && xx >= 0 && xx < w;
+                const size_t o = in ? (size_t)yy * pitch + xx : 0;
+                const float v0 = in ? rbf(F[o]) : 0.f, v1 = in ? rbf(C[o]) : 0.f;
+                const float v2 = in ? rbf(Rh[o]) : 0.f, v3 = in ? tb : 0.f;
+                b[k][0] = make_float2(v0, v0);
+                b[k][1] = make_float2(v1, v1);
+                b[k][2] = make_float2(v2, v2);
+                b[k][3] = make_float2(v3, v3);
+            }
+            const float4* wk = reinterpret_cast<const float4*>(ws2 + (ky * 3 + kx) * 4 * 16);
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) {  // two output pairs per 16-byte weight load
+                float4 wv[4];
+#pragma unroll
+                for (int ci = 0; ci < 4; ++ci) wv[ci] = wk[ci * 8 + q2];
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int q = 2 * q2 + h2;
+                    float2 wc[4];
+#pragma unroll
+                    for (int ci = 0; ci < 4; ++ci)
+                        wc[ci] = h2 ? make_float2(wv[ci].z, wv[ci].w) : make_float2(wv[ci].x, wv[ci].y);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        acc[k][q] = __ffma2_rn(b[k][0], wc[0], __ffma2_rn(b[k][1], wc[1],
+                                               __ffma2_rn(b[k][2], wc[2], __ffma2_rn(b[k][3], wc[3], acc[k][q]))));
+                }
+            }
         }
-    uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)img * h * w + p) * 32);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        dst[q] = make_uint4(to_bf2(acc[4 * q].x, acc[4 * q].y), to_bf2(acc[4 * q + 1].x, acc[4 * q + 1].y),
-                            to_bf2(acc[4 * q + 2].x, acc[4 * q + 2].y), to_bf2(acc[4 * q + 3].x, acc[4 * q + 3].y));
-    // group sums (8 groups of 4 channels): value 2 g + k is the sum (k = 0) or the sum of squares (k = 1)
-    float sv[16];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-        const float2 a0 = acc[2 * g], a1 = acc[2 * g + 1];
-        sv[2 * g] = (a0.x + a0.y) + (a1.x + a1.y);
-        sv[2 * g + 1] = fmaf(a1.y, a1.y, fmaf(a1.x, a1.x, fmaf(a0.y, a0.y, a0.x * a0.x)));
-    }
     const int lane = threadIdx.x & 31;
-    const float tot = warp_sum_scatter<16>(sv, lane);  // even lane l: value l / 2
-    if (!(lane & 1)) red[threadIdx.x >> 5][lane >> 1] = tot;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !two) break;
+        uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)img * h * w + (size_t)(t0 + k) * TPB + threadIdx.x) * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            dst[q] = make_uint4(to_bf2(acc[k][4 * q].x, acc[k][4 * q].y), to_bf2(acc[k][4 * q + 1].x, acc[k][4 * q + 1].y),
+                                to_bf2(acc[k][4 * q + 2].x, acc[k][4 * q + 2].y),
+                                to_bf2(acc[k][4 * q + 3].x, acc[k][4 * q + 3].y));
+        // group sums (8 groups of 4 channels): value 2 g + j is the sum (j = 0) or the sum of squares (j = 1)
+        float sv[16];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const float2 a0 = acc[k][2 * g], a1 = acc[k][2 * g + 1];
+            sv[2 * g] = (a0.x + a0.y) + (a1.x + a1.y);
+            sv[2 * g + 1] = fmaf(a1.y, a1.y, fmaf(a1.x, a1.x, fmaf(a0.y, a0.y, a0.x * a0.x)));
+        }
+        const float tot = warp_sum_scatter<16>(sv, lane);  // even lane l: value l / 2
+        if (!(lane & 1)) red[k][threadIdx.x >> 5][lane >> 1] = tot;
+    }
     __syncthreads();
-    if (threadIdx.x < 16) {
-        const int g = threadIdx.x >> 1, which = threadIdx.x & 1;
-        partials[(((size_t)img * 8 + g) * tpi + t) * 2 + which] = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+    if (threadIdx.x < 32) {
+        const int k = threadIdx.x >> 4, i = threadIdx.x & 15;
+        if (k == 0 || two) {
+            const int g = i >> 1, which = i & 1;
+            partials[(((size_t)img * 8 + g) * tpi + t0 + k) * 2 + which] =
+                red[k][0][i] + red[k][1][i] + red[k][2][i] + red[k][3][i];
+        }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -353,7 +393,7 @@ cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const
                            int h, int w, float tau, const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * (h * w / TPB))), TPB, s, attr);
+    cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * ((h * w / TPB + 1) / 2))), TPB, s, attr);
     return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, rho, pitch, h, w, tau, wgt, out, partials);
 }
 
