@@ -273,7 +273,7 @@ const char* pf_adjoint_last_error(void);
  *   out is n x 2h x 2w pixels.
  * Shapes: cin % 32 == 0 (<= 1024); conv: cout in {32, 64, 128, 256} with groups
  * = 8 (the U-Net's widths); transposed conv: cout in {16, 32, 64, 128}; h*w % 128
- * == 0 and w a multiple or a divisor of 128; pointers
+ * == 0 and w a multiple or a divisor of 128; n h w < 2^27 (2^20 tiles of 128 pixels); pointers
  * 16-byte aligned; out_coff and out_cstride multiples of 8.  err_dev: device int;
  * bit 1 is set if a bounded pipeline wait ran out (the kernel then stops early).
  * Asynchronous on `stream`; PF_ERR_ARG / PF_ERR_LAYOUT / PF_ERR_CUDA on errors, with
@@ -315,7 +315,8 @@ int pf_conv_halo(int on);
  * pf_unet_workspace_size: bytes of caller-owned device workspace (weights in
  *   device layouts, all activations, statistics, tables); 0 if the shape is
  *   unsupported.  Supported shapes: sides >= 128 and multiples of 8, nx/8 dividing
- *   or a multiple of 128, (nx/8)(ny/8) a multiple of 128 (e.g. 128^2, 256^2, 512^2).
+ *   or a multiple of 128, (nx/8)(ny/8) a multiple of 128 (e.g. 128^2, 256^2, 512^2),
+ *   and batch nx ny < 2^27.
  * pf_unet_init: weights = 40 host FP32 arrays, in PyTorch layouts and this order:
  *   0-5   mlp_w0 [128][1], mlp_b0 [128], mlp_w1 [128][128], mlp_b1, mlp_w2 [128][128], mlp_b2
  *   6-9   proj1..proj4 [C_p][128] (C = 32, 64, 128, 256)

@@ -107,6 +107,7 @@ enum { A_PRE1, A_CAT1, A_P1, A_PRE2, A_CAT2, A_P2, A_PRE3, A_CAT3, A_P3, A_PRE4,
 bool shape_ok(int n, int h, int w)
 {
     if (n < 1 || n > 4096 || h < 128 || w < 128 || h > 8192 || w > 8192 || h % 8 || w % 8) return false;
+    if ((long long)n * h * w >= (1LL << 27)) return false;  // the convolutions' tile-index range
     const int w8 = w / 8;
     if ((w8 % 128) && (128 % w8)) return false;
     return ((long long)(h / 8) * w8) % 128 == 0;

@@ -114,19 +114,20 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return d;
 }
 
-// Quotient and remainder of a non-negative int by a positive divisor through a reciprocal
-// computed once: the FP64 product is within 2^-52 relative of x / d, so the truncated
-// quotient is off by at most one, and one correction step makes it exact.
+// Quotient and remainder of a non-negative int x < 2^22 by a positive divisor through an FP32
+// reciprocal computed once: x and 1/d are exact to 2^-24 relative, so the product is within 1/2 of
+// x / d and the truncated quotient is off by at most one; one correction step makes it exact.
+// (The GPU's FP64 rate is too low for this to be done in double precision on the hot path.)
 struct FastDiv {
     int d;
-    double inv;
+    float inv;
 };
 
-__device__ __forceinline__ FastDiv make_fastdiv(int d) { return {d, 1.0 / (double)d}; }
+__device__ __forceinline__ FastDiv make_fastdiv(int d) { return {d, 1.0f / (float)d}; }
 
 __device__ __forceinline__ int fast_divmod(int x, const FastDiv& f, int& r)
 {
-    int q = __double2int_rz((double)x * f.inv);
+    int q = __float2int_rz(__int2float_rn(x) * f.inv);
     r = x - q * f.d;
     if (r < 0) {
         --q;
@@ -637,6 +638,8 @@ cudaError_t launch_umma_conv(int mode, const uint16_t* in, const uint16_t* wgt, 
     a.nt = halo ? hnt : conv_nt(mode, a.cout);
     if (ncols % a.nt) return cudaErrorInvalidValue;
     const int nsplit = ncols / a.nt;
+    // tile indices (pixel tiles x at most 2 column tiles) stay below 2^22, the range of the FP32 divisions
+    if ((long long)a.n * a.h * a.w / TM >= (1LL << 20) || nsplit > 2) return cudaErrorInvalidValue;
     a.stages = halo ? halo_stages(a.cin, a.nt) : conv_stages(a.kc, a.nt);
     if (halo && a.stages < a.cin / a.kc) return cudaErrorInvalidValue;  // a tile's channel blocks are resident together
     a.tmem_cols = 32;
