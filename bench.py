@@ -317,7 +317,8 @@ class HybridRun:
         self.jump_flops = W["n_runs"] * flops_per_sample(side, side)
         self.config = {"runs": W["n_runs"], "nx": side, "ny": side, "timesteps_per_run": self.nsteps,
                        "dns_stretch": self.stretch, "jump_steps": self.jump_steps, "cycles": self.cycles,
-                       "unet": "32-64-128-256, BF16 tensor-core convolutions, seeded untrained weights",
+                       "unet": "32-64-128-256, BF16 tensor-core convolutions, "
+                               + ("trained weights" if wpath else "seeded untrained weights"),
                        "launch": "fused ensemble step launches (graph replays) + ~31 U-Net launches per jump"}
 
     def reset_counters(self):
