@@ -6,14 +6,13 @@
 //                   per-level conditioning factors W_p f(dt), in FP64, stored as BF16 values
 //   in_conv_kernel  the first 3x3 convolution (4 -> 32 channels) straight from the DNS
 //                   fields (phi, c, rho and a plane holding dt / dt_ref), with its group sums
-//   out_conv_kernel the last 3x3 convolution (32 -> 3) as affine increments of the DNS fields
-//   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums (FP64, fixed order),
+//   gn_stats_kernel group mean and 1/sqrt(var + eps) from the per-tile sums (FP32, fixed order),
 //                   folded with gamma and beta into a per-channel affine a x + b
 //   gn_apply_*      GN + GELU (+ conditioning product, + 2x2 max pooling) on stored BF16 values
+// (the last convolution, 32 -> 3, runs on the tensor cores: OUT3 mode of pf_unet_conv.cu)
 //
 // Storage follows the precision model of the reference: every stored activation is BF16
-// (round to nearest even), sums are FP32 (FP64 for the statistics), products of BF16 values
-// are exact in FP32.
+// (round to nearest even), sums are FP32, products of BF16 values are exact in FP32.
 #include <cstdint>
 
 #include "pf_unet_internal.h"
