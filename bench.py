@@ -256,7 +256,9 @@ class AdjointRun:
 class HybridRun:
     """The hybrid solver: a batch of runs advanced by DNS stretches (one fused ensemble launch per
     step) alternating with jumps of the time-conditioned U-Net (tensor-core convolutions), against
-    the same runs advanced by plain DNS.  The weights are seeded and untrained."""
+    the same runs advanced by plain DNS.  The weights are seeded and untrained unless a trained
+    set is given.  Both runs use the tile shape the ensemble autotuner picks for this batch (timed
+    on a throwaway copy, so the measured runs start from the seeded state)."""
 
     def __init__(self, pf, W):
         import torch
@@ -267,8 +269,11 @@ class HybridRun:
             p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
             ms.append((p, *I.film_state(m["spec"], p)))
         self.pf = pf
+        probe = pf.Ensemble(ms)
+        self.tile, _ = probe.autotune(20)
+        probe.close()
         self.ens = pf.Ensemble(ms)
-        self.ens.set_tile(0)
+        self.ens.set_tile(self.tile)
         self.stream = self.ens.stream
         self.fields = [t for run in self.ens.fields for t in run]
         side = W["side"]
@@ -319,6 +324,7 @@ class HybridRun:
                        "dns_stretch": self.stretch, "jump_steps": self.jump_steps, "cycles": self.cycles,
                        "unet": "32-64-128-256, BF16 tensor-core convolutions, "
                                + ("trained weights" if wpath else "seeded untrained weights"),
+                       "dns_tile": ("56x8", "56x24", "56x16")[self.tile] + " (autotuned)",
                        "launch": "fused ensemble step launches (graph replays) + ~31 U-Net launches per jump"}
 
     def reset_counters(self):

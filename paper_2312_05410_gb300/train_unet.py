@@ -38,8 +38,11 @@ def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 2000, 
         p = I.default_params(v_mag=m["v_mag"])
         p["dt"] = 0.5 * pf.pf_dt_limit(p)[0]
         ms.append((p, *I.film_state(m["spec"], p)))
+    probe = pf.Ensemble(ms)  # the autotuner's tile shape, timed on a throwaway copy of the batch
+    tile, _ = probe.autotune(20)
+    probe.close()
     ens = pf.Ensemble(ms)
-    ens.set_tile(0)
+    ens.set_tile(tile)
 
     def grab():
         return torch.stack([torch.stack([run[q][:, :side] for q in range(3)]) for run in ens.fields]).clone()
