@@ -23,10 +23,15 @@
 // again) and frees its tensor memory.  The N tile is a template parameter, so the
 // epilogue's loops unroll and its group indices are compile-time constants.
 //
+// Halo form (3x3 convolutions of 32, 64 or 128 channels on rows that are whole tiles): one box of
+// 3 rows x 130 pixels per channel block serves all nine taps as shifted windows, and the weights
+// of the CTA's column tile stay resident for the whole launch (see halo_box below).
+//
 // Epilogues: CONV3 stores the raw convolution (BF16, into a channel slice of an
 // NHWC buffer) and, per 32-pixel quarter of each tile, the sums of the FP32
 // values and of their squares per normalisation group; TCONV scatters each input
-// pixel's 4 x Cout outputs to the 2x2 block of output pixels it feeds.
+// pixel's 4 x Cout outputs to the 2x2 block of output pixels it feeds; OUT3 adds
+// gamma x (its first three columns) + beta to three FP32 fields in place.
 #include <cstdint>
 #include <cstring>
 
@@ -87,12 +92,13 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, int kc)
     return d;
 }
 
-// Halo mode (CONV3, 64 input channels, rows of at least 128 pixels): a tile's three input rows of
-// 130 pixels (the 128 of the tile and one on each side) arrive in ONE box; tap (dy, dx) is the
-// 128-row window starting at row (dy + 1) * 130 + dx + 1 of it.  TMA and the MMA both apply the
-// 128-byte swizzle as a function of the absolute shared-memory address (the copy starts on a
-// 1024-byte boundary), so a window that starts at any 128-byte row takes a plain descriptor with
-// base offset 0.  The weights of all taps stay resident in shared memory for the whole launch.
+// Halo form (3x3, 32, 64 or 128 input channels, rows that are whole 128-pixel tiles): per channel
+// block, a tile's three input rows of 130 pixels (the 128 of the tile and one on each side) arrive
+// in ONE box; tap (dy, dx) is the 128-row window starting at row (dy + 1) * 130 + dx + 1 of it.
+// TMA and the MMA both apply the 128- or 64-byte swizzle as a function of the absolute shared-
+// memory address (the copy starts on a 1024-byte boundary), so a window that starts at any row
+// takes a plain descriptor with base offset 0.  The weights of the CTA's column tile, all taps,
+// stay resident in shared memory for the whole launch.
 constexpr int HALO_W = TM + 2;
 // Bytes of a tile's box with channel blocks of kc (rows of 2 kc bytes), and the stage stride
 // (1024-byte aligned, a whole number of swizzle atoms of either width).
