@@ -190,6 +190,34 @@ def test_unet_jump_matches_the_reference_network(pf):
     net.close()
 
 
+def test_jump_is_the_same_with_halo_and_per_tap_staging(pf):
+    """A whole jump at 256^2 (every halo form: 32, 64 and 128 input channels, the two-column-tile split,
+    the output layer) against the same jump with every convolution staged per tap: bit for bit."""
+    from paper_2312_05410_gb300 import inputs as I2
+    import oracle as O
+    W = I2.unet_weights(3)
+    p = O.with_dt(I2.default_params())
+    states = [I2.film_state(I2.FilmSpec(256, 256, 60.0, seed=20 + k), p) for k in range(2)]
+    out = []
+    prev = pf.conv_halo(True)
+    try:
+        for on in (True, False):
+            pf.conv_halo(on)
+            fields = [tuple(pf.device_fields(st)) for st in states]
+            net = pf.UNet(W, 2, 256, 256)
+            net.jump(fields, 0.5)
+            net.sync()
+            out.append([[t.clone() for t in f] for f in fields] + [net.buffer("h1").clone()])
+            net.close()
+    finally:
+        pf.conv_halo(prev)
+    a, b = out
+    assert torch.equal(a[-1], b[-1])
+    for fa, fb in zip(a[:-1], b[:-1]):
+        for x, y in zip(fa, fb):
+            assert torch.equal(x, y)
+
+
 def test_plausibility_check_flags_out_of_range_runs(pf):
     from paper_2312_05410_gb300 import inputs as I2
     import oracle as O
