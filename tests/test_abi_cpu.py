@@ -127,3 +127,22 @@ def test_ensemble_init_error_paths(pf):
     assert _ens_init(pf, [good, good], shapes, work_bytes=4096) == pf.PF_ERR_LAYOUT
     assert _ens_init(pf, [good, good], [(64, 64), (0, 5)]) == pf.PF_ERR_ARG
     assert _ens_init(pf, [good, good], shapes, ptr=FAKE + 4) == pf.PF_ERR_LAYOUT
+
+
+def test_unet_workspace_shape_rules(pf):
+    """Host-side shape rules of the U-Net surrogate: sides >= 128 and multiples of 8, the quarter-resolution
+    width dividing or a multiple of the 128-pixel tile, and fewer than 2^27 pixels in the batch (the range
+    of the convolutions' tile indices)."""
+    ws = pf.lib.pf_unet_workspace_size
+    s16 = ws(16, 256, 256)
+    assert s16 > 0 and s16 % 256 == 0
+    # at least the full-resolution activations: pre1, cat1 (64 channels), h1, in BF16
+    assert s16 >= 2 * 16 * 256 * 256 * (32 + 64 + 32)
+    assert ws(32, 256, 256) > s16 > ws(8, 256, 256) > 0
+    assert ws(1, 128, 128) > 0 and ws(1, 512, 512) > 0 and ws(2, 1024, 128) > 0
+    for n, nx, ny in ((0, 256, 256), (1, 120, 256), (1, 256, 120), (1, 260, 256), (1, 384, 256),
+                      (4097, 128, 128)):
+        assert ws(n, nx, ny) == 0, (n, nx, ny)
+    # 2^27 pixels: 2047 runs of 256^2 fit, 2048 do not
+    assert ws(2047, 256, 256) > 0
+    assert ws(2048, 256, 256) == 0
