@@ -168,3 +168,21 @@ def test_flop_count_matches_the_layer_shapes():
     # 256^2: encoder 151 M + 3 x 604 M, decoder 1208 M + 3 x 2416 M, up-sampling 3 x 268 M, output 113 M
     want = 151.0e6 + 3 * 604.0e6 + 1208.0e6 + 3 * 2416.0e6 + 3 * 268.4e6 + 113.2e6
     assert U.flops_per_sample(256, 256) == pytest.approx(want, rel=1e-3)
+
+
+def test_training_network_is_the_reference_network():
+    """The network that train_unet.py fits (PyTorch operations, FP32, no BF16 storage) and the FP64
+    reference network that the inference kernels are tested against are the same function: their
+    increments agree to 1 % (the BF16 storage of the reference), while a conditioning factor scaled by 2
+    or a reversed channel order in the last block moves it by 30 % and more."""
+    from paper_2312_05410_gb300 import train_unet as T
+    net = T.make_model(0)
+    W = {k: v.detach().numpy().copy() for k, v in net.p.items()}
+    x = _net_input()
+    with torch.no_grad():
+        y = net(torch.tensor(x, dtype=torch.float32), 0.25).double().numpy()
+    ref = U.forward(W, x, 0.25)
+    base = x[:, :3].astype(np.float32).astype(np.float64)
+    assert _rel(y - base, ref - base) < 3e-2
+    assert _rel(U.forward(dict(W, proj1=W["proj1"] * 2.0), x, 0.25) - base, ref - base) > 0.1
+    assert _rel(U.forward(dict(W, dec1=W["dec1"][:, ::-1].copy()), x, 0.25) - base, ref - base) > 0.1
