@@ -292,7 +292,7 @@ class HybridRun:
         self.stretch, self.jump_steps = W["dns_stretch"], W["jump"]
         self.cycles = self.nsteps // (self.stretch + self.jump_steps)
 
-        self.launches = self.cycles * (self.stretch + 31)
+        self.launches = self.cycles * (self.stretch + 28 + 1)  # DNS steps, the jump's kernels, the check
         self.fallbacks = 0
         init = [t.clone() for t in self.fields]
         self.backup = [t.clone() for t in self.fields]
@@ -325,7 +325,8 @@ class HybridRun:
                        "unet": "32-64-128-256, BF16 tensor-core convolutions, "
                                + ("trained weights" if wpath else "seeded untrained weights"),
                        "dns_tile": ("56x8", "56x24", "56x16")[self.tile] + " (autotuned)",
-                       "launch": "fused ensemble step launches (graph replays) + ~31 U-Net launches per jump"}
+                       "launch": "fused ensemble step launches (graph replays) + 28 U-Net launches and one "
+                                 "plausibility check per jump"}
 
     def reset_counters(self):
         pass
