@@ -349,6 +349,8 @@ class HybridRun:
                         t.copy_(b)
                 self.ens.step(self.jump_steps)
                 self.fallbacks += 1
+        # DNS steps, the jump's 28 kernels and the check per cycle, and the DNS steps of any fallback
+        self.launches = self.cycles * (self.stretch + 28 + 1) + self.fallbacks * self.jump_steps
 
     def final_diag(self):
         """[relative L2 of phi, of c, mean relative L2 of the S2 map] of the hybrid final states
