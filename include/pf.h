@@ -309,8 +309,11 @@ int pf_conv_halo(int on);
  *     - the vapor density is predicted as well, because resetting it after each jump
  *       instead costs 12.6% relative L2 in phi over 25 exact jumps.
  * Channels are 32-64-128-256, with 8 groups in the hidden normalisations.  Weights and activations are stored as BF16 and
- * accumulated in FP32; the 3x3 and transposed convolutions of levels 2-4 and of
- * the decoder run on the tensor cores (pf_conv3x3_bf16 / pf_tconv2x2_bf16).
+ * accumulated in FP32; the 3x3 and transposed convolutions of levels 2-4, of
+ * the decoder and of the output layer run on the tensor cores (the kernels of
+ * pf_conv3x3_bf16 / pf_tconv2x2_bf16; the output layer as a 16-column tile whose
+ * epilogue adds the affine increment to the fields); the first convolution, the
+ * normalisations (GELU through the hardware tanh) and the MLP run on the CUDA cores.
  *
  * pf_unet_workspace_size: bytes of caller-owned device workspace (weights in
  *   device layouts, all activations, statistics, tables); 0 if the shape is
@@ -331,8 +334,8 @@ int pf_conv_halo(int on);
  *   work: 256-byte aligned.
  * pf_unet_jump: advances (phi[i], c[i], rho[i]) of runs i < n (n == batch; device
  *   FP32 fields ny x nx with row pitch `pitch` floats) in place by the predicted
- *   increments for jump length tau.  Asynchronous on the handle's stream, about 30
- *   kernel launches.
+ *   increments for jump length tau.  Asynchronous on the handle's stream, 28
+ *   kernel launches (29 when tau differs from the previous jump's: the MLP basis).
  * pf_unet_sync: synchronise; PF_ERR_TIMEOUT if a tensor-core pipeline wait ran out.
  * pf_unet_check: plausibility of the last jump's prediction, the hybrid solver's
  *   gate for its plain-DNS fallback.  ok[i] (host, n ints) is 1 if every phi, c and
