@@ -182,10 +182,13 @@ int pf_diagnostics(const pf_params* p, int nx, int ny, int pitch,
  * static device array of 1216 x 4 doubles plus an error word (about 39 KB)
  * that every GPU loading the library keeps until the process exits; any grid
  * the library accepts (sides up to 2^20) fits in it, other sizes are rejected
- * with PF_ERR_ARG / PF_ERR_LAYOUT.  The first call on each device performs a
- * one-time set-up (it looks up the array's device address), so make that first
- * call before any stream capture.  All calls share the array: calls that can
- * overlap on the GPU (unordered streams) race.  Nothing is allocated.
+ * with PF_ERR_ARG / PF_ERR_LAYOUT (pf_last_error() gives the reason).  The
+ * array's device address is looked up on every call made outside a stream
+ * capture and remembered per device and CUDA context; a call made while
+ * `stream` is being captured reuses the remembered address, so make the first
+ * call on each device, and the first after a cudaDeviceReset, before any
+ * stream capture.  All calls share the array: calls that can overlap on the
+ * GPU (unordered streams) race.  Nothing is allocated.
  * Returns PF_OK or a PF_ERR_* code; asynchronous on `stream`.
  */
 int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,

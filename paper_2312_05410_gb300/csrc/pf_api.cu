@@ -13,9 +13,11 @@
 #include "pf.h"
 #include "pf_internal.h"
 
-namespace {
+namespace pf {
 
+namespace {
 thread_local std::string g_last_error;
+}
 
 int fail(int code, const char* fmt, ...)
 {
@@ -32,6 +34,28 @@ int cuda_fail(cudaError_t e, const char* what)
 {
     return fail(PF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+constexpr int MAX_SIDE = 1 << 20;
+
+int check_sizes(int nx, int ny, int pitch)
+{
+    if (nx < 1 || ny < 1) return fail(PF_ERR_ARG, "empty grid (nx=%d, ny=%d)", nx, ny);
+    if (nx > MAX_SIDE || ny > MAX_SIDE)
+        return fail(PF_ERR_ARG, "grid side above %d (nx=%d, ny=%d)", MAX_SIDE, nx, ny);
+    if (pitch < nx || pitch % 4 != 0)
+        return fail(PF_ERR_LAYOUT, "pitch %d must be >= nx=%d and a multiple of 4", pitch, nx);
+    return PF_OK;
+}
+
+const char* last_error_text() { return g_last_error.c_str(); }
+
+}  // namespace pf
+
+namespace {
+
+using pf::check_sizes;
+using pf::cuda_fail;
+using pf::fail;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -63,18 +87,6 @@ Layout layout(int nx, int ny, int pitch, int history_rows)
     off = align256(off + sizeof(int));
     L.total = off;
     return L;
-}
-
-constexpr int MAX_SIDE = 1 << 20;
-
-int check_sizes(int nx, int ny, int pitch)
-{
-    if (nx < 1 || ny < 1) return fail(PF_ERR_ARG, "empty grid (nx=%d, ny=%d)", nx, ny);
-    if (nx > MAX_SIDE || ny > MAX_SIDE)
-        return fail(PF_ERR_ARG, "grid side above %d (nx=%d, ny=%d)", MAX_SIDE, nx, ny);
-    if (pitch < nx || pitch % 4 != 0)
-        return fail(PF_ERR_LAYOUT, "pitch %d must be >= nx=%d and a multiple of 4", pitch, nx);
-    return PF_OK;
 }
 
 int check_params(const pf_params* p)
@@ -235,7 +247,7 @@ const char* pf_strerror(int code)
     }
 }
 
-const char* pf_last_error(void) { return g_last_error.c_str(); }
+const char* pf_last_error(void) { return pf::last_error_text(); }
 
 int pf_dt_limit(const pf_params* p, double out[4])
 {

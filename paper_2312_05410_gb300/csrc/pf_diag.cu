@@ -17,7 +17,6 @@ namespace pf {
 namespace {
 
 constexpr int DIAG_THREADS = 256;
-constexpr int DIAG_MAX_BLOCKS = 1216;  // 8 x 152 SMs
 
 __device__ __forceinline__ double warp_sum(double v)
 {

@@ -74,7 +74,9 @@ size_t step_smem_bytes(int tile);
 cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,
                          const float* rho0, float* phi1, float* c1, float* rho1, cudaStream_t s);
 
-// Diagnostics: per-block FP64 partials then a fixed-order final reduction.
+// Diagnostics: per-block FP64 partials then a fixed-order final reduction over at
+// most DIAG_MAX_BLOCKS blocks (8 per SM on 152 SMs).
+constexpr int DIAG_MAX_BLOCKS = 1216;
 struct DiagConst {
     int nx, ny, pitch;
     float Wc, Wf;
@@ -96,5 +98,11 @@ void velocity_of(const pf_params& p, double* vx, double* vy);
 StepConst step_const_of(const pf_params& p, int nx, int ny, int pitch);
 DiagConst diag_const_of(const pf_params& p, int nx, int ny, int pitch);
 int mob_kind_of(const pf_params& p);
+
+// Error reporting and size checks of the C-ABI layer (pf_api.cu): fail() records the
+// thread-local text that pf_last_error() returns and passes the code through.
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+int check_sizes(int nx, int ny, int pitch);
 
 }  // namespace pf

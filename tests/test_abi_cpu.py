@@ -99,6 +99,23 @@ def test_diagnostics_error_paths(pf):
     assert pf.pf_diagnostics(p, 64, 64, 64, FAKE, FAKE, FAKE, FAKE + 8, need, FAKE, 0) == pf.PF_ERR_LAYOUT
 
 
+def test_static_diagnostics_error_paths_report_their_reason(pf):
+    """The allocation-free diagnostics reject bad arguments before any CUDA call, through the same
+    checks and error text as the workspace entry point."""
+    p = I.default_params()
+    cases = [
+        ((p, 64, 64, 64, FAKE, FAKE, 0, FAKE, None, 0), pf.PF_ERR_ARG, "null pointer"),
+        ((p, 0, 64, 64, FAKE, FAKE, FAKE, FAKE, None, 0), pf.PF_ERR_ARG, "empty grid"),
+        ((p, (1 << 20) + 4, 8, (1 << 20) + 4, FAKE, FAKE, FAKE, FAKE, None, 0), pf.PF_ERR_ARG, "grid side above"),
+        ((p, 40, 8, 42, FAKE, FAKE, FAKE, FAKE, None, 0), pf.PF_ERR_LAYOUT, "pitch"),
+        ((p, 40, 8, 40, FAKE, FAKE, FAKE, FAKE + 4, None, 0), pf.PF_ERR_LAYOUT, "8-byte aligned"),
+        ((dict(p, dx=0.0), 40, 8, 40, FAKE, FAKE, FAKE, FAKE, None, 0), pf.PF_ERR_ARG, "dx"),
+    ]
+    for args, code, text in cases:
+        assert pf.pf_diagnostics_static(*args) == code, text
+        assert text in pf.last_error(), (text, pf.last_error())
+
+
 def _ens_init(pf, plist, shapes, work_bytes=None, ptr=FAKE):
     import ctypes as C
 

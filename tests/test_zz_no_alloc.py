@@ -67,7 +67,7 @@ def _static(pf, p, nx, ny, pitch, ts, stream):
     return out.cpu().numpy(), int(err.item())
 
 
-@pytest.mark.parametrize("nx,ny", [(512, 512), (37, 23)])
+@pytest.mark.parametrize("nx,ny", [(512, 512), (37, 23), (2048, 1024)])
 def test_static_scratch_matches_workspace_entry_point(pf, nx, ny):
     import torch
 
@@ -78,6 +78,17 @@ def test_static_scratch_matches_workspace_entry_point(pf, nx, ny):
         got, err = _static(pf, p, nx, ny, pitch, ts, stream)
         np.testing.assert_allclose(got, ref, rtol=1e-12)
         assert err == 0
+
+
+def test_static_scratch_capacity_is_the_reduction_block_cap(pf):
+    """The static array holds the partials of the most reduction blocks any accepted grid uses
+    (1216, documented in pf.h): the workspace entry point's size stops growing there, and
+    2048 x 1024 (run above) already reaches it."""
+    cap = 1216
+    full = (4 * 8 * cap + 255) // 256 * 256 + 256
+    assert pf.pf_diag_workspace_size(2048, 1024) == full
+    assert pf.pf_diag_workspace_size(1 << 20, 1 << 20) == full
+    assert pf.pf_diag_workspace_size(1024, 1024) < full
 
 
 def test_static_scratch_error_word_is_cleared_between_calls(pf):
@@ -101,3 +112,6 @@ def test_static_entry_point_rejects_bad_sizes(pf):
         == pf.PF_ERR_ARG
     assert pf.pf_diagnostics_static(p, 40, 8, 42, fake, fake, fake, fake, None, 0) == pf.PF_ERR_LAYOUT
     assert pf.pf_diagnostics_static(p, 40, 8, 40, fake, fake, fake, fake + 4, None, 0) == pf.PF_ERR_LAYOUT
+    assert "8-byte aligned" in pf.last_error()
+    assert pf.pf_diagnostics_static(p, 40, 8, 42, fake, fake, fake, fake, None, 0) == pf.PF_ERR_LAYOUT
+    assert "pitch" in pf.last_error()
