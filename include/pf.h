@@ -298,14 +298,17 @@ int pf_conv_halo(int on);
 /*
  * The time-conditioned U-Net surrogate and its jump ("U-Net with temporal
  * conditioning", Methods; the hybrid solver of Results alternates DNS stretches
- * with such jumps).  For each of `batch` runs it maps (phi, c) at time t to a
- * prediction at t + dt.  Structure:
- *   - input planes (phi, c, rho, tau), with tau = dt / dt_ref;
+ * with such jumps).  For each of `batch` runs it maps the state at time t, with
+ * look-back frames before t, to a prediction at t + dt.  Structure:
+ *   - input planes: lb = 3 frames of (phi, c, rho), oldest first (the paper's
+ *     operator reads lb = 3 consecutive frames of its field), then tau = dt / dt_ref;
+ *     the two older frames are the ones pushed with pf_unet_frame, the newest is
+ *     the fields being advanced;
  *   - encoder z1 = block(x), zp = block(down(z_{p-1})), with block = GELU(GN(conv3x3));
  *   - conditioning zc_p = z_p * (W_p f(tau)), where f is the sin MLP;
  *   - decoder d3 = up(block(zc4)), d2 = up(block(zc3 ++ d3)), d1 = up(block(zc2 ++ d2));
  *   - output (phi, c, rho) += gamma * conv3x3(block(zc1 ++ d1)) + beta, a
- *     per-channel affine increment of the input fields.  The paper predicts its one
+ *     per-channel affine increment of the newest frame.  The paper predicts its one
  *     normalised composition field and applies a final group normalisation.  Here:
  *     - the state is the three coupled fields, whose per-sample mean and spread vary
  *       with film thickness and incident composition, so the increment form is used;
@@ -326,7 +329,8 @@ int pf_conv_halo(int on);
  * pf_unet_init: weights = 40 host FP32 arrays, in PyTorch layouts and this order:
  *   0-5   mlp_w0 [128][1], mlp_b0 [128], mlp_w1 [128][128], mlp_b1, mlp_w2 [128][128], mlp_b2
  *   6-9   proj1..proj4 [C_p][128] (C = 32, 64, 128, 256)
- *   10-13 enc1 [32][4][3][3], enc2 [64][32][3][3], enc3 [128][64][3][3], enc4 [256][128][3][3]
+ *   10-13 enc1 [32][10][3][3], enc2 [64][32][3][3], enc3 [128][64][3][3], enc4 [256][128][3][3]
+ *         (enc1's input planes: frames oldest first, (phi, c, rho) each, then tau)
  *   14-17 dec4 [256][256][3][3], dec3 [128][256][3][3], dec2 [64][128][3][3], dec1 [32][64][3][3]
  *   18-20 up4 [256][128][2][2], up3 [128][64][2][2], up2 [64][32][2][2]  ([Cin][Cout][dy][dx])
  *   21    out [3][32][3][3]
@@ -335,10 +339,17 @@ int pf_conv_halo(int on);
  *   projections are kept in FP64 and the affine parameters in FP32.  Everything is
  *   copied into the workspace (synchronises once).
  *   work: 256-byte aligned.
+ * pf_unet_frame: push the current fields of every run (same arguments as the jump's)
+ *   as the newest look-back frame, rounded to BF16 into the workspace; the handle keeps
+ *   the two newest pushed frames.  One kernel launch, asynchronous.
+ * pf_unet_reset_frames: forget the pushed frames (host only).  A jump made with fewer
+ *   than two frames held takes the oldest frame held, or the current fields when none
+ *   is, in place of the missing ones.
  * pf_unet_jump: advances (phi[i], c[i], rho[i]) of runs i < n (n == batch; device
  *   FP32 fields ny x nx with row pitch `pitch` floats) in place by the predicted
- *   increments for jump length tau.  Asynchronous on the handle's stream, 28
- *   kernel launches (29 when tau differs from the previous jump's: the MLP basis).
+ *   increments for jump length tau, the pushed frames being its look-back.
+ *   Asynchronous on the handle's stream, 28 kernel launches (29 when tau differs
+ *   from the previous jump's: the MLP basis).  The pushed frames are kept.
  * pf_unet_sync: synchronise; PF_ERR_TIMEOUT if a tensor-core pipeline wait ran out.
  * pf_unet_check: plausibility of the last jump's prediction, the hybrid solver's
  *   gate for its plain-DNS fallback.  ok[i] (host, n ints) is 1 if every phi, c and
@@ -351,6 +362,9 @@ typedef struct pf_unet pf_unet;
 size_t pf_unet_workspace_size(int batch, int nx, int ny);
 int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, int ny, void* work, size_t work_bytes,
                  void* stream, pf_unet** out);
+int pf_unet_frame(pf_unet* u, int n, const float* const* phi, const float* const* c, const float* const* rho,
+                  int pitch);
+int pf_unet_reset_frames(pf_unet* u);
 int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau);
 int pf_unet_sync(pf_unet* u);
 int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double c_hi, double rho_lo, double rho_hi,
@@ -358,6 +372,39 @@ int pf_unet_check(pf_unet* u, double phi_lo, double phi_hi, double c_lo, double 
 int pf_unet_buffer(const pf_unet* u, int which, void** ptr, int* channels);
 int pf_unet_destroy(pf_unet* u);
 const char* pf_unet_last_error(void);
+
+/*
+ * The hybrid DNS / U-Net solver ("Hybrid" in Results: stretches of direct
+ * simulation alternate with leaps of the neural operator over the time the DNS
+ * would have taken).  Every run of ensemble `e` must have the U-Net's grid
+ * (batch = number of runs, one row pitch for all), and both handles must use the
+ * same stream.  pf_hybrid_run advances every run `total_steps` steps by cycles of
+ *   1. `dns_stretch` DNS steps (pf_ens_step), pushing the state as a look-back frame
+ *      (pf_unet_frame) 2 frame_every and frame_every steps before the stretch ends;
+ *   2. a backup of every run's state, then one jump (pf_unet_jump) standing for
+ *      `jump_steps` steps, with tau = jump_steps / dt_ref_steps;
+ *   3. the plausibility gate (pf_unet_check with the given ranges; synchronises):
+ *      if any run fails, every run is restored and the jumped steps are run by DNS.
+ * The steps left after the last whole cycle are run by DNS.  stats receives the
+ * jumps kept, the fallbacks and the DNS steps taken.  work: caller-owned device
+ * scratch of pf_hybrid_workspace_size(e) bytes (the backup), 256-byte aligned.
+ * Returns PF_OK or a PF_ERR_* code, with the text in pf_hybrid_last_error();
+ * PF_ERR_TIMEOUT if a tensor-core pipeline wait of a jump ran out.
+ */
+typedef struct pf_hybrid_params {
+    long dns_stretch;     /* DNS steps before each jump, >= 2 frame_every */
+    long jump_steps;      /* steps one jump stands for */
+    long frame_every;     /* steps between the look-back frames */
+    double dt_ref_steps;  /* the network's time unit in steps */
+    double phi_lo, phi_hi, c_lo, c_hi, rho_lo, rho_hi;  /* plausible ranges of a prediction */
+} pf_hybrid_params;
+typedef struct pf_hybrid_stats {
+    long jumps, fallbacks, dns_steps;
+} pf_hybrid_stats;
+size_t pf_hybrid_workspace_size(const pf_ens* e);
+int pf_hybrid_run(pf_ens* e, pf_unet* u, const pf_hybrid_params* hp, long total_steps, void* work, size_t work_bytes,
+                  pf_hybrid_stats* stats);
+const char* pf_hybrid_last_error(void);
 
 /*
  * Two-point autocorrelation of the solid A phase ("Autocorrelations", Results; the

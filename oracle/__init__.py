@@ -21,6 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pf_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")  # the same loops over all host cores
 _lock = threading.Lock()
 _lib = None
 
@@ -33,14 +34,46 @@ class OrcParams(C.Structure):
         ("phi_mode", C.c_int), ("deposition", C.c_int), ("diag_every", C.c_int)]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (plain -O2, single thread)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle: plain -O2, single thread (the checker); with openmp=True the same source
+    with -fopenmp into a second library (the all-cores CPU baseline)."""
+    out = _LIB_OMP if openmp else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def _bind(L):
+    dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+    P = C.POINTER(OrcParams)
+    L.orc_step.argtypes = [P, C.c_int, C.c_int, dp, dp, dp, C.c_long]
+    L.orc_step.restype = C.c_int
+    return L
+
+
+_lib_omp = None
+
+
+def lib_omp():
+    """The -fopenmp build (CPU baseline only: the checker is lib())."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            _lib_omp = _bind(C.CDLL(build(openmp=True)))
+    return _lib_omp
+
+
+def step_all_cores(pd, phi, c, rho, nsteps: int):
+    """O.step through the OpenMP build (identical results, rows split over the host's cores)."""
+    phi, c, rho = _f64(phi).copy(), _f64(c).copy(), _f64(rho).copy()
+    ny, nx = phi.shape
+    rc = lib_omp().orc_step(C.byref(params(pd)), nx, ny, phi, c, rho, int(nsteps))
+    assert rc == 0
+    return phi, c, rho
 
 
 def lib():

@@ -5,6 +5,11 @@
  * benchmark's CPU-baseline leg may load this library.  It shares no code,
  * header or constant with the CUDA path.
  *
+ * The checker is this file built without OpenMP (single thread).  Built with
+ * -fopenmp (the CPU baseline over all host cores), the per-cell loops split their
+ * rows over threads; every cell is computed by the same expressions either way,
+ * so both builds give identical results.
+ *
  * What it follows (all in "Materials and Methods", subsection "Phase-field
  * modeling of physical vapor deposition", and "Dataset"):
  *   [CH-c]   dc/dt   = div( M_c(phi,c) grad dF/dc )            composition
@@ -120,6 +125,7 @@ int orc_chem_pot(const orc_params* P, int nx, int ny, const double* phi, const d
     if (!pp || !cp) { free(pp); free(cp); return -2; }
     pad_field(nx, ny, phi, pp, 0, 0.0);
     pad_field(nx, ny, c, cp, 0, 0.0);
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double f = phi[IDX(j, i)], cc = c[IDX(j, i)];
@@ -166,6 +172,7 @@ int orc_rhs(const orc_params* P, int nx, int ny, const double* phi, const double
         return -2;
     }
     orc_chem_pot(P, nx, ny, phi, c, mu_c, mu_f);
+#pragma omp parallel for
     for (size_t k = 0; k < n; ++k) Mc[k] = orc_mobility(P, phi[k], c[k]);
 
     /* ghosts of the computed chemical potentials and mobility (mirror in y) */
@@ -175,6 +182,7 @@ int orc_rhs(const orc_params* P, int nx, int ny, const double* phi, const double
     pad_field(nx, ny, phi, pp, 0, 0.0);
     pad_field(nx, ny, rho, rp, 1, P->rho_top);
 
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             const size_t k = IDX(j, i);
@@ -223,12 +231,14 @@ int orc_step(const orc_params* P, int nx, int ny, double* phi, double* c, double
     const double dt = P->dt;
     for (long s = 0; s < nsteps; ++s) {
         orc_rhs(P, nx, ny, phi, c, rho, Rf, Rc, Rr);
+#pragma omp parallel for
         for (size_t k = 0; k < n; ++k) {
             fs[k] = phi[k] + 0.5 * dt * Rf[k];
             cs[k] = c[k] + 0.5 * dt * Rc[k];
             rs[k] = rho[k] + 0.5 * dt * Rr[k];
         }
         orc_rhs(P, nx, ny, fs, cs, rs, Rf2, Rc2, Rr2);
+#pragma omp parallel for
         for (size_t k = 0; k < n; ++k) {
             phi[k] += dt * Rf2[k];
             c[k] += dt * Rc2[k];

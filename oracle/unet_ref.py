@@ -25,11 +25,16 @@ the paper is silent are marked READING):
              thickness and the incident composition, which a final normalisation would pin, so the
              last convolution instead gives a per-channel affine increment added to the input fields)
 
-Channels 32-64-128-256.  Input x = (phi, c, rho, dt / dt_ref) planes and output the
-increments of (phi, c, rho) (READING: the paper feeds lb = 3 frames of its one field c;
-here the state is the three coupled fields, and the vapor density is predicted too:
-resetting it instead costs 12.6 % relative L2 in phi after 25 exact jumps), plus a plane
-holding the jump length.
+Channels 32-64-128-256.  Input x = lb = 3 look-back frames of the state (phi, c, rho),
+oldest first, then a plane holding the jump length dt / dt_ref; output y = the newest
+frame plus the predicted increments of (phi, c, rho).  The paper's operator reads lb
+consecutive frames [c(t - lb + 1), ..., c(t)] of its single field and its look-back
+study finds lb = 1 markedly worse (the process is non-Markovian in that field).
+READING: here the state is the three coupled fields, so every frame carries all three
+(9 planes), and the vapor density is predicted too (resetting it instead costs 12.6 %
+relative L2 in phi after 25 exact jumps).  The frames are 1000 steps apart and the
+jump is 2000 steps: the two older frames are the start and the middle of the DNS
+stretch that precedes a jump.
 
 Weights come from ``paper_2312_05410_gb300.inputs.unet_weights`` (seeded numbers,
 no arithmetic of the method).
@@ -54,7 +59,8 @@ CH = (32, 64, 128, 256)
 GROUPS = 8
 EPS = 1e-5
 FDIM = 128       # width of the MLP's hidden layers and of the basis f(dt)
-IN_CH, OUT_CH = 4, 3
+LB = 3                   # look-back frames
+IN_CH, OUT_CH = 3 * LB + 1, 3
 
 
 def bf16(a) -> np.ndarray:
@@ -136,9 +142,11 @@ def up(x: torch.Tensor, w) -> torch.Tensor:
 
 
 def forward(W: dict, x, tau: float, taps: dict | None = None) -> np.ndarray:
-    """Network output for x [N, 4, H, W] (float array; rounded to BF16 here); returns [N, 3, H, W] FP64.
+    """Network output for x [N, 10, H, W] (3 frames of phi, c, rho, oldest first, then the dt plane;
+    rounded to BF16 here); returns [N, 3, H, W] FP64: the newest frame plus the increments.
     If `taps` is a dict it receives the intermediate tensors by name."""
-    x_fields = _t(np.asarray(x, dtype=np.float32)[:, :OUT_CH])  # the residual adds the FP32 input fields
+    newest = 3 * (LB - 1)
+    x_fields = _t(np.asarray(x, dtype=np.float32)[:, newest:newest + OUT_CH])  # the residual adds the newest frame
     x = _rb(_t(x))
     s = [_t(bf16(v)) for v in scales(W, tau)]     # conditioning factors are stored as BF16
     z1 = block(x, W, "enc1")

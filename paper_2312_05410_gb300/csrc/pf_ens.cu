@@ -157,6 +157,25 @@ constexpr long ENS_GRAPH_STEPS = 100;  // even: a replay starts and ends in the 
 
 }  // namespace
 
+namespace pf {
+
+int ens_runs(const pf_ens* e) { return e ? e->nruns : 0; }
+
+void ens_run_fields(const pf_ens* e, int run, float** phi, float** c, float** rho, int* nx, int* ny, int* pitch)
+{
+    const EnsRun& r = e->host_runs[run];
+    *phi = r.f[0][0];
+    *c = r.f[0][1];
+    *rho = r.f[0][2];
+    *nx = e->nx[run];
+    *ny = e->ny[run];
+    *pitch = e->pitch[run];
+}
+
+cudaStream_t ens_stream(const pf_ens* e) { return e->stream; }
+
+}  // namespace pf
+
 extern "C" {
 
 size_t pf_ens_workspace_size(int nruns, const int* nx, const int* ny, const int* pitch)

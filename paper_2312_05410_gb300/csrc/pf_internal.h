@@ -105,4 +105,12 @@ int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 int check_sizes(int nx, int ny, int pitch);
 
+// Accessors used by the hybrid driver (pf_hybrid.cu): the run fields of an ensemble
+// (pf_ens.cu) and the shape and stream of a U-Net handle (pf_unet_api.cu).
+int ens_runs(const pf_ens* e);
+void ens_run_fields(const pf_ens* e, int run, float** phi, float** c, float** rho, int* nx, int* ny, int* pitch);
+cudaStream_t ens_stream(const pf_ens* e);
+void unet_shape(const pf_unet* u, int* batch, int* nx, int* ny);
+cudaStream_t unet_stream(const pf_unet* u);
+
 }  // namespace pf

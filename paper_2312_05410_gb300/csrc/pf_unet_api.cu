@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "pf.h"
+#include "pf_internal.h"
 #include "pf_unet_internal.h"
 #include "pf_unet_net.h"
 
@@ -76,6 +77,7 @@ int conv_common(int mode, const void* in, int n, int h, int w, int cin, const vo
 namespace {
 
 constexpr int NW = 40;  // weight arrays, in the order documented in pf.h
+static_assert(pf::UNET_LB == 3, "the look-back ring holds two frames (slots 0 and 1)");
 const int CH[4] = {32, 64, 128, 256};
 
 // host BF16 rounding (nearest, ties to even) from the format definition
@@ -100,7 +102,7 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 struct UnetLayout {
     size_t mlp, proj, win, wout, wc[7], wt[3], gb[9][2];
     size_t act[16];  // see ACT_* below
-    size_t partials, stats, scales, err, ptrs, flags, total;
+    size_t partials, stats, scales, err, ptrs, flags, ring, fptrs, total;
 };
 enum { A_PRE1, A_CAT1, A_P1, A_PRE2, A_CAT2, A_P2, A_PRE3, A_CAT3, A_P3, A_PRE4, A_ZC4, A_H4, A_H3, A_H2, A_H1, A_PREO };
 
@@ -124,7 +126,7 @@ UnetLayout unet_layout(int n, int h, int w)
     };
     L.mlp = take(sizeof(double) * (3 * 128 + 2 * 128 * 128 + 128));
     L.proj = take(sizeof(double) * 480 * 128);
-    L.win = take(sizeof(float) * 36 * 32);
+    L.win = take(sizeof(float) * 9 * pf::UNET_IN * 32);
     L.wout = take(2 * 9 * 16 * 32);  // output conv as one 16-column tensor-core tile: [tap][16][32] BF16, rows 3.. zero
     const int conv_io[7][2] = {{32, 64}, {64, 128}, {128, 256}, {256, 256}, {256, 128}, {128, 64}, {64, 32}};
     for (int k = 0; k < 7; ++k) L.wc[k] = take(2 * 9 * (size_t)conv_io[k][0] * conv_io[k][1]);
@@ -143,6 +145,8 @@ UnetLayout unet_layout(int n, int h, int w)
     L.err = take(sizeof(int));
     L.ptrs = take(sizeof(float*) * 3 * (size_t)n);
     L.flags = take(sizeof(int) * (size_t)n);
+    L.ring = take(2 * (size_t)(pf::UNET_LB - 1) * n * 3 * h * w);  // look-back frames, BF16 [slot][n][3][h][w]
+    L.fptrs = take(sizeof(float*) * 3 * (size_t)n);
     L.total = off;
     return L;
 }
@@ -158,9 +162,25 @@ struct pf_unet {
     double cond_tau;           // jump length the stored conditioning factors belong to
     int last_pitch;            // row pitch of the fields of the last jump
     bool cond_valid;
+    int frames;                // look-back frames held (0 .. UNET_LB - 1)
+    int newest;                // ring slot of the newest frame
+    std::vector<const float*> fptrs;  // host copy of the pointer table of the last pushed frame
     template <class T>
     T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
 };
+
+namespace pf {
+
+void unet_shape(const pf_unet* u, int* batch, int* nx, int* ny)
+{
+    *batch = u->n;
+    *nx = u->w;
+    *ny = u->h;
+}
+
+cudaStream_t unet_stream(const pf_unet* u) { return u->stream; }
+
+}  // namespace pf
 
 namespace {
 
@@ -251,6 +271,9 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     u->cond_valid = false;
     u->last_pitch = nx;
     u->cond_tau = 0.0;
+    u->frames = 0;
+    u->newest = 0;
+    u->fptrs.assign(3 * (size_t)batch, nullptr);
     // ---- host-side conversion into the device layouts (once)
     std::vector<double> mlp;
     for (int k = 0; k < 6; ++k) {
@@ -259,11 +282,12 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     }
     std::vector<double> proj;
     for (int p = 0; p < 4; ++p) proj.insert(proj.end(), weights[6 + p], weights[6 + p] + (size_t)CH[p] * 128);
-    // first conv [32][4][3][3] -> [(ky,kx,ci)][co], BF16 values
-    std::vector<float> win(36 * 32);
+    // first conv [32][UNET_IN][3][3] -> [(ky,kx,ci)][co], BF16 values
+    constexpr int CI = pf::UNET_IN;
+    std::vector<float> win(9 * CI * 32);
     for (int co = 0; co < 32; ++co)
-        for (int ci = 0; ci < 4; ++ci)
-            for (int t = 0; t < 9; ++t) win[(t * 4 + ci) * 32 + co] = host_rbf(weights[10][((co * 4 + ci) * 9) + t]);
+        for (int ci = 0; ci < CI; ++ci)
+            for (int t = 0; t < 9; ++t) win[(t * CI + ci) * 32 + co] = host_rbf(weights[10][((co * CI + ci) * 9) + t]);
     // last conv [3][32][3][3] -> [tap][16][32] BF16 (output columns 3..15 zero)
     std::vector<uint16_t> wout(9 * 16 * 32, 0);
     for (int co = 0; co < 3; ++co)
@@ -354,7 +378,14 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
         u->cond_tau = tau;
     }
     // ---- encoder
-    ck(pf::launch_in_conv(dp, dp + n, dp + 2 * n, pitch, n, H, W, (float)tau, u->at<float>(L.win), act(A_PRE1), part, s),
+    // look-back frames: the oldest and the middle one (a missing frame is the oldest one held, or the
+    // current fields when none is)
+    const size_t frame_elems = (size_t)n * 3 * H * W;
+    const uint16_t* ring = u->at<uint16_t>(L.ring);
+    const uint16_t* newest = u->frames > 0 ? ring + (size_t)u->newest * frame_elems : nullptr;
+    const uint16_t* older = u->frames > 1 ? ring + (size_t)(1 - u->newest) * frame_elems : newest;
+    ck(pf::launch_in_conv(dp, dp + n, dp + 2 * n, pitch, older, newest, n, H, W, (float)tau, u->at<float>(L.win),
+                          act(A_PRE1), part, s),
        "input conv");
     ck(pf::launch_gn_stats(part, n, G, H * W / 128, 4.0 * H * W, 32, gam(0), bet(0), stats, s), "statistics");
     ck(pf::launch_gn_enc(act(A_PRE1), n, H, W, 32, stats, sc, act(A_CAT1), 64, act(A_P1), s), "level 1");
@@ -401,6 +432,40 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
         ck(pf::launch_umma_conv(pf::OUT3, act(A_H1), u->at<uint16_t>(L.wout), a, s), "output");
     }
     return rc;
+}
+
+int pf_unet_frame(pf_unet* u, int n, const float* const* phi, const float* const* c, const float* const* rho,
+                  int pitch)
+{
+    if (!u || !phi || !c || !rho) return ufail(PF_ERR_ARG, "null pointer");
+    if (n != u->n) return ufail(PF_ERR_ARG, "batch %d, the handle was built for %d", n, u->n);
+    if (pitch < u->w) return ufail(PF_ERR_LAYOUT, "pitch %d < nx %d", pitch, u->w);
+    for (int i = 0; i < n; ++i) {
+        if (!phi[i] || !c[i] || !rho[i]) return ufail(PF_ERR_ARG, "run %d: null field", i);
+        u->fptrs[i] = phi[i];
+        u->fptrs[n + i] = c[i];
+        u->fptrs[2 * n + i] = rho[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(u->base + u->L.fptrs, u->fptrs.data(), sizeof(float*) * 3 * n,
+                                    cudaMemcpyHostToDevice, u->stream);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "frame pointer table: %s", cudaGetErrorString(e));
+    const float** dp = u->at<const float*>(u->L.fptrs);
+    const int slot = u->frames == 0 ? 0 : 1 - u->newest;  // overwrite the oldest frame held
+    const size_t frame_elems = (size_t)n * 3 * u->h * u->w;
+    e = pf::launch_frame(dp, dp + n, dp + 2 * n, pitch, n, u->h, u->w,
+                         u->at<uint16_t>(u->L.ring) + (size_t)slot * frame_elems, u->stream);
+    if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "frame: %s", cudaGetErrorString(e));
+    u->newest = slot;
+    if (u->frames < pf::UNET_LB - 1) ++u->frames;
+    return PF_OK;
+}
+
+int pf_unet_reset_frames(pf_unet* u)
+{
+    if (!u) return ufail(PF_ERR_ARG, "null handle");
+    u->frames = 0;
+    u->newest = 0;
+    return PF_OK;
 }
 
 int pf_unet_sync(pf_unet* u)

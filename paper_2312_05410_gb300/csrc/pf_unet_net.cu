@@ -97,22 +97,27 @@ __device__ __forceinline__ void unpack8(const uint4 v, float* f)
     }
 }
 
-// First convolution: x = BF16(phi, c, rho, tau) with zero padding outside the image, 3x3, 4 -> 32.
+// First convolution over the look-back input, 3x3, 10 -> 32, zero padding outside the image:
+// x = BF16 of (phi, c, rho) of the oldest frame, of the middle frame, of the current fields, then
+// the tau plane.  The two older frames are BF16 planes [image][3][h][w] (old0, old1; either may be
+// NULL: that frame is the current fields, the history of a run that has none yet).
 // A block covers two consecutive 128-pixel tiles of one image; thread t computes pixel t of each
 // (neighbours come through L1: staging the halo in shared memory measured slower).  The 32 outputs
-// are 16 pairs updated by packed FP32x2 FMAs (each half runs the scalar chain unchanged), and each
-// weight pair read from shared memory serves both pixels.  Group sums: one scatter-halving per warp
-// and tile.
+// are 16 pairs updated by packed FP32x2 FMAs, and each weight pair read from shared memory serves
+// both pixels.  Group sums: one scatter-halving per warp and tile.
+constexpr int IN_CH = UNET_IN;
+static_assert(IN_CH == 10, "three frames of (phi, c, rho) and the tau plane");
 __global__ void __launch_bounds__(TPB)
 in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
-               const float* const* __restrict__ rho, int pitch, int h, int w, float tau,
-               const float* __restrict__ wgt /* [36][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
+               const float* const* __restrict__ rho, int pitch, const uint16_t* __restrict__ old0,
+               const uint16_t* __restrict__ old1, int h, int w, float tau,
+               const float* __restrict__ wgt /* [9 * IN_CH][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
                float* __restrict__ partials)
 {
-    __shared__ __align__(16) float ws[36 * 32];
+    __shared__ __align__(16) float ws[9 * IN_CH * 32];
     __shared__ float red[2][4][16];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = threadIdx.x; i < 36 * 32; i += TPB) ws[i] = wgt[i];
+    for (int i = threadIdx.x; i < 9 * IN_CH * 32; i += TPB) ws[i] = wgt[i];
     __syncthreads();
     const int tpi = h * w / TPB, bpi = (tpi + 1) / 2;  // tiles and blocks per image
     const int img = blockIdx.x / bpi, t0 = 2 * (blockIdx.x % bpi);
@@ -120,6 +125,9 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     const float* F = phi[img];
     const float* C = c[img];
     const float* Rh = rho[img];
+    const size_t plane = (size_t)h * w;
+    const uint16_t* O0 = old0 ? old0 + (size_t)img * 3 * plane : nullptr;
+    const uint16_t* O1 = old1 ? old1 + (size_t)img * 3 * plane : nullptr;
     const float tb = rbf(tau);
     int y[2], x[2];
 #pragma unroll
@@ -128,7 +136,6 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
         y[k] = p / w;
         x[k] = p % w;
     }
-    const float2* ws2 = reinterpret_cast<const float2*>(ws);
     float2 acc[2][16];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -136,36 +143,36 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
         for (int o = 0; o < 16; ++o) acc[k][o] = make_float2(0.f, 0.f);
     for (int ky = 0; ky < 3; ++ky)
         for (int kx = 0; kx < 3; ++kx) {
-            float2 b[2][4];
+            float v[2][IN_CH];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int yy = y[k] + ky - 1, xx = x[k] + kx - 1;
                 const bool in = (k == 0 || two) && yy >= 0 && yy < h && xx >= 0 && xx < w;
                 const size_t o = in ? (size_t)yy * pitch + xx : 0;
-                const float v0 = in ? rbf(F[o]) : 0.f, v1 = in ? rbf(C[o]) : 0.f;
-                const float v2 = in ? rbf(Rh[o]) : 0.f, v3 = in ? tb : 0.f;
-                b[k][0] = make_float2(v0, v0);
-                b[k][1] = make_float2(v1, v1);
-                b[k][2] = make_float2(v2, v2);
-                b[k][3] = make_float2(v3, v3);
+                const size_t ob = in ? (size_t)yy * w + xx : 0;
+                const float f0 = in ? rbf(F[o]) : 0.f, f1 = in ? rbf(C[o]) : 0.f, f2 = in ? rbf(Rh[o]) : 0.f;
+                v[k][6] = f0;
+                v[k][7] = f1;
+                v[k][8] = f2;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    v[k][q] = in ? (O0 ? bf(O0[q * plane + ob]) : v[k][6 + q]) : 0.f;
+                    v[k][3 + q] = in ? (O1 ? bf(O1[q * plane + ob]) : v[k][6 + q]) : 0.f;
+                }
+                v[k][9] = in ? tb : 0.f;
             }
-            const float4* wk = reinterpret_cast<const float4*>(ws2 + (ky * 3 + kx) * 4 * 16);
+            const float4* wk = reinterpret_cast<const float4*>(ws + (ky * 3 + kx) * IN_CH * 32);
 #pragma unroll
-            for (int q2 = 0; q2 < 8; ++q2) {  // two output pairs per 16-byte weight load
-                float4 wv[4];
+            for (int ci = 0; ci < IN_CH; ++ci) {
+                const float2 b0 = make_float2(v[0][ci], v[0][ci]), b1 = make_float2(v[1][ci], v[1][ci]);
 #pragma unroll
-                for (int ci = 0; ci < 4; ++ci) wv[ci] = wk[ci * 8 + q2];
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int q = 2 * q2 + h2;
-                    float2 wc[4];
-#pragma unroll
-                    for (int ci = 0; ci < 4; ++ci)
-                        wc[ci] = h2 ? make_float2(wv[ci].z, wv[ci].w) : make_float2(wv[ci].x, wv[ci].y);
-#pragma unroll
-                    for (int k = 0; k < 2; ++k)
-                        acc[k][q] = __ffma2_rn(b[k][0], wc[0], __ffma2_rn(b[k][1], wc[1],
-                                               __ffma2_rn(b[k][2], wc[2], __ffma2_rn(b[k][3], wc[3], acc[k][q]))));
+                for (int q2 = 0; q2 < 8; ++q2) {  // two output pairs per 16-byte weight load
+                    const float4 wv = wk[ci * 8 + q2];
+                    const float2 wa = make_float2(wv.x, wv.y), wb = make_float2(wv.z, wv.w);
+                    acc[0][2 * q2] = __ffma2_rn(b0, wa, acc[0][2 * q2]);
+                    acc[0][2 * q2 + 1] = __ffma2_rn(b0, wb, acc[0][2 * q2 + 1]);
+                    acc[1][2 * q2] = __ffma2_rn(b1, wa, acc[1][2 * q2]);
+                    acc[1][2 * q2 + 1] = __ffma2_rn(b1, wb, acc[1][2 * q2 + 1]);
                 }
             }
         }
@@ -200,6 +207,24 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
         }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// One look-back frame: the FP32 fields (row pitch `pitch`) of every image rounded to BF16 planes
+// [image][3][h][w] (the rounding the first convolution applies to its inputs).
+__global__ void frame_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
+                             const float* const* __restrict__ rho, int pitch, int n, int h, int w,
+                             uint16_t* __restrict__ dst)
+{
+    const size_t plane = (size_t)h * w, total = (size_t)n * 3 * plane;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int img = (int)(i / (3 * plane));
+        const size_t r = i - (size_t)img * 3 * plane;
+        const int q = (int)(r / plane);
+        const size_t pix = r - (size_t)q * plane;
+        const int yy = (int)(pix / w), xx = (int)(pix - (size_t)yy * w);
+        const float* src = q == 0 ? phi[img] : (q == 1 ? c[img] : rho[img]);
+        dst[i] = to_bf(src[(size_t)yy * pitch + xx]);
+    }
 }
 
 // Group statistics -> per-channel affine of the normalisation: block (image, group) sums its
@@ -406,12 +431,22 @@ cudaError_t launch_cond(const double* mlp, const double* proj, double tau, float
     return cudaLaunchKernelEx(&cfg, cond_kernel, mlp, proj, tau, scales, nscales);
 }
 
-cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const float* const* rho, int pitch, int n,
-                           int h, int w, float tau, const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
+cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const float* const* rho, int pitch,
+                           const uint16_t* old0, const uint16_t* old1, int n, int h, int w, float tau,
+                           const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cfg_of(dim3((unsigned)(n * ((h * w / TPB + 1) / 2))), TPB, s, attr);
-    return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, rho, pitch, h, w, tau, wgt, out, partials);
+    return cudaLaunchKernelEx(&cfg, in_conv_kernel, phi, c, rho, pitch, old0, old1, h, w, tau, wgt, out, partials);
+}
+
+cudaError_t launch_frame(const float* const* phi, const float* const* c, const float* const* rho, int pitch, int n,
+                         int h, int w, uint16_t* dst, cudaStream_t s)
+{
+    const size_t total = (size_t)n * 3 * h * w;
+    const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    frame_kernel<<<blocks, 256, 0, s>>>(phi, c, rho, pitch, n, h, w, dst);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gn_stats(const float* partials, int n, int groups, int entries, double count, int C,

@@ -181,7 +181,9 @@ def ensemble_members(n_runs: int = 64, seed: int = 3, v_range=(0.1, 0.9), c_rang
 STREAM_HYBRID = 4
 UNET_CHANNELS = (32, 64, 128, 256)
 UNET_FDIM = 128
-UNET_IN, UNET_OUT = 4, 3  # (phi, c, rho, dt / dt_ref) in; increments of (phi, c, rho) out
+UNET_LB = 3               # look-back frames of (phi, c, rho) fed to the network
+UNET_IN = 3 * UNET_LB + 1  # the frames oldest first, then a plane holding dt / dt_ref
+UNET_OUT = 3               # increments of (phi, c, rho) of the newest frame
 
 
 def unet_weights(seed: int = 0) -> dict:

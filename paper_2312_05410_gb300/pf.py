@@ -45,6 +45,18 @@ class Params(C.Structure):
         return p
 
 
+class HybridParams(C.Structure):
+    """Mirror of struct pf_hybrid_params."""
+    _fields_ = [("dns_stretch", C.c_long), ("jump_steps", C.c_long), ("frame_every", C.c_long),
+                ("dt_ref_steps", C.c_double)] + [(n, C.c_double) for n in (
+                    "phi_lo", "phi_hi", "c_lo", "c_hi", "rho_lo", "rho_hi")]
+
+
+class HybridStats(C.Structure):
+    """Mirror of struct pf_hybrid_stats."""
+    _fields_ = [("jumps", C.c_long), ("fallbacks", C.c_long), ("dns_steps", C.c_long)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libpf.so not built ({_LIB_PATH}); run python -m paper_2312_05410_gb300.build")
@@ -102,6 +114,9 @@ def _load():
     L.pf_unet_init.argtypes = [C.POINTER(C.POINTER(C.c_float)), C.c_int, C.c_int, C.c_int, C.c_int, vp, sz, vp,
                                C.POINTER(vp)]
     L.pf_unet_init.restype = C.c_int
+    L.pf_unet_frame.argtypes = [vp, C.c_int, pp, pp, pp, C.c_int]
+    L.pf_unet_frame.restype = C.c_int
+    L.pf_unet_reset_frames.argtypes, L.pf_unet_reset_frames.restype = [vp], C.c_int
     L.pf_unet_jump.argtypes = [vp, C.c_int, pp, pp, pp, C.c_int, C.c_double]
     L.pf_unet_jump.restype = C.c_int
     L.pf_unet_sync.argtypes, L.pf_unet_sync.restype = [vp], C.c_int
@@ -110,6 +125,10 @@ def _load():
     L.pf_unet_buffer.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(C.c_int)]
     L.pf_unet_buffer.restype = C.c_int
     L.pf_unet_destroy.argtypes, L.pf_unet_destroy.restype = [vp], C.c_int
+    L.pf_hybrid_workspace_size.argtypes, L.pf_hybrid_workspace_size.restype = [vp], sz
+    L.pf_hybrid_run.argtypes = [vp, vp, C.POINTER(HybridParams), C.c_long, vp, sz, C.POINTER(HybridStats)]
+    L.pf_hybrid_run.restype = C.c_int
+    L.pf_hybrid_last_error.argtypes, L.pf_hybrid_last_error.restype = [], C.c_char_p
     L.pf_s2_counts.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     L.pf_s2_counts.restype = C.c_int
     L.pf_strerror.argtypes, L.pf_strerror.restype = [C.c_int], C.c_char_p
@@ -564,11 +583,23 @@ class UNet:
                                  C.byref(h)))
         self.h = h
 
-    def jump(self, fields, tau: float):
-        """fields: `batch` tuples (phi, c, rho) of (ny, pitch) float32 CUDA tensors, updated in place."""
+    @staticmethod
+    def _tables(fields):
         n = len(fields)
-        arr = [(C.c_void_p * n)(*[int(f[q].data_ptr()) for f in fields]) for q in range(3)]
-        pitch = fields[0][0].shape[1]
+        return n, [(C.c_void_p * n)(*[int(f[q].data_ptr()) for f in fields]) for q in range(3)], fields[0][0].shape[1]
+
+    def frame(self, fields):
+        """Push `batch` tuples (phi, c, rho) of (ny, pitch) float32 CUDA tensors as the newest look-back frame."""
+        n, arr, pitch = self._tables(fields)
+        _ucheck(lib.pf_unet_frame(self.h, n, arr[0], arr[1], arr[2], pitch))
+
+    def reset_frames(self):
+        _ucheck(lib.pf_unet_reset_frames(self.h))
+
+    def jump(self, fields, tau: float):
+        """fields: `batch` tuples (phi, c, rho) of (ny, pitch) float32 CUDA tensors, updated in place; the
+        frames pushed with frame() are the look-back."""
+        n, arr, pitch = self._tables(fields)
         _ucheck(lib.pf_unet_jump(self.h, n, arr[0], arr[1], arr[2], pitch, float(tau)))
 
     def sync(self):
@@ -603,6 +634,34 @@ class UNet:
             self.close()
         except Exception:
             pass
+
+
+class Hybrid:
+    """The hybrid DNS / U-Net solver (pf_hybrid_run): an Ensemble of equal grids and a UNet of the same
+    batch and grid, sharing one stream.  Each cycle runs `dns_stretch` DNS steps (pushing look-back
+    frames `2 frame_every` and `frame_every` steps before its end), backs the state up, jumps
+    `jump_steps` steps with the U-Net and falls back to DNS for the jumped steps when a prediction
+    fails the plausibility ranges."""
+
+    def __init__(self, ens: "Ensemble", net: "UNet", dns_stretch: int = 2000, jump_steps: int = 2000,
+                 frame_every: int = 1000, dt_ref_steps: float = 2000.0, phi_range=(-1.5, 1.5),
+                 c_range=(-0.5, 1.5), rho_range=(-0.5, 1.5)):
+        import torch
+        self.ens, self.net = ens, net
+        self.params = HybridParams(int(dns_stretch), int(jump_steps), int(frame_every), float(dt_ref_steps),
+                                   *phi_range, *c_range, *rho_range)
+        size = int(lib.pf_hybrid_workspace_size(ens.h))
+        self.work = torch.empty(size + 256, dtype=torch.uint8, device="cuda")
+        self._wp = (self.work.data_ptr() + 255) // 256 * 256
+        self._size = size
+
+    def run(self, total_steps: int) -> dict:
+        st = HybridStats()
+        rc = lib.pf_hybrid_run(self.ens.h, self.net.h, C.byref(self.params), int(total_steps), self._wp,
+                               self._size, C.byref(st))
+        if rc != PF_OK:
+            raise PFError(rc, f"{strerror(rc)}: {lib.pf_hybrid_last_error().decode()}")
+        return {"jumps": st.jumps, "fallbacks": st.fallbacks, "dns_steps": st.dns_steps}
 
 
 def s2_counts(phi, c, nx: int, ny: int, R: int, stream=None):

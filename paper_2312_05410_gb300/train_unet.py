@@ -1,17 +1,21 @@
 """Train the time-conditioned U-Net on trajectories that the GPU DNS generates.
 
-    python -m paper_2312_05410_gb300.train_unet --out weights.npz [--runs 32] [--budget 300]
+    python -m paper_2312_05410_gb300.train_unet --out weights.npz [--runs 200] [--budget 1800]
 
 This is offline tooling, not the solver's path.
-- **Data.** The batched ensemble kernel advances `runs` seeded films of 256 x 256 cells.
-  A snapshot of (phi, c, rho) is kept every 2000 steps, 50 snapshots per run, like the
-  paper's 50-snapshot trajectories ("Dataset").
-- **Training.** Each pair of consecutive snapshots is a sample with jump length
-  tau = 1 (2000 steps), input (phi, c, rho, tau) and target (phi, c, rho).  Samples are shifted and mirrored in x at random: the domain is
-  periodic in x and, at normal incidence, mirror-symmetric.  The network is the one the inference kernels compute
-  (pf_unet_jump), written a second time with PyTorch operations so that autograd
-  can differentiate it.  Training uses Adam on the relative squared error of both
-  fields ("Training of the network", "Error metrics").
+- **Data.** The batched ensemble kernel advances `runs` seeded films of 256 x 256 cells
+  (another seed than the hybrid benchmark's runs).  A snapshot of (phi, c, rho) is kept
+  every 1000 steps, 100 snapshots per run.
+- **Samples.** The network's input is three look-back frames 1000 steps apart, oldest
+  first (the paper's operator reads lb = 3 consecutive frames), and the jump length
+  tau = 1 (2000 steps); the target is the state 2000 steps after the newest frame.  This
+  is what the hybrid solver feeds it: the two older frames are the start and the middle
+  of the DNS stretch before the jump.  Samples are shifted and mirrored in x at random:
+  the domain is periodic in x and, at normal incidence, mirror-symmetric.
+- **Training.** The network is the one the inference kernels compute (pf_unet_jump),
+  written a second time with PyTorch operations so that autograd can differentiate it.
+  Adam on the summed relative squared error of the three fields ("Training of the
+  network", "Error metrics"), cosine learning-rate decay over the time budget, BF16 autocast.
 - **Output.** The weights are written under the names pf.UNet expects.  Prediction
   with them runs only in the hand-written BF16 tensor-core kernels.
 """
@@ -29,8 +33,9 @@ CH = I.UNET_CHANNELS
 FDIM = I.UNET_FDIM
 
 
-def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 2000, snapshots: int = 50):
-    """(phi, c, rho) snapshots [snapshots + 1, runs, 3, side, side] on the GPU, from seeded films."""
+def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 1000, snapshots: int = 100):
+    """(phi, c, rho) snapshots [snapshots + 1, runs, 3, side, side] (FP32, on the GPU) of seeded films,
+    one every `every` steps."""
     import torch
 
     ms = []
@@ -43,17 +48,20 @@ def generate(pf, runs: int, side: int = 256, seed: int = 11, every: int = 2000, 
     probe.close()
     ens = pf.Ensemble(ms)
     ens.set_tile(tile)
+    out = torch.empty((snapshots + 1, runs, 3, side, side), dtype=torch.float32, device="cuda")
 
-    def grab():
-        return torch.stack([torch.stack([run[q][:, :side] for q in range(3)]) for run in ens.fields]).clone()
+    def grab(k):
+        for r, run in enumerate(ens.fields):
+            for q in range(3):
+                out[k, r, q].copy_(run[q][:, :side])
 
-    out = [grab()]
-    for _ in range(snapshots):
+    grab(0)
+    for k in range(1, snapshots + 1):
         ens.step(every)
-        out.append(grab())
+        grab(k)
     torch.cuda.synchronize()
     ens.close()
-    return torch.stack(out)
+    return out
 
 
 def make_model(seed: int = 0):
@@ -90,28 +98,32 @@ def make_model(seed: int = 0):
             d1 = F.conv_transpose2d(self.block(torch.cat([zc[1], d2], 1), "dec2"), p["up2"], stride=2)
             h1 = self.block(torch.cat([zc[0], d1], 1), "dec1")
             inc = F.conv2d(h1, p["out"], padding=1)
-            return x[:, :3] + inc * p["out_gamma"][None, :, None, None] + p["out_beta"][None, :, None, None]
+            k = 3 * (I.UNET_LB - 1)  # the newest frame
+            return x[:, k:k + 3] + inc * p["out_gamma"][None, :, None, None] + p["out_beta"][None, :, None, None]
 
     return Net()
 
 
-def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float = 1e-3, seed: int = 0,
-          log=print) -> dict:
+def train(pf, runs: int = 200, budget_s: float = 1800.0, batch: int = 8, lr: float = 1e-3, seed: int = 0,
+          held_out: int = 4, log=print) -> dict:
     import torch
 
     torch.manual_seed(seed)
-    data = generate(pf, runs)                      # [51, runs, 3, H, W]
-    S, R = data.shape[0] - 1, data.shape[1]
-    pairs = [(k, r) for k in range(S) for r in range(R)]
-    val = [(k, r) for (k, r) in pairs if r == R - 1]  # the last run is held out
-    trn = [(k, r) for (k, r) in pairs if r != R - 1]
+    lb, gap, ahead = I.UNET_LB, 1, 2  # frames 1 snapshot apart, target 2 snapshots after the newest frame
+    data = generate(pf, runs)          # [101, runs, 3, H, W]
+    S, R = data.shape[0], data.shape[1]
+    first = (lb - 1) * gap
+    idx = [(k, r) for k in range(first, S - ahead) for r in range(R)]
+    val = [(k, r) for (k, r) in idx if r >= R - held_out]  # the last runs are held out
+    trn = [(k, r) for (k, r) in idx if r < R - held_out]
     net = make_model(seed).cuda()
     opt = torch.optim.Adam(net.parameters(), lr=lr)
-    sched_T = None
+    g = np.random.default_rng(seed)
 
-    def sample(idx, augment=False):
-        x = torch.stack([torch.cat([data[k, r], torch.ones_like(data[k, r, :1])]) for k, r in idx])
-        y = torch.stack([data[k + 1, r] for k, r in idx])
+    def sample(ids, augment=False):
+        x = torch.stack([torch.cat([data[k - (lb - 1 - f) * gap, r] for f in range(lb)]
+                                   + [torch.ones_like(data[k, r, :1])]) for k, r in ids])
+        y = torch.stack([data[k + ahead, r] for k, r in ids])
         if augment:  # x is periodic and, at normal incidence, mirror-symmetric: random shifts and flips
             shift = int(g.integers(0, x.shape[-1]))
             x, y = torch.roll(x, shift, dims=-1), torch.roll(y, shift, dims=-1)
@@ -122,10 +134,18 @@ def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float
     def loss_fn(pred, y):
         return sum(((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(3))
 
-    g = np.random.default_rng(seed)
+    def validate():
+        tot, cnt = 0.0, 0
+        with torch.no_grad(), torch.autocast("cuda", dtype=torch.bfloat16):
+            for i in range(0, len(val), 16):
+                x, y = sample(val[i:i + 16])
+                tot += float(loss_fn(net(x, 1.0).float(), y)) * len(val[i:i + 16])
+                cnt += len(val[i:i + 16])
+        return tot / cnt / 3
+
     t0 = time.time()
-    step = 0
-    epoch = 0
+    step = epoch = 0
+    loss = torch.zeros(())
     while time.time() - t0 < budget_s:
         order = g.permutation(len(trn))
         for i in range(0, len(order) - batch + 1, batch):
@@ -143,20 +163,17 @@ def train(pf, runs: int = 32, budget_s: float = 300.0, batch: int = 8, lr: float
             if time.time() - t0 > budget_s:
                 break
         epoch += 1
-        with torch.no_grad(), torch.autocast("cuda", dtype=torch.bfloat16):
-            x, y = sample(val)
-            v = float(loss_fn(net(x, 1.0).float(), y)) / 3
+        v = validate()
         log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss) / 3:.3e} "
             f"val rel-sq {v:.3e} (rel L2 {math.sqrt(v):.3e})")
-    del sched_T
     return {k: v.detach().float().cpu().numpy() for k, v in net.p.items()}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
-    ap.add_argument("--runs", type=int, default=32)
-    ap.add_argument("--budget", type=float, default=300.0)
+    ap.add_argument("--runs", type=int, default=200)
+    ap.add_argument("--budget", type=float, default=1800.0)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args()

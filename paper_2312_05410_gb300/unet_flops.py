@@ -1,12 +1,14 @@
 """Multiply-add work of one U-Net forward pass (2 FLOPs per multiply-add), by layer."""
 from __future__ import annotations
 
+from .inputs import UNET_IN
+
 
 def layer_flops(h: int, w: int) -> list[tuple[str, float]]:
     """(layer, FLOPs) of one sample on an h x w input: 3x3 convolutions of the encoder and decoder
     blocks, the stride-2 transposed convolutions, and the output convolution."""
     out = []
-    enc = [(4, 32), (32, 64), (64, 128), (128, 256)]
+    enc = [(UNET_IN, 32), (32, 64), (64, 128), (128, 256)]
     for lvl, (ci, co) in enumerate(enc):
         out.append((f"enc{lvl + 1}", 2.0 * 9 * ci * co * (h >> lvl) * (w >> lvl)))
     dec = [("dec4", 256, 256, 3), ("dec3", 256, 128, 2), ("dec2", 128, 64, 1), ("dec1", 64, 32, 0)]

@@ -67,7 +67,12 @@ def test_training_data_has_the_printed_shape():
     P = paper_values()
     d = inspect.signature(T.generate).parameters
     assert [d["side"].default] * 2 == P["dataset_grid"]
-    assert d["snapshots"].default == P["dataset_snapshots"]
+    # a trajectory holds the paper's 50 equally spaced snapshots one jump (2000 steps) apart, and the
+    # midpoints between them, which the look-back frames (1000 steps apart) need
+    every, snaps = d["every"].default, d["snapshots"].default
+    jump = 2 * every
+    assert snaps * every == P["dataset_snapshots"] * jump
+    assert snaps == 2 * P["dataset_snapshots"]
 
 
 def test_paper_shaped_parameter_ranges():

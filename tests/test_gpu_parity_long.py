@@ -124,8 +124,8 @@ def test_ensemble_members_384_and_512_at_2000_steps(pf):
 
 
 def test_unet_jump_at_256_elementwise_against_the_reference_network(pf):
-    """Two 256^2 films (the hybrid's grid) through pf_unet_jump against the FP64 reference network,
-    element by element.
+    """Two 256^2 films (the hybrid's grid) with two pushed look-back frames each, through pf_unet_jump
+    against the FP64 reference network, element by element.
 
     The output is y = x + gamma conv(h1, w) + beta, with h1 the BF16 activations of the last
     block.  The reference mirrors the GPU's BF16 storage of every activation, so the two differ
@@ -142,14 +142,19 @@ def test_unet_jump_at_256_elementwise_against_the_reference_network(pf):
     H, tau = 256, 1.0
     W = I.unet_weights(2)
     p = O.with_dt(I.default_params())
-    states = [I.film_state(I.FilmSpec(H, H, 60.0 + 30 * k, seed=40 + k, c_inc=0.4 + 0.2 * k), p) for k in range(2)]
-    fields = [tuple(pf.device_fields(st)) for st in states]
+    # three look-back frames per run (oldest first): a film thickening and its composition drifting
+    frames = [[I.film_state(I.FilmSpec(H, H, 60.0 + 30 * k + 6 * f, seed=40 + k, c_inc=0.4 + 0.2 * k + 0.03 * f), p)
+               for f in range(3)] for k in range(2)]
+    dev = [[tuple(pf.device_fields(fr)) for fr in run] for run in frames]
     net = pf.UNet(W, 2, H, H)
+    net.frame([run[0] for run in dev])
+    net.frame([run[1] for run in dev])
+    fields = [run[2] for run in dev]
     net.jump(fields, tau)
     net.sync()
     got = np.stack([np.stack([f[q][:, :H].cpu().numpy().astype(np.float64) for q in range(3)]) for f in fields])
     net.close()
-    x = np.stack([np.stack([st[0], st[1], st[2], np.full((H, H), tau)]) for st in states])
+    x = np.stack([np.concatenate([np.stack(fr) for fr in run] + [np.full((1, H, H), tau)]) for run in frames])
     taps = {}
     ref = U.forward(W, x, tau, taps)
     h1 = taps["h1"]
@@ -162,6 +167,6 @@ def test_unet_jump_at_256_elementwise_against_the_reference_network(pf):
     ratio = d / bound
     worst = np.unravel_index(np.argmax(ratio), ratio.shape)
     print(f"U-Net 2 x 256^2: max |d| {d.max():.3e}, max d/bound {ratio.max():.3f} at {worst}, "
-          f"99.9th pct {np.quantile(ratio, 0.999):.3f}, increment scale {np.abs(ref - x[:, :3]).mean():.3e}")
+          f"99.9th pct {np.quantile(ratio, 0.999):.3f}, increment scale {np.abs(ref - x[:, 6:9]).mean():.3e}")
     assert np.all(np.isfinite(got))
     assert ratio.max() <= 1.0, (worst, float(d[worst]), float(bound[worst]))

@@ -143,20 +143,32 @@ def test_unsupported_shapes_are_rejected(pf):
     assert e.value.code == pf.PF_ERR_ARG
 
 
-def _unet_case(pf, n=2, H=128, seed=0, tau=0.5):
+def _lookback_states(n, H, base_seed=0):
+    """Three look-back frames per run: films of growing thickness and drifting composition (oldest first)."""
     import oracle as O
     from paper_2312_05410_gb300 import inputs as I
-    W = I.unet_weights(seed)
     p = O.with_dt(I.default_params())
-    states = [I.film_state(I.FilmSpec(H, H, 40.0 + 10 * k, seed=k), p) for k in range(n)]
-    fields = [tuple(pf.device_fields(st)) for st in states]
+    return [[I.film_state(I.FilmSpec(H, H, 40.0 + 10 * k + 4 * f, seed=base_seed + k, c_inc=0.45 + 0.05 * f), p)
+             for f in range(3)] for k in range(n)]
+
+
+def _unet_case(pf, n=2, H=128, seed=0, tau=0.5):
+    """A jump of n runs with two pushed look-back frames, and the reference network on the same input."""
+    from paper_2312_05410_gb300 import inputs as I
+    W = I.unet_weights(seed)
+    frames = _lookback_states(n, H)
+    fields = [[tuple(pf.device_fields(fr)) for fr in run] for run in frames]
     net = pf.UNet(W, n, H, H)
-    net.jump(fields, tau)
+    net.frame([run[0] for run in fields])
+    net.frame([run[1] for run in fields])
+    cur = [run[2] for run in fields]
+    net.jump(cur, tau)
     net.sync()
-    x = np.stack([np.stack([st[0], st[1], st[2], np.full((H, H), tau)]) for st in states])
+    x = np.stack([np.concatenate([np.stack(fr) for fr in run] + [np.full((1, H, H), tau)]) for run in frames])
     taps = {}
     ref = U.forward(W, x, tau, taps)
-    return net, fields, ref, taps, x
+    states = [run[2] for run in frames]
+    return net, cur, ref, taps, x, states
 
 
 def _layer_report(net, taps):
@@ -172,7 +184,7 @@ def _layer_report(net, taps):
 
 
 def test_unet_jump_matches_the_reference_network(pf):
-    net, fields, ref, taps, x = _unet_case(pf)
+    net, fields, ref, taps, x, states = _unet_case(pf)
     rep = _layer_report(net, taps)
     print("per-layer (fraction beyond 1 BF16 ulp, relative L2):", rep)
     for tap, (_, rel) in rep.items():
@@ -182,12 +194,43 @@ def test_unet_jump_matches_the_reference_network(pf):
             got = f[q][:, :128].cpu().numpy().astype(np.float64)
             e = np.linalg.norm(got - ref[i, q]) / np.linalg.norm(ref[i, q])
             # the increment alone (the output convolution's affine result), against the reference's
-            base = np.asarray(x[i, q], dtype=np.float32).astype(np.float64)
+            base = np.asarray(states[i][q], dtype=np.float32).astype(np.float64)
             di = np.linalg.norm((got - base) - (ref[i, q] - base)) / np.linalg.norm(ref[i, q] - base)
             print(f"run {i} {name}: relative L2 {e:.3e}, of the increment {di:.3e}")
             assert e <= 2e-2, (i, name, e)
             assert di <= 5e-2, (i, name, di)
     net.close()
+
+
+def test_lookback_frames_enter_the_jump(pf):
+    """The jump reads the pushed frames: with no frame pushed it equals the jump whose frames are the
+    current fields themselves (bit for bit), and pushing other frames changes its result; reset_frames
+    forgets them."""
+    from paper_2312_05410_gb300 import inputs as I
+    W = I.unet_weights(6)
+    frames = _lookback_states(2, 128, base_seed=30)
+    out = {}
+    for mode in ("none", "current", "history", "reset"):
+        fields = [[tuple(pf.device_fields(fr)) for fr in run] for run in frames]
+        net = pf.UNet(W, 2, 128, 128)
+        cur = [run[2] for run in fields]
+        if mode == "current":
+            net.frame(cur)
+            net.frame(cur)
+        elif mode in ("history", "reset"):
+            net.frame([run[0] for run in fields])
+            net.frame([run[1] for run in fields])
+            if mode == "reset":
+                net.reset_frames()
+        net.jump(cur, 0.5)
+        net.sync()
+        out[mode] = [t.clone() for f in cur for t in f]
+        net.close()
+    for a, b in zip(out["none"], out["current"]):
+        assert torch.equal(a, b)
+    for a, b in zip(out["none"], out["reset"]):
+        assert torch.equal(a, b)
+    assert any(not torch.equal(a, b) for a, b in zip(out["none"], out["history"]))
 
 
 def test_jump_is_the_same_with_halo_and_per_tap_staging(pf):
@@ -243,30 +286,9 @@ def test_plausibility_check_flags_out_of_range_runs(pf):
     net.close()
 
 
-def _hybrid(pf, ens, net, cycles, stretch, jump):
-    """The hybrid loop of bench.py's hybrid workload: DNS stretch, snapshot, jump, plausibility gate."""
-    fields = [t for run in ens.fields for t in run]
-    backup = [t.clone() for t in fields]
-    fallbacks = 0
-    for _ in range(cycles):
-        ens.step(stretch)
-        with torch.cuda.stream(ens.stream):
-            for b, t in zip(backup, fields):
-                b.copy_(t)
-        net.jump(ens.fields, jump / 2000.0)
-        if not all(net.check()):
-            with torch.cuda.stream(ens.stream):
-                for b, t in zip(backup, fields):
-                    t.copy_(b)
-            ens.step(jump)
-            fallbacks += 1
-    torch.cuda.synchronize()
-    return fallbacks
-
-
 def test_hybrid_with_rejected_jumps_is_exactly_the_dns(pf):
     """Seeded untrained weights make every jump implausible: each one must be undone and replaced by the DNS
-    stretch, so the hybrid result equals plain DNS bit for bit."""
+    stretch, so the hybrid result (pf_hybrid_run) equals plain DNS bit for bit."""
     import oracle as O
     from paper_2312_05410_gb300 import inputs as I2
     ms = []
@@ -276,7 +298,8 @@ def test_hybrid_with_rejected_jumps_is_exactly_the_dns(pf):
     ens = pf.Ensemble(ms)
     ens.set_tile(0)
     net = pf.UNet(I2.unet_weights(0), 2, 128, 128, stream=ens.stream)
-    assert _hybrid(pf, ens, net, cycles=3, stretch=200, jump=200) == 3
+    st = pf.Hybrid(ens, net, dns_stretch=200, jump_steps=200, frame_every=100).run(1200)
+    assert st == {"jumps": 0, "fallbacks": 3, "dns_steps": 1200}
     hyb = [tuple(t.clone() for t in run) for run in ens.fields]
     ens.close()
     ref = pf.Ensemble(ms)
@@ -290,7 +313,8 @@ def test_hybrid_with_rejected_jumps_is_exactly_the_dns(pf):
 
 
 def test_hybrid_with_identity_jumps_skips_the_jumped_steps(pf):
-    """A zero output affine makes each jump the identity: the hybrid then equals DNS of the stretches only."""
+    """A zero output affine makes each jump the identity: the hybrid (pf_hybrid_run) then equals DNS of the
+    stretches only."""
     import oracle as O
     from paper_2312_05410_gb300 import inputs as I2
     ms = []
@@ -303,7 +327,8 @@ def test_hybrid_with_identity_jumps_skips_the_jumped_steps(pf):
     ens = pf.Ensemble(ms)
     ens.set_tile(0)
     net = pf.UNet(W, 2, 128, 128, stream=ens.stream)
-    assert _hybrid(pf, ens, net, cycles=2, stretch=100, jump=300) == 0
+    st = pf.Hybrid(ens, net, dns_stretch=100, jump_steps=300, frame_every=50).run(800)
+    assert st == {"jumps": 2, "fallbacks": 0, "dns_steps": 200}
     hyb = [tuple(t.clone() for t in run) for run in ens.fields]
     ens.close()
     ref = pf.Ensemble(ms)

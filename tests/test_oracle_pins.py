@@ -424,3 +424,15 @@ def test_vapor_relaxes_to_reservoir_value():
     pd["dt"] = 0.5 * O.dt_limit(pd)["dt_rho"]  # phi = -1 and c are frozen in pure vapor
     _, _, r = O.step(pd, -np.ones((ny, nx)), np.full((ny, nx), 0.5), np.zeros((ny, nx)), 30000)
     assert np.allclose(r, 0.75, atol=1e-6)
+
+
+def test_all_cores_build_gives_the_checker_results_bit_for_bit():
+    """The CPU baseline's OpenMP build of the same source splits rows over threads; every cell is
+    computed by the same expressions, so its states equal the single-thread checker's exactly."""
+    p = O.with_dt(I.default_params(v_angle_deg=70.0, MA_bulk=2.0, MB_bulk=0.5, MA_surf=3.0, MB_surf=1.0,
+                                   sigma_surf=0.5))
+    st = I.film_state(I.FilmSpec(70, 45, 12.0, seed=8), p)
+    a = O.step(p, *st, 30)
+    b = O.step_all_cores(p, *st, 30)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)

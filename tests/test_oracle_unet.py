@@ -111,13 +111,23 @@ def test_mlp_basis_matches_a_loop_restatement():
 
 
 def _net_input(seed=4, n=2, h=32, w=32):
+    """Three look-back frames of (phi, c, rho) that drift apart a little, then the dt plane."""
     g = np.random.default_rng(seed)
-    x = np.empty((n, 4, h, w))
-    x[:, 0] = np.tanh(g.standard_normal((n, h, w)))
-    x[:, 1] = 0.5 + 0.2 * g.standard_normal((n, h, w))
-    x[:, 2] = 0.5 * (1 - x[:, 0])
-    x[:, 3] = 0.25
+    x = np.empty((n, U.IN_CH, h, w))
+    phi = np.tanh(g.standard_normal((n, h, w)))
+    c = 0.5 + 0.2 * g.standard_normal((n, h, w))
+    for f in range(U.LB):
+        pf_ = np.tanh(np.arctanh(np.clip(phi, -0.99, 0.99)) + 0.3 * f)
+        x[:, 3 * f] = pf_
+        x[:, 3 * f + 1] = c + 0.1 * f * g.standard_normal((n, h, w))
+        x[:, 3 * f + 2] = 0.5 * (1 - pf_)
+    x[:, -1] = 0.25
     return x
+
+
+def _newest(x):
+    k = 3 * (U.LB - 1)
+    return x[:, k:k + 3]
 
 
 def _rel(a, b):
@@ -131,11 +141,11 @@ def test_network_shapes_and_the_residual_output():
     y = U.forward(W, x, 0.25, taps)
     assert y.shape == (2, 3, 32, 32)
     assert taps["z4"].shape == (2, 256, 4, 4) and taps["d1"].shape == (2, 32, 32, 32)
-    np.testing.assert_allclose(y, x[:, :3].astype(np.float32) + taps["inc"].numpy() * W["out_gamma"][None, :, None, None]
+    np.testing.assert_allclose(y, _newest(x).astype(np.float32) + taps["inc"].numpy() * W["out_gamma"][None, :, None, None]
                                + W["out_beta"][None, :, None, None], rtol=1e-12, atol=1e-12)
     # with a zero output affine the jump is the identity on the FP32 fields
     W0 = dict(W, out_gamma=np.zeros(3, np.float32), out_beta=np.zeros(3, np.float32))
-    np.testing.assert_array_equal(U.forward(W0, x, 0.25), x[:, :3].astype(np.float32).astype(np.float64))
+    np.testing.assert_array_equal(U.forward(W0, x, 0.25), _newest(x).astype(np.float32).astype(np.float64))
 
 
 def test_network_invariants_of_the_normalisation_and_conditioning():
@@ -162,11 +172,18 @@ def test_network_invariants_of_the_normalisation_and_conditioning():
     assert _rel(inc(W1, x, 0.25), y) > 0.05
     # the jump length enters through the basis: another tau gives another prediction
     assert _rel(inc(W, x, 0.75), y) > 0.05
+    # every look-back frame enters the prediction: replacing the oldest or the middle frame by the newest
+    # one (a stationary history) moves the increment
+    for f in range(U.LB - 1):
+        xs = x.copy()
+        xs[:, 3 * f:3 * f + 3] = _newest(x)
+        assert _rel(inc(W, xs, 0.25), y) > 0.05, f
 
 
 def test_flop_count_matches_the_layer_shapes():
-    # 256^2: encoder 151 M + 3 x 604 M, decoder 1208 M + 3 x 2416 M, up-sampling 3 x 268 M, output 113 M
-    want = 151.0e6 + 3 * 604.0e6 + 1208.0e6 + 3 * 2416.0e6 + 3 * 268.4e6 + 113.2e6
+    # 256^2: encoder 377 M (10 input planes) + 3 x 604 M, decoder 1208 M + 3 x 2416 M, up-sampling
+    # 3 x 268 M, output 113 M
+    want = 377.5e6 + 3 * 604.0e6 + 1208.0e6 + 3 * 2416.0e6 + 3 * 268.4e6 + 113.2e6
     assert U.flops_per_sample(256, 256) == pytest.approx(want, rel=1e-3)
 
 
@@ -182,7 +199,7 @@ def test_training_network_is_the_reference_network():
     with torch.no_grad():
         y = net(torch.tensor(x, dtype=torch.float32), 0.25).double().numpy()
     ref = U.forward(W, x, 0.25)
-    base = x[:, :3].astype(np.float32).astype(np.float64)
+    base = _newest(x).astype(np.float32).astype(np.float64)
     assert _rel(y - base, ref - base) < 3e-2
     assert _rel(U.forward(dict(W, proj1=W["proj1"] * 2.0), x, 0.25) - base, ref - base) > 0.1
     assert _rel(U.forward(dict(W, dec1=W["dec1"][:, ::-1].copy()), x, 0.25) - base, ref - base) > 0.1
