@@ -149,6 +149,13 @@ int pf_set_wait_limit(pf_handle* h, int polls);
  * driver without tensor-map support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
 
+/* Grids above 2^20 cells (56 x 24 tiles): on = 1 (the default) steps them with a
+ * persistent kernel in which every resident CTA walks a share of the tiles and stages
+ * the next tile (TMA for interior tiles) while it computes one; on = 0 launches one
+ * CTA per tile.  Both give identical results.  Returns the previous setting (0 or 1),
+ * or PF_ERR_ARG for a smaller grid or a null handle. */
+int pf_set_tile_loop(pf_handle* h, int on);
+
 /* Clear the sticky device error word (async). */
 int pf_clear_error(pf_handle* h);
 
@@ -211,10 +218,12 @@ int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
  * pf_ens_step: advance every run n steps (async on the stream); the caller's
  *   fields hold the new states when the stream reaches the end of the call.
  * pf_ens_autotune: time trial_steps (even, >= 2) steps with each compiled tile
- *   shape and keep the fastest; these are real steps of the simulation (3 x
+ *   kind and keep the fastest; these are real steps of the simulation (4 x
  *   (trial_steps + 2) in total).  chosen (may be NULL) receives the tile kind,
- *   seconds_per_step (may be NULL, 3 doubles) the timings.  Synchronises.
- * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x24), 2 (56x16).
+ *   seconds_per_step (may be NULL, 4 doubles) the timings.  Synchronises.
+ * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x24), 2 (56x16), or
+ *   3: 56x24 tiles walked by a persistent kernel (one CTA per resident slot) that
+ *   stages the next tile while it computes one.  All kinds give identical results.
  * pf_ens_diag: pf_diag of run `run` (synchronises).
  */
 typedef struct pf_ens pf_ens;

@@ -145,6 +145,7 @@ struct pf_handle {
     pf::DiagConst d;
     int mob;
     int tile;
+    bool ring;              // large grids: the persistent tile loop (TILE_LARGE tiles, next tile staged ahead)
     bool tma;               // interior tiles staged by TMA through maps[buffer]
     pf::StepMaps maps[2];   // tensor maps of u[0] and u[1]
     cudaGraphExec_t gexec;
@@ -156,8 +157,11 @@ namespace {
 int do_step(pf_handle* h)
 {
     const int a = h->cur, b = 1 - h->cur;
-    cudaError_t e = pf::launch_step(h->k, h->tile, h->p.phi_mode, h->mob, h->u[a][0], h->u[a][1], h->u[a][2], h->u[b][0],
-                                    h->u[b][1], h->u[b][2], h->stream, h->tma ? &h->maps[a] : nullptr, h->err);
+    const pf::StepMaps* maps = h->tma ? &h->maps[a] : nullptr;
+    cudaError_t e = h->ring ? pf::launch_step_ring(h->k, h->p.phi_mode, h->mob, h->u[a][0], h->u[a][1], h->u[a][2],
+                                                   h->u[b][0], h->u[b][1], h->u[b][2], h->stream, maps, h->err)
+                            : pf::launch_step(h->k, h->tile, h->p.phi_mode, h->mob, h->u[a][0], h->u[a][1], h->u[a][2],
+                                              h->u[b][0], h->u[b][1], h->u[b][2], h->stream, maps, h->err);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
     h->cur = b;
     return PF_OK;
@@ -334,6 +338,7 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
     h->d = pf::diag_const_of(*p, nx, ny, pitch);
     h->mob = pf::mob_kind_of(*p);
     h->tile = pf::choose_tile(nx, ny);
+    h->ring = h->tile == pf::TILE_LARGE;
     // interior tiles are staged by TMA whenever the grid holds a full staged window
     h->tma =
              pf::make_step_maps(h->u[0][0], h->u[0][1], h->u[0][2], nx, ny, pitch, h->tile, &h->maps[0]) &&
@@ -456,6 +461,19 @@ int pf_set_wait_limit(pf_handle* h, int polls)
 }
 
 int pf_staging_mode(const pf_handle* h) { return h ? (h->tma ? 1 : 0) : -1; }
+
+int pf_set_tile_loop(pf_handle* h, int on)
+{
+    if (!h) return fail(PF_ERR_ARG, "null handle");
+    if (h->tile != pf::TILE_LARGE) return fail(PF_ERR_ARG, "the tile loop is built for grids above 2^20 cells");
+    const int prev = h->ring ? 1 : 0;
+    if ((on != 0) != h->ring && h->gexec) {  // the captured graph holds the other kernel
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    h->ring = on != 0;
+    return prev;
+}
 
 int pf_clear_error(pf_handle* h)
 {

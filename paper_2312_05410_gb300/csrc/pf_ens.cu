@@ -36,8 +36,8 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 struct EnsLayout {
     std::vector<size_t> state;  // per-run offset of the partner buffer (3 planes)
     size_t runs;                // EnsRun[nruns]
-    size_t tiles[pf::NUM_TILE_KINDS];
-    int ntiles[pf::NUM_TILE_KINDS];
+    size_t tiles[pf::NUM_TILE_TABLES];
+    int ntiles[pf::NUM_TILE_TABLES];
     size_t partials, out, err, total;
 };
 
@@ -52,7 +52,7 @@ bool ens_layout(int nruns, const int* nx, const int* ny, const int* pitch, EnsLa
     }
     L.runs = off;
     off = al256(off + size_t(nruns) * sizeof(pf::EnsRun));
-    for (int t = 0; t < pf::NUM_TILE_KINDS; ++t) {
+    for (int t = 0; t < pf::NUM_TILE_TABLES; ++t) {
         long long n = 0;
         for (int r = 0; r < nruns; ++r)
             n += (long long)((nx[r] + pf::tile_width() - 1) / pf::tile_width()) *
@@ -88,8 +88,8 @@ struct pf_ens {
     std::vector<int> nx, ny, pitch;
     std::vector<pf::EnsRun> host_runs;  // [0] buffers = caller's fields
     pf::EnsRun* runs;                    // device copy
-    pf::EnsTile* tiles[pf::NUM_TILE_KINDS];
-    int ntiles[pf::NUM_TILE_KINDS];
+    pf::EnsTile* tiles[pf::NUM_TILE_TABLES];
+    int ntiles[pf::NUM_TILE_TABLES];
     int tile;
     int phi_mode, mob;
     int parity;  // which buffer of every run is current (0: caller's)
@@ -107,8 +107,9 @@ namespace {
 
 int ens_launch(pf_ens* e)
 {
-    cudaError_t c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[e->tile], e->runs,
-                                        e->ntiles[e->tile], e->parity, e->stream);
+    const int tab = pf::tile_table(e->tile);
+    cudaError_t c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab],
+                                        e->parity, e->stream);
     if (c != cudaSuccess) return efail(PF_ERR_CUDA, "ensemble step launch: %s", cudaGetErrorString(c));
     e->parity = 1 - e->parity;
     return PF_OK;
@@ -130,7 +131,8 @@ int ens_graph(pf_ens* e, long G)
     }
     int rc = PF_OK;
     for (long s = 0; s < G && rc == PF_OK; ++s) {
-        c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[e->tile], e->runs, e->ntiles[e->tile],
+        c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[pf::tile_table(e->tile)], e->runs,
+                                e->ntiles[pf::tile_table(e->tile)],
                                 int(s & 1), cap);
         if (c != cudaSuccess) rc = efail(PF_ERR_CUDA, "ensemble capture: %s", cudaGetErrorString(c));
     }
@@ -248,8 +250,8 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
             std::swap(order[j], order[j - 1]);
     cudaError_t ce = cudaMemcpyAsync(e->runs, e->host_runs.data(), sizeof(pf::EnsRun) * nruns,
                                      cudaMemcpyHostToDevice, e->stream);
-    std::vector<std::vector<pf::EnsTile>> tabs(pf::NUM_TILE_KINDS);
-    for (int t = 0; t < pf::NUM_TILE_KINDS && ce == cudaSuccess; ++t) {
+    std::vector<std::vector<pf::EnsTile>> tabs(pf::NUM_TILE_TABLES);
+    for (int t = 0; t < pf::NUM_TILE_TABLES && ce == cudaSuccess; ++t) {
         const int TW = pf::tile_width(), TH = pf::tile_height(t);
         for (int r : order)
             for (int y = 0; y < ny[r]; y += TH)

@@ -31,12 +31,16 @@ enum MobKind { MOB_UNIFORM = 0, MOB_BULK = 1, MOB_SURF = 2 };
 
 
 // Output tile of the fused step kernel (4-cell halo staged around it): 56 columns
-// by tile_height(kind) rows; TILE_SMALL gives small grids many CTAs.
-enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1, TILE_MEDIUM = 2 };
-constexpr int NUM_TILE_KINDS = 3;
+// by tile_height(kind) rows; TILE_SMALL gives small grids many CTAs.  TILE_LARGE_RING is the
+// 56 x 24 tile walked by a persistent kernel that stages the next tile while computing one
+// (it uses TILE_LARGE's tile table and tensor maps).
+enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1, TILE_MEDIUM = 2, TILE_LARGE_RING = 3 };
+constexpr int NUM_TILE_KINDS = 4;
+constexpr int NUM_TILE_TABLES = 3;  // tile tables: TILE_SMALL, TILE_LARGE, TILE_MEDIUM
 int choose_tile(int nx, int ny);
 int tile_width();
 int tile_height(int tile);
+int tile_table(int tile);  // the tile table (and tensor-map box) a tile kind uses
 
 // Ensemble of independent runs stepped by one launch: per-run constants and the
 // two buffers of its ping-pong pair; one table entry per output tile.
@@ -70,6 +74,11 @@ cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob,
                         float* phi1, float* c1, float* rho1, cudaStream_t s,
                         const StepMaps* maps = nullptr, int* err = nullptr);
 size_t step_smem_bytes(int tile);
+// One fused step by the persistent 56 x 24 tile loop (maps: those of TILE_LARGE, or NULL for
+// per-thread staging only).
+cudaError_t launch_step_ring(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,
+                             const float* rho0, float* phi1, float* c1, float* rho1, cudaStream_t s,
+                             const StepMaps* maps, int* err);
 // One forward-Euler update u + k.dt R(u) (the adjoint's u* with k.dt = dt/2), small tile.
 cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,
                          const float* rho0, float* phi1, float* c1, float* rho1, cudaStream_t s);

@@ -279,125 +279,18 @@ __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, i
     n = lo + ((s + 1) * H) / S - r0;
 }
 
-// One step of the output tile with corner (x0, y0) of one run (the whole CTA).
-// STAGES = 2: the explicit midpoint step; STAGES = 1: one forward-Euler update
-// u + dt R(u) with the dt held in k (the adjoint uses it for u* with dt/2).
-template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2, bool TMA = false>
-__device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, const float* __restrict__ phi0,
-                                          const float* __restrict__ c0, const float* __restrict__ rho0,
-                                          float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1,
-                                          const StepMaps* maps = nullptr, int* err = nullptr)
+// The two Runge-Kutta stages of one staged tile (window corner (gx0, gy0), u^n in U, u* in B):
+// stage 1 into B, the ghost rows of u* where the tile touches the bottom or top, stage 2 to global
+// memory.  STAGES = 1: one forward-Euler update u + dt R(u) straight to global memory.
+template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2>
+__device__ __forceinline__ void compute_tile(const StepConst& k, int gx0, int gy0, const float* __restrict__ U,
+                                             float* __restrict__ B, float* __restrict__ phi1,
+                                             float* __restrict__ c1, float* __restrict__ rho1)
 {
     using G = Geo<TY, S>;
     constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
-    extern __shared__ __align__(128) float smraw[];
-    // TMA destinations need a 128-byte aligned base; that launch reserves the extra bytes
-    float* const sm = TMA ? reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127))
-                          : smraw;
-    float* const U = sm;               // u^n: phi, c, rho
-    float* const B = sm + 3 * PLANE;   // u*:  phi, c, rho (followed by the guard rows)
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gx0 = x0 - HALO, gy0 = y0 - HALO;
     const int nx = k.nx, ny = k.ny, pitch = k.pitch;
-
-    // Wait for the previous step's grid (programmatic dependent launch) before reading.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-
-    // ---- interior tiles: three TMA box copies (64 x LY each) completing on one mbarrier
-    bool staged = false;
-    if (TMA && gx0 >= 0 && gx0 + LX <= nx && gy0 >= 0 && gy0 + LY <= ny) {
-        __shared__ __align__(8) uint64_t mbar;
-        const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
-        if (tid == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
-        if (tid == 0) {
-            constexpr unsigned bytes = 3u * PLANE * sizeof(float);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-            const CUtensorMap* tm[3] = {&maps->phi, &maps->c, &maps->rho};
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const unsigned dst = (unsigned)__cvta_generic_to_shared(U + f * PLANE);
-                asm volatile(
-                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-                    "l"(reinterpret_cast<uint64_t>(tm[f])), "r"(gx0), "r"(gy0), "r"(mb)
-                    : "memory");
-            }
-        }
-        // bounded wait on phase 0; every thread votes so the whole CTA leaves together on a timeout
-        unsigned done = 0;
-        for (int it = 0; it < k.wait_cap && !done; ++it)
-            asm volatile(
-                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                : "=r"(done) : "r"(mb) : "memory");
-        if (__syncthreads_or(!done)) {
-            if (tid == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
-            for (int it = 0; it < (1 << 22) && !done; ++it)  // let the copies in flight land before leaving
-                asm volatile(
-                    "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                    : "=r"(done) : "r"(mb) : "memory");
-            return;
-        }
-        staged = true;
-    }
-    // ---- other tiles: stage u^n with its ghost rows; every 16-byte group is an asynchronous copy
-    if (!staged) {
-        auto field = [&](int f) { return f == 0 ? phi0 : (f == 1 ? c0 : rho0); };
-        auto wrap = [&](int gx) {  // periodic x; one correction suffices when nx >= LX
-            if (nx >= LX) {
-                gx = gx < 0 ? gx + nx : gx;
-                return gx >= nx ? gx - nx : gx;
-            }
-            gx %= nx;
-            return gx < 0 ? gx + nx : gx;
-        };
-        // source row of staged row ly for field fld; -1: zero, -2: reservoir value
-        auto src_row = [&](int fld, int ly) {
-            const int gy = gy0 + ly;
-            if (gy < -2 || gy > ny + 1) return -1;
-            if (fld == 2 && gy == ny) return -2;
-            return reflect(gy, ny);
-        };
-        if ((nx & 3) == 0) {
-            // x0 and nx are multiples of 4: each aligned group of 4 staged columns is
-            // wholly inside [0, nx) or wholly wrapped
-            constexpr int Q = LX / 4;
-            for (int idx = tid; idx < 3 * LY * Q; idx += G::THREADS) {
-                const int fld = idx / (LY * Q);
-                const int rem = idx - fld * (LY * Q);
-                const int ly = rem / Q, q = rem - ly * Q;
-                float* dst = U + fld * PLANE + ly * PX + 4 * q;
-                const int sr = src_row(fld, ly);
-                if (sr < 0) {
-                    const float v = (sr == -2) ? k.rho_top : 0.f;
-                    *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
-                } else {
-                    const float* src = field(fld) + (size_t)sr * pitch + wrap(gx0 + 4 * q);
-                    const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(src) : "memory");
-                }
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-        } else {
-            for (int idx = tid; idx < 3 * LY * LX; idx += G::THREADS) {
-                const int fld = idx / (LY * LX);
-                const int rem = idx - fld * (LY * LX);
-                const int ly = rem / LX, lx = rem - ly * LX;
-                const int sr = src_row(fld, ly);
-                float v = (sr == -2) ? k.rho_top : 0.f;
-                if (sr >= 0) v = __ldg(field(fld) + (size_t)sr * pitch + wrap(gx0 + lx));
-                U[fld * PLANE + ly * PX + lx] = v;
-            }
-        }
-    }
-    // Let the next step's grid begin launching; it waits for this grid to finish.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    __syncthreads();
-
     // staged rows holding domain rows: [dlo, dhi)
     const int dlo = -gy0 > 0 ? -gy0 : 0;
     const int dhi = ny - gy0 < LY ? ny - gy0 : LY;
@@ -454,6 +347,155 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
                                                  store_x, pair_full);
 }
 
+// Per-thread staging of the window with corner (gx0, gy0) of u^n into U: periodic wrap in x,
+// reflected ghost rows of phi and c, the reservoir row of rho above the top, zero rows beyond.
+// nx % 4 == 0: every aligned 16-byte group is one asynchronous copy (cp.async, not waited for
+// here); other widths: plain loads and stores.
+template <int TY, int S>
+__device__ __forceinline__ void issue_plain(const StepConst& k, int gx0, int gy0, const float* __restrict__ phi0,
+                                            const float* __restrict__ c0, const float* __restrict__ rho0,
+                                            float* __restrict__ U)
+{
+    using G = Geo<TY, S>;
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    const int tid = threadIdx.x;
+    const int nx = k.nx, ny = k.ny, pitch = k.pitch;
+    auto field = [&](int f) { return f == 0 ? phi0 : (f == 1 ? c0 : rho0); };
+    auto wrap = [&](int gx) {  // periodic x; one correction suffices when nx >= LX
+        if (nx >= LX) {
+            gx = gx < 0 ? gx + nx : gx;
+            return gx >= nx ? gx - nx : gx;
+        }
+        gx %= nx;
+        return gx < 0 ? gx + nx : gx;
+    };
+    // source row of staged row ly for field fld; -1: zero, -2: reservoir value
+    auto src_row = [&](int fld, int ly) {
+        const int gy = gy0 + ly;
+        if (gy < -2 || gy > ny + 1) return -1;
+        if (fld == 2 && gy == ny) return -2;
+        return reflect(gy, ny);
+    };
+    if ((nx & 3) == 0) {
+        // x0 and nx are multiples of 4: each aligned group of 4 staged columns is
+        // wholly inside [0, nx) or wholly wrapped
+        constexpr int Q = LX / 4;
+        for (int idx = tid; idx < 3 * LY * Q; idx += G::THREADS) {
+            const int fld = idx / (LY * Q);
+            const int rem = idx - fld * (LY * Q);
+            const int ly = rem / Q, q = rem - ly * Q;
+            float* dst = U + fld * PLANE + ly * PX + 4 * q;
+            const int sr = src_row(fld, ly);
+            if (sr < 0) {
+                const float v = (sr == -2) ? k.rho_top : 0.f;
+                *reinterpret_cast<float4*>(dst) = make_float4(v, v, v, v);
+            } else {
+                const float* src = field(fld) + (size_t)sr * pitch + wrap(gx0 + 4 * q);
+                const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst), "l"(src) : "memory");
+            }
+        }
+    } else {
+        for (int idx = tid; idx < 3 * LY * LX; idx += G::THREADS) {
+            const int fld = idx / (LY * LX);
+            const int rem = idx - fld * (LY * LX);
+            const int ly = rem / LX, lx = rem - ly * LX;
+            const int sr = src_row(fld, ly);
+            float v = (sr == -2) ? k.rho_top : 0.f;
+            if (sr >= 0) v = __ldg(field(fld) + (size_t)sr * pitch + wrap(gx0 + lx));
+            U[fld * PLANE + ly * PX + lx] = v;
+        }
+    }
+}
+
+// Thread 0 only: three TMA box copies (64 x LY per field) of the window with corner (gx0, gy0)
+// into U, completing on the mbarrier at shared address mb (armed here for their bytes).
+template <int TY, int S>
+__device__ __forceinline__ void issue_tma(const StepMaps* maps, int gx0, int gy0, float* U, unsigned mb)
+{
+    constexpr int PLANE = Geo<TY, S>::PLANE;
+    constexpr unsigned bytes = 3u * PLANE * sizeof(float);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+    const CUtensorMap* tm[3] = {&maps->phi, &maps->c, &maps->rho};
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(U + f * PLANE);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+            "l"(reinterpret_cast<uint64_t>(tm[f])), "r"(gx0), "r"(gy0), "r"(mb)
+            : "memory");
+    }
+}
+
+// Bounded poll of mbarrier phase `parity` by the calling thread: 1 if it completed within cap polls.
+__device__ __forceinline__ unsigned poll_phase(unsigned mb, unsigned parity, int cap)
+{
+    unsigned done = 0;
+    for (int it = 0; it < cap && !done; ++it)
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+    return done;
+}
+
+// One step of the output tile with corner (x0, y0) of one run (the whole CTA).
+// STAGES = 2: the explicit midpoint step; STAGES = 1: one forward-Euler update
+// u + dt R(u) with the dt held in k (the adjoint uses it for u* with dt/2).
+template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2, bool TMA = false>
+__device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, const float* __restrict__ phi0,
+                                          const float* __restrict__ c0, const float* __restrict__ rho0,
+                                          float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1,
+                                          const StepMaps* maps = nullptr, int* err = nullptr)
+{
+    using G = Geo<TY, S>;
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    extern __shared__ __align__(128) float smraw[];
+    // TMA destinations need a 128-byte aligned base; that launch reserves the extra bytes
+    float* const sm = TMA ? reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127))
+                          : smraw;
+    float* const U = sm;               // u^n: phi, c, rho
+    float* const B = sm + 3 * PLANE;   // u*:  phi, c, rho (followed by the guard rows)
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gx0 = x0 - HALO, gy0 = y0 - HALO;
+    const int nx = k.nx, ny = k.ny, pitch = k.pitch;
+
+    // Wait for the previous step's grid (programmatic dependent launch) before reading.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    // ---- interior tiles: three TMA box copies (64 x LY each) completing on one mbarrier
+    bool staged = false;
+    if (TMA && gx0 >= 0 && gx0 + LX <= nx && gy0 >= 0 && gy0 + LY <= ny) {
+        __shared__ __align__(8) uint64_t mbar;
+        const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) issue_tma<TY, S>(maps, gx0, gy0, U, mb);
+        // bounded wait on phase 0; every thread votes so the whole CTA leaves together on a timeout
+        const unsigned done = poll_phase(mb, 0, k.wait_cap);
+        if (__syncthreads_or(!done)) {
+            if (tid == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
+            poll_phase(mb, 0, 1 << 22);  // let the copies in flight land before leaving
+            return;
+        }
+        staged = true;
+    }
+    // ---- other tiles: stage u^n with its ghost rows
+    if (!staged) {
+        issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, U);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    // Let the next step's grid begin launching; it waits for this grid to finish.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __syncthreads();
+
+    compute_tile<TY, S, PHI_MODE, MOB, STAGES>(k, gx0, gy0, U, B, phi1, c1, rho1);
+}
+
 // One step of one run: a 2D grid of 56 x TY tiles.
 template <int TY, int S, int PHI_MODE, int MOB>
 __global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
@@ -496,6 +538,169 @@ ens_step_kernel(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ ru
     const int a = parity, b = 1 - parity;
     step_tile<TY, S, PHI_MODE, MOB>(r.k, t.x0, t.y0, r.f[a][0], r.f[a][1], r.f[a][2], r.f[b][0], r.f[b][1],
                                     r.f[b][2]);
+}
+
+// ---- persistent tile loops for large grids and ensembles
+//
+// CTA b takes tiles b, b + G, b + 2G, ... of the row-major tile order (G = the grid: as many CTAs
+// as are resident at once), and while it computes tile i the staging of tile i+1 is in flight
+// into the second of two staging buffers: interior tiles by TMA (thread 0, an mbarrier per
+// buffer), the others by per-thread cp.async.  The arithmetic per tile is compute_tile's, so the
+// results equal the one-tile-per-CTA kernels bit for bit.  Shared memory: two staged windows and
+// u* (76.7 KB at 56 x 24), 3 CTAs per SM.  When nx % 4 != 0 the per-thread staging is synchronous
+// (no overlap), with the same results.
+constexpr int RING_MINB = 3;
+
+template <int TY, int S>
+struct RingGeo {
+    static constexpr size_t BYTES = (size_t(9) * Geo<TY, S>::PLANE + Geo<TY, S>::GUARD) * sizeof(float) + 128;
+};
+
+// Ring state of one CTA: the staging buffers, their mbarriers and phases.
+template <int TY, int S>
+struct Ring {
+    float* U;  // buffer b at U + b * 3 PLANE
+    float* B;  // u* and the guard rows
+    unsigned mb[2];
+    unsigned phase[2] = {0u, 0u};
+    bool tma[2] = {false, false};
+    __device__ float* buf(int b) const { return U + b * 3 * Geo<TY, S>::PLANE; }
+};
+
+template <int TY, int S>
+__device__ __forceinline__ Ring<TY, S> ring_setup(uint64_t* mbar)
+{
+    extern __shared__ __align__(128) float smraw[];
+    Ring<TY, S> r;
+    r.U = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+    r.B = r.U + 6 * Geo<TY, S>::PLANE;
+    r.mb[0] = (unsigned)__cvta_generic_to_shared(&mbar[0]);
+    r.mb[1] = (unsigned)__cvta_generic_to_shared(&mbar[1]);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb[0]) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb[1]) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    return r;
+}
+
+// Wait until buffer b holds its tile.  false: a TMA wait ran out (ERR_BIT_TIMEOUT set, the
+// copies in flight drained with a bound): the whole CTA must leave.
+template <int TY, int S>
+__device__ __forceinline__ bool ring_wait(Ring<TY, S>& r, int b, int cap, int* err)
+{
+    if (r.tma[b]) {
+        const unsigned done = poll_phase(r.mb[b], r.phase[b], cap);
+        if (__syncthreads_or(!done)) {
+            if (threadIdx.x == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
+            poll_phase(r.mb[b], r.phase[b], 1 << 22);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            return false;
+        }
+        r.phase[b] ^= 1u;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    return true;
+}
+
+// Stage the window with corner (gx0, gy0) into buffer b: TMA for interior windows when maps are
+// given, else per-thread cp.async.  The buffer's last readers passed a barrier before this.
+template <int TY, int S>
+__device__ __forceinline__ void ring_issue(Ring<TY, S>& r, int b, const StepConst& k, int gx0, int gy0,
+                                           const float* phi0, const float* c0, const float* rho0,
+                                           const StepMaps* maps)
+{
+    constexpr int LY = Geo<TY, S>::LY;
+    r.tma[b] = maps && gx0 >= 0 && gx0 + LX <= k.nx && gy0 >= 0 && gy0 + LY <= k.ny;
+    if (r.tma[b]) {
+        if (threadIdx.x == 0) {
+            // order the generic-proxy reads of this buffer before the asynchronous-proxy writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_tma<TY, S>(maps, gx0, gy0, r.buf(b), r.mb[b]);
+        }
+    } else {
+        issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, r.buf(b));
+    }
+}
+
+// One step of one run over all its 56 x TY tiles (maps NULL: no TMA).
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, RING_MINB)
+step_kernel_ring(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
+                 const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
+                 float* __restrict__ rho1, const __grid_constant__ StepMaps maps, int use_maps, int* __restrict__ err)
+{
+    __shared__ __align__(8) uint64_t mbar[2];
+    Ring<TY, S> r = ring_setup<TY, S>(mbar);
+    const int ntx = (k.nx + TXO - 1) / TXO, ntiles = ntx * ((k.ny + TY - 1) / TY);
+    const StepMaps* mp = use_maps ? &maps : nullptr;
+    auto corner = [&](int t, int& gx0, int& gy0) {
+        const int ty = t / ntx;
+        gx0 = (t - ty * ntx) * TXO - HALO;
+        gy0 = ty * TY - HALO;
+    };
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    int t = blockIdx.x, gx0, gy0;
+    if (t < ntiles) {
+        corner(t, gx0, gy0);
+        ring_issue<TY, S>(r, 0, k, gx0, gy0, phi0, c0, rho0, mp);
+    }
+#pragma unroll 2
+    for (int i = 0; t < ntiles; ++i) {
+        const int b = i & 1;
+        if (!ring_wait<TY, S>(r, b, k.wait_cap, err)) return;
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) {
+            int nx0, ny0;
+            corner(tn, nx0, ny0);
+            ring_issue<TY, S>(r, b ^ 1, k, nx0, ny0, phi0, c0, rho0, mp);
+        } else {
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        }
+        corner(t, gx0, gy0);
+        compute_tile<TY, S, PHI_MODE, MOB>(k, gx0, gy0, r.buf(b), r.B, phi1, c1, rho1);
+        __syncthreads();
+        t = tn;
+    }
+}
+
+// One step of every run of an ensemble over its tile table (per-thread staging only).
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, RING_MINB)
+ens_step_kernel_ring(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ runs, int ntiles, int parity)
+{
+    __shared__ __align__(8) uint64_t mbar[2];
+    Ring<TY, S> r = ring_setup<TY, S>(mbar);
+    const int a = parity;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    int t = blockIdx.x;
+    if (t < ntiles) {
+        const EnsTile e = tiles[t];
+        const EnsRun& run = runs[e.run];
+        ring_issue<TY, S>(r, 0, run.k, e.x0 - HALO, e.y0 - HALO, run.f[a][0], run.f[a][1], run.f[a][2], nullptr);
+    }
+#pragma unroll 2
+    for (int i = 0; t < ntiles; ++i) {
+        const int b = i & 1;
+        ring_wait<TY, S>(r, b, 0, nullptr);  // per-thread copies only: no bounded TMA wait
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) {
+            const EnsTile e = tiles[tn];
+            const EnsRun& run = runs[e.run];
+            ring_issue<TY, S>(r, b ^ 1, run.k, e.x0 - HALO, e.y0 - HALO, run.f[a][0], run.f[a][1], run.f[a][2],
+                              nullptr);
+        } else {
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        }
+        const EnsTile e = tiles[t];
+        const EnsRun& run = runs[e.run];
+        compute_tile<TY, S, PHI_MODE, MOB>(run.k, e.x0 - HALO, e.y0 - HALO, r.buf(b), r.B, run.f[1 - a][0],
+                                           run.f[1 - a][1], run.f[1 - a][2]);
+        __syncthreads();
+        t = tn;
+    }
 }
 
 // Opt the kernel into its dynamic shared-memory size (once per kernel function).
@@ -581,6 +786,78 @@ cudaError_t launch_ens_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, i
     return cudaLaunchKernelEx(&cfg, kern, tiles, runs, parity);
 }
 
+// Grid of a persistent kernel: as many CTAs as are resident at once (at most `ntiles`).
+template <class Kern>
+cudaError_t ring_grid(Kern kern, int threads, size_t smem, int ntiles, int& grid)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long g = (long long)sms * per_sm;
+    grid = (int)(g < ntiles ? g : ntiles);
+    return cudaSuccess;
+}
+
+template <class Kern>
+cudaError_t configure_ring(Kern kern, bool& configured, size_t smem)
+{
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+    }
+    return configure_smem(kern, configured, smem);
+}
+
+template <int PHI_MODE, int MOB>
+cudaError_t launch_ring_t(const StepConst& k, const float* f0, const float* c0, const float* r0, float* f1,
+                          float* c1, float* r1, cudaStream_t s, const StepMaps* maps, int* err)
+{
+    constexpr int TY = PF_LARGE_TY, S = PF_LARGE_S;
+    using G = Geo<TY, S>;
+    auto kern = step_kernel_ring<TY, S, PHI_MODE, MOB>;
+    static bool configured = false;
+    static int grid_cache = 0;
+    static int ntiles_cache = -1;
+    const size_t smem = RingGeo<TY, S>::BYTES;
+    cudaError_t e = configure_ring(kern, configured, smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = ((k.nx + TXO - 1) / TXO) * ((k.ny + TY - 1) / TY);
+    if (ntiles != ntiles_cache) {
+        e = ring_grid(kern, G::THREADS, smem, ntiles, grid_cache);
+        if (e != cudaSuccess) return e;
+        ntiles_cache = ntiles;
+    }
+    StepMaps none = {};
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_config(dim3(grid_cache), G::THREADS, smem, s, attr);
+    return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1, maps ? *maps : none, maps ? 1 : 0, err);
+}
+
+template <int PHI_MODE, int MOB>
+cudaError_t launch_ens_ring_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, int parity, cudaStream_t s)
+{
+    constexpr int TY = PF_LARGE_TY, S = PF_LARGE_S;
+    using G = Geo<TY, S>;
+    auto kern = ens_step_kernel_ring<TY, S, PHI_MODE, MOB>;
+    static bool configured = false;
+    static int grid_cache = 0;
+    static int ntiles_cache = -1;
+    const size_t smem = RingGeo<TY, S>::BYTES;
+    cudaError_t e = configure_ring(kern, configured, smem);
+    if (e != cudaSuccess) return e;
+    if (ntiles != ntiles_cache) {
+        e = ring_grid(kern, G::THREADS, smem, ntiles, grid_cache);
+        if (e != cudaSuccess) return e;
+        ntiles_cache = ntiles;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_config(dim3(grid_cache), G::THREADS, smem, s, attr);
+    return cudaLaunchKernelEx(&cfg, kern, tiles, runs, ntiles, parity);
+}
+
 template <int TY, int S>
 cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
@@ -625,6 +902,8 @@ int tile_height(int tile)
     return tile == TILE_SMALL ? PF_SMALL_TY : (tile == TILE_MEDIUM ? PF_MEDIUM_TY : PF_LARGE_TY);
 }
 
+int tile_table(int tile) { return tile == TILE_LARGE_RING ? TILE_LARGE : tile; }
+
 size_t step_smem_bytes(int tile)
 {
     if (tile == TILE_SMALL) return Geo<PF_SMALL_TY, PF_SMALL_S>::BYTES;
@@ -641,6 +920,20 @@ cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob, con
     if (tile == TILE_MEDIUM)
         return launch_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s, maps, err);
     return launch_tile<PF_LARGE_TY, PF_LARGE_S>(k, phi_mode, mob, f0, c0, r0, f1, c1, r1, s, maps, err);
+}
+
+cudaError_t launch_step_ring(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
+                             const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
+                             int* err)
+{
+    if (phi_mode == 0) {
+        if (mob == MOB_UNIFORM) return launch_ring_t<0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+        if (mob == MOB_BULK) return launch_ring_t<0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+        return launch_ring_t<0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    }
+    if (mob == MOB_UNIFORM) return launch_ring_t<1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    if (mob == MOB_BULK) return launch_ring_t<1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    return launch_ring_t<1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
 }
 
 cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
@@ -661,6 +954,16 @@ cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tile
                             int parity, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
+    if (tile == TILE_LARGE_RING) {
+        if (phi_mode == 0) {
+            if (mob == MOB_UNIFORM) return launch_ens_ring_t<0, MOB_UNIFORM>(tiles, runs, ntiles, parity, s);
+            if (mob == MOB_BULK) return launch_ens_ring_t<0, MOB_BULK>(tiles, runs, ntiles, parity, s);
+            return launch_ens_ring_t<0, MOB_SURF>(tiles, runs, ntiles, parity, s);
+        }
+        if (mob == MOB_UNIFORM) return launch_ens_ring_t<1, MOB_UNIFORM>(tiles, runs, ntiles, parity, s);
+        if (mob == MOB_BULK) return launch_ens_ring_t<1, MOB_BULK>(tiles, runs, ntiles, parity, s);
+        return launch_ens_ring_t<1, MOB_SURF>(tiles, runs, ntiles, parity, s);
+    }
     if (tile == TILE_SMALL)
         return launch_ens_tile<PF_SMALL_TY, PF_SMALL_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
     if (tile == TILE_MEDIUM)

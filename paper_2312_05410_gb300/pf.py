@@ -76,6 +76,7 @@ def _load():
     L.pf_clear_error.argtypes, L.pf_clear_error.restype = [vp], C.c_int
     L.pf_set_wait_limit.argtypes, L.pf_set_wait_limit.restype = [vp, C.c_int], C.c_int
     L.pf_staging_mode.argtypes, L.pf_staging_mode.restype = [vp], C.c_int
+    L.pf_set_tile_loop.argtypes, L.pf_set_tile_loop.restype = [vp, C.c_int], C.c_int
     L.pf_destroy.argtypes, L.pf_destroy.restype = [vp], C.c_int
     L.pf_diag_workspace_size.argtypes, L.pf_diag_workspace_size.restype = [C.c_int, C.c_int], sz
     L.pf_diag_error_offset.argtypes, L.pf_diag_error_offset.restype = [C.c_int, C.c_int], sz
@@ -210,6 +211,10 @@ def pf_staging_mode(h) -> int:
     return int(lib.pf_staging_mode(h))
 
 
+def pf_set_tile_loop(h, on: bool) -> int:
+    return int(lib.pf_set_tile_loop(h, 1 if on else 0))
+
+
 def pf_destroy(h) -> int:
     return lib.pf_destroy(h)
 
@@ -249,19 +254,30 @@ class Sim:
     torch's current stream).
     """
 
-    def __init__(self, params: dict, phi, c, rho, history_rows: int = 256, stream=None, device="cuda"):
+    def __init__(self, params: dict, phi, c, rho, history_rows: int = 256, stream=None, device="cuda", nx=None):
+        """phi, c, rho: (ny, nx) arrays, or CUDA tensors (ny, >= nx) whose first nx columns (default: all)
+        are the state; tensors are copied device to device on the launch stream."""
         import torch
 
-        phi, c, rho = (np.asarray(a, dtype=np.float32) for a in (phi, c, rho))
-        ny, nx = phi.shape
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        on_device = all(isinstance(a, torch.Tensor) and a.is_cuda for a in (phi, c, rho))
+        if not on_device:
+            phi, c, rho = (np.asarray(a, dtype=np.float32) for a in (phi, c, rho))
+        ny = phi.shape[0]
+        nx = int(nx) if nx is not None else phi.shape[1]
         self.nx, self.ny, self.pitch = nx, ny, padded_pitch(nx)
         self.params = dict(params)
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.fields = []
-        for a in (phi, c, rho):
-            t = torch.zeros((ny, self.pitch), dtype=torch.float32, device=device)
-            t[:, :nx] = torch.from_numpy(a).to(device)
-            self.fields.append(t)
+        # the fields are filled on the launch stream, after whatever the caller's stream has queued
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            for a in (phi, c, rho):
+                t = torch.zeros((ny, self.pitch), dtype=torch.float32, device=device)
+                if on_device:
+                    t[:, :nx].copy_(a[:, :nx])
+                else:
+                    t[:, :nx] = torch.from_numpy(a).to(device)
+                self.fields.append(t)
         self.phi, self.c, self.rho = self.fields
         nbytes = pf_workspace_size(nx, ny, self.pitch, history_rows)
         if nbytes == 0:
@@ -270,7 +286,6 @@ class Sim:
         base = self.work.data_ptr()
         self._work_ptr = (base + 255) // 256 * 256
         self._work_bytes = nbytes
-        torch.cuda.synchronize()
         rc, h = pf_init(self.params, nx, ny, self.pitch, self.phi.data_ptr(), self.c.data_ptr(),
                         self.rho.data_ptr(), self._work_ptr, nbytes, history_rows, self.stream.cuda_stream)
         _check(rc)
@@ -364,7 +379,7 @@ class Ensemble:
 
     def autotune(self, trial_steps: int = 20):
         chosen = C.c_int(-1)
-        secs = (C.c_double * 3)()
+        secs = (C.c_double * 4)()
         self._check(lib.pf_ens_autotune(self.h, int(trial_steps), C.byref(chosen), secs))
         return chosen.value, list(secs)
 
@@ -436,7 +451,8 @@ def adjoint(params: dict, init, nx: int, nsteps: int, K: int, w_phi, w_c, w_rho=
     g = [torch.zeros_like(phi0) for _ in range(3)]
     fin = [torch.zeros_like(phi0) for _ in range(3)]
     gp = (C.c_double * 3)()
-    torch.cuda.synchronize()
+    # the inputs and the zeroed outputs were written on the caller's stream: order the call after them
+    stream.wait_stream(torch.cuda.current_stream())
     rc = lib.pf_adjoint(C.byref(Params.from_dict(params)), nx, ny, pitch, phi0.data_ptr(), c0.data_ptr(),
                         rho0.data_ptr(), int(nsteps), int(K), w_phi.data_ptr(), w_c.data_ptr(),
                         None if w_rho is None else w_rho.data_ptr(), g[0].data_ptr(), g[1].data_ptr(),
@@ -468,8 +484,10 @@ def make_run_function():
         @staticmethod
         def forward(ctx, v_mag, m_scale, kappa_c, phi0, c0, rho0, params, nx, nsteps, K):
             q = _scaled(params, float(v_mag), float(m_scale), float(kappa_c))
-            sim = Sim(q, *(t[:, :nx].detach().cpu().numpy() for t in (phi0, c0, rho0)), history_rows=1)
+            # the given device tensors are bound by a device-to-device copy (no host round trip)
+            sim = Sim(q, phi0.detach(), c0.detach(), rho0.detach(), history_rows=1, nx=nx)
             sim.step(int(nsteps))
+            torch.cuda.current_stream().wait_stream(sim.stream)
             out = tuple(t.clone() for t in sim.fields)
             sim.close()
             ctx.save_for_backward(v_mag, m_scale, kappa_c, phi0, c0, rho0)

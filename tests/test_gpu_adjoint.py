@@ -123,3 +123,27 @@ def test_autograd_function_gives_the_adjoint_gradients(pf):
     assert float(m.grad) == pytest.approx(res["m_scale"], rel=1e-12)
     assert float(kc.grad) == pytest.approx(res["kappa_c"], rel=1e-12)
     assert torch.equal(init[1].grad, res["c0"])
+
+
+def test_autograd_forward_binds_the_device_tensors(pf, monkeypatch):
+    """The forward copies the given CUDA tensors device to device: with host copies of tensors made
+    impossible it still runs, and its final state equals a run started from host arrays bit for bit."""
+    p, st, _ = case(nx=40, ny=24)
+    ny, nx = st[0].shape
+    PFRun = pf.make_run_function()
+    init = pf.device_fields(st)
+
+    def no_host_copy(*a, **k):
+        raise AssertionError("device-to-host copy in the forward")
+
+    monkeypatch.setattr(torch.Tensor, "cpu", no_host_copy)
+    monkeypatch.setattr(torch.Tensor, "numpy", no_host_copy)
+    v = torch.tensor(p["v_mag"], dtype=torch.float64)
+    out = PFRun.apply(v, torch.tensor(1.0, dtype=torch.float64), torch.tensor(p["kappa_c"], dtype=torch.float64),
+                      *init, p, nx, 25, 10)
+    monkeypatch.undo()
+    sim = pf.Sim(p, *st, history_rows=1)
+    sim.step(25)
+    for a, b in zip(out, sim.fields):
+        assert torch.equal(a[:, :nx], b[:, :nx])
+    sim.close()

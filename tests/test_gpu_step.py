@@ -209,13 +209,16 @@ def test_nonfinite_is_reported(pf):
     sim.close()
 
 
-def test_staging_wait_timeout_is_reported_and_recoverable(pf):
+@pytest.mark.parametrize("loop", [1, 0])
+def test_staging_wait_timeout_is_reported_and_recoverable(pf, loop):
     """A bounded TMA wait that runs out (limit of zero polls) sets the error word; pf_diag reports
-    PF_ERR_TIMEOUT, the context stays usable, and with the default limit the run is correct again."""
+    PF_ERR_TIMEOUT, the context stays usable, and with the default limit the run is correct again.
+    Both the persistent tile loop (loop = 1) and one CTA per tile (loop = 0)."""
     p = O.with_dt(I.default_params())
     state = I.film_state(I.FilmSpec(1120, 960, 16.0, seed=4), p)  # above 2^20 cells: TMA-staged tiles
     sim = pf.Sim(p, *state)
     assert pf.pf_staging_mode(sim.h) == 1
+    assert pf.pf_set_tile_loop(sim.h, loop) == 1
     assert pf.pf_set_wait_limit(sim.h, 0) == 0
     sim.step(1)
     rc, _ = pf.pf_diag(sim.h)
@@ -230,6 +233,32 @@ def test_staging_wait_timeout_is_reported_and_recoverable(pf):
     got = sim.numpy()
     sim.close()
     assert max_err(got, O.step(p, *state, 10)) <= 1e-5
+
+
+@pytest.mark.parametrize("nx,ny", [(1100, 1000), (1101, 960), (1456, 744)])
+def test_tile_loop_equals_one_cta_per_tile_bitwise(pf, nx, ny):
+    """The persistent tile loop (next tile staged while one computes; TMA for interior tiles, cp.async or,
+    for nx % 4 != 0, plain loads for the rest) runs the same per-tile arithmetic as one CTA per tile:
+    identical fields after 603 steps, through single launches and graph replays alike."""
+    p = O.with_dt(I.default_params(v_angle_deg=80.0))
+    state = I.film_state(I.FilmSpec(nx, ny, 30.0, seed=nx + ny), p)
+    out = []
+    for loop in (1, 0):
+        sim = pf.Sim(p, *state, history_rows=1)
+        assert pf.pf_set_tile_loop(sim.h, loop) == 1
+        sim.step(3)
+        sim.step(600)
+        out.append(sim.numpy())
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+def test_tile_loop_is_refused_on_small_grids(pf):
+    p = O.with_dt(I.default_params())
+    sim = pf.Sim(p, *I.film_state(I.FilmSpec(512, 512, 16.0, seed=1), p), history_rows=1)
+    assert pf.pf_set_tile_loop(sim.h, 1) == pf.PF_ERR_ARG
+    sim.close()
 
 
 def test_standalone_diagnostics_entry_point(pf):
