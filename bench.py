@@ -526,8 +526,13 @@ def run_native(args):
     barrier()
     # max time over ranks and the cell-updates of all ranks (independent replicas)
     total_s, all_units = aggregate(sum(run_ms) / 1e3, cells * nsteps * args.steps, device="cuda")
-    final_diag = R.final_diag()
     launches = R.launches
+    hybrid = None
+    if kind == "hybrid":  # errors need the plain-DNS run of the same batch, timed in the same loop
+        hybrid = hybrid_block(R.pair, time_hybrid_against_dns(R.pair, args.steps, 1, flush), peaks)
+        final_diag = dict(hybrid["rel_l2_vs_dns"], s2=hybrid["s2_rel_l2_vs_dns"])
+    else:
+        final_diag = R.final_diag()
 
     # ---- end to end through the public API with host buffers (pinned H2D + D2H inside)
     host_in = [torch.from_numpy(np.ascontiguousarray(t.cpu().numpy())).pin_memory() for t in init]
@@ -550,9 +555,6 @@ def run_native(args):
     e2e_s, _ = aggregate(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, 0.0, device="cuda")
     io_bytes = sum(h.numel() * h.element_size() for h in host_in)
 
-    hybrid = None
-    if kind == "hybrid":
-        hybrid = hybrid_block(R.pair, time_hybrid_against_dns(R.pair, args.steps, 1, flush), peaks)
     R.close()
     extras = {}
     if ws == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_extras:

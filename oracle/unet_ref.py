@@ -39,12 +39,15 @@ stretch that precedes a jump.
 Weights come from ``paper_2312_05410_gb300.inputs.unet_weights`` (seeded numbers,
 no arithmetic of the method).
 
-Precision model of the GPU path that this mirrors: inputs, weights and every
-stored activation are BF16 (round to nearest even); products are exact and sums
-are kept in high precision (FP64 here, FP32 on the GPU); group statistics are
-taken from the unrounded convolution outputs; GN + GELU are evaluated in high
-precision on the rounded stored values.  ``bf16`` below is written from the
-format definition (1 sign, 8 exponent, 7 fraction bits), not taken from a library.
+Precision model of the GPU path that this mirrors: the first convolution reads the
+FP32 fields and frames with FP32 weights (the composition fluctuations that seed the
+spinodal pattern are about 0.01 on c ~ 0.5, a few BF16 units, so BF16 inputs would
+quantize them away); every other weight and every stored activation is BF16 (round to
+nearest even); products are exact and sums are kept in high precision (FP64 here, FP32
+on the GPU); group statistics are taken from the unrounded convolution outputs; GN +
+GELU are evaluated in high precision on the rounded stored values.  ``bf16`` below is
+written from the format definition (1 sign, 8 exponent, 7 fraction bits), not taken
+from a library.
 """
 from __future__ import annotations
 
@@ -100,9 +103,11 @@ def scales(W: dict, tau: float) -> list[np.ndarray]:
     return [W[f"proj{p}"].astype(np.float64) @ f for p in range(1, 5)]
 
 
-def conv3x3(x: torch.Tensor, w) -> torch.Tensor:
-    """Zero-padded 'same' 3x3 cross-correlation of NCHW x with w [Cout, Cin, 3, 3] (BF16 weights)."""
-    return F.conv2d(x, _t(bf16(w)), padding=1)
+def conv3x3(x: torch.Tensor, w, weights_bf16: bool = True) -> torch.Tensor:
+    """Zero-padded 'same' 3x3 cross-correlation of NCHW x with w [Cout, Cin, 3, 3] (BF16 weights, or the
+    FP32 weights as given)."""
+    wt = bf16(w) if weights_bf16 else np.asarray(w, dtype=np.float32).astype(np.float64)
+    return F.conv2d(x, _t(wt), padding=1)
 
 
 def group_stats(y: torch.Tensor, groups: int):
@@ -125,9 +130,10 @@ def gelu(u: torch.Tensor) -> torch.Tensor:
     return 0.5 * u * (1.0 + torch.tanh(math.sqrt(2.0 / math.pi) * (u + 0.044715 * u ** 3)))
 
 
-def block(x: torch.Tensor, W: dict, name: str, groups: int = GROUPS, act: bool = True) -> torch.Tensor:
+def block(x: torch.Tensor, W: dict, name: str, groups: int = GROUPS, act: bool = True,
+          weights_bf16: bool = True) -> torch.Tensor:
     """conv -> (stats of the unrounded output) -> BF16 store -> GN -> GELU -> BF16 store."""
-    y = conv3x3(x, W[name])
+    y = conv3x3(x, W[name], weights_bf16)
     mean, var = group_stats(y, groups)
     y = group_norm(_rb(y), mean, var, W[name + "_gamma"], W[name + "_beta"], groups)
     return _rb(gelu(y)) if act else y
@@ -143,13 +149,13 @@ def up(x: torch.Tensor, w) -> torch.Tensor:
 
 def forward(W: dict, x, tau: float, taps: dict | None = None) -> np.ndarray:
     """Network output for x [N, 10, H, W] (3 frames of phi, c, rho, oldest first, then the dt plane;
-    rounded to BF16 here); returns [N, 3, H, W] FP64: the newest frame plus the increments.
+    rounded to FP32 here); returns [N, 3, H, W] FP64: the newest frame plus the increments.
     If `taps` is a dict it receives the intermediate tensors by name."""
     newest = 3 * (LB - 1)
     x_fields = _t(np.asarray(x, dtype=np.float32)[:, newest:newest + OUT_CH])  # the residual adds the newest frame
-    x = _rb(_t(x))
+    x = _t(np.asarray(x, dtype=np.float32))        # the first convolution reads the FP32 fields
     s = [_t(bf16(v)) for v in scales(W, tau)]     # conditioning factors are stored as BF16
-    z1 = block(x, W, "enc1")
+    z1 = block(x, W, "enc1", weights_bf16=False)
     z2 = block(down(z1), W, "enc2")
     z3 = block(down(z2), W, "enc3")
     z4 = block(down(z3), W, "enc4")

@@ -145,7 +145,7 @@ UnetLayout unet_layout(int n, int h, int w)
     L.err = take(sizeof(int));
     L.ptrs = take(sizeof(float*) * 3 * (size_t)n);
     L.flags = take(sizeof(int) * (size_t)n);
-    L.ring = take(2 * (size_t)(pf::UNET_LB - 1) * n * 3 * h * w);  // look-back frames, BF16 [slot][n][3][h][w]
+    L.ring = take(sizeof(float) * (pf::UNET_LB - 1) * (size_t)n * 3 * h * w);  // look-back frames, FP32 [slot][n][3][h][w]
     L.fptrs = take(sizeof(float*) * 3 * (size_t)n);
     L.total = off;
     return L;
@@ -282,12 +282,12 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
     }
     std::vector<double> proj;
     for (int p = 0; p < 4; ++p) proj.insert(proj.end(), weights[6 + p], weights[6 + p] + (size_t)CH[p] * 128);
-    // first conv [32][UNET_IN][3][3] -> [(ky,kx,ci)][co], BF16 values
+    // first conv [32][UNET_IN][3][3] -> [(ky,kx,ci)][co], FP32 (this layer runs in FP32 on the CUDA cores)
     constexpr int CI = pf::UNET_IN;
     std::vector<float> win(9 * CI * 32);
     for (int co = 0; co < 32; ++co)
         for (int ci = 0; ci < CI; ++ci)
-            for (int t = 0; t < 9; ++t) win[(t * CI + ci) * 32 + co] = host_rbf(weights[10][((co * CI + ci) * 9) + t]);
+            for (int t = 0; t < 9; ++t) win[(t * CI + ci) * 32 + co] = weights[10][((co * CI + ci) * 9) + t];
     // last conv [3][32][3][3] -> [tap][16][32] BF16 (output columns 3..15 zero)
     std::vector<uint16_t> wout(9 * 16 * 32, 0);
     for (int co = 0; co < 3; ++co)
@@ -381,9 +381,9 @@ int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* c
     // look-back frames: the oldest and the middle one (a missing frame is the oldest one held, or the
     // current fields when none is)
     const size_t frame_elems = (size_t)n * 3 * H * W;
-    const uint16_t* ring = u->at<uint16_t>(L.ring);
-    const uint16_t* newest = u->frames > 0 ? ring + (size_t)u->newest * frame_elems : nullptr;
-    const uint16_t* older = u->frames > 1 ? ring + (size_t)(1 - u->newest) * frame_elems : newest;
+    const float* ring = u->at<float>(L.ring);
+    const float* newest = u->frames > 0 ? ring + (size_t)u->newest * frame_elems : nullptr;
+    const float* older = u->frames > 1 ? ring + (size_t)(1 - u->newest) * frame_elems : newest;
     ck(pf::launch_in_conv(dp, dp + n, dp + 2 * n, pitch, older, newest, n, H, W, (float)tau, u->at<float>(L.win),
                           act(A_PRE1), part, s),
        "input conv");
@@ -453,7 +453,7 @@ int pf_unet_frame(pf_unet* u, int n, const float* const* phi, const float* const
     const int slot = u->frames == 0 ? 0 : 1 - u->newest;  // overwrite the oldest frame held
     const size_t frame_elems = (size_t)n * 3 * u->h * u->w;
     e = pf::launch_frame(dp, dp + n, dp + 2 * n, pitch, n, u->h, u->w,
-                         u->at<uint16_t>(u->L.ring) + (size_t)slot * frame_elems, u->stream);
+                         u->at<float>(u->L.ring) + (size_t)slot * frame_elems, u->stream);
     if (e != cudaSuccess) return ufail(PF_ERR_CUDA, "frame: %s", cudaGetErrorString(e));
     u->newest = slot;
     if (u->frames < pf::UNET_LB - 1) ++u->frames;

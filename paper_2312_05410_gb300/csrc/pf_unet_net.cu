@@ -98,9 +98,11 @@ __device__ __forceinline__ void unpack8(const uint4 v, float* f)
 }
 
 // First convolution over the look-back input, 3x3, 10 -> 32, zero padding outside the image:
-// x = BF16 of (phi, c, rho) of the oldest frame, of the middle frame, of the current fields, then
-// the tau plane.  The two older frames are BF16 planes [image][3][h][w] (old0, old1; either may be
-// NULL: that frame is the current fields, the history of a run that has none yet).
+// x = (phi, c, rho) of the oldest frame, of the middle frame, of the current fields, then the tau
+// plane, all in FP32 with FP32 weights (the composition fluctuations that seed the spinodal pattern
+// are about 0.01 on c ~ 0.5, a few BF16 units: BF16 inputs would quantize them away).  The two
+// older frames are FP32 planes [image][3][h][w] (old0, old1; either may be NULL: that frame is the
+// current fields, the history of a run that has none yet).  The output is stored as BF16.
 // A block covers two consecutive 128-pixel tiles of one image; thread t computes pixel t of each
 // (neighbours come through L1: staging the halo in shared memory measured slower).  The 32 outputs
 // are 16 pairs updated by packed FP32x2 FMAs, and each weight pair read from shared memory serves
@@ -109,8 +111,8 @@ constexpr int IN_CH = UNET_IN;
 static_assert(IN_CH == 10, "three frames of (phi, c, rho) and the tau plane");
 __global__ void __launch_bounds__(TPB)
 in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
-               const float* const* __restrict__ rho, int pitch, const uint16_t* __restrict__ old0,
-               const uint16_t* __restrict__ old1, int h, int w, float tau,
+               const float* const* __restrict__ rho, int pitch, const float* __restrict__ old0,
+               const float* __restrict__ old1, int h, int w, float tau,
                const float* __restrict__ wgt /* [9 * IN_CH][32]: (ky,kx,ci) x co */, uint16_t* __restrict__ out,
                float* __restrict__ partials)
 {
@@ -126,9 +128,9 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     const float* C = c[img];
     const float* Rh = rho[img];
     const size_t plane = (size_t)h * w;
-    const uint16_t* O0 = old0 ? old0 + (size_t)img * 3 * plane : nullptr;
-    const uint16_t* O1 = old1 ? old1 + (size_t)img * 3 * plane : nullptr;
-    const float tb = rbf(tau);
+    const float* O0 = old0 ? old0 + (size_t)img * 3 * plane : nullptr;
+    const float* O1 = old1 ? old1 + (size_t)img * 3 * plane : nullptr;
+    const float tb = tau;
     int y[2], x[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -150,14 +152,14 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
                 const bool in = (k == 0 || two) && yy >= 0 && yy < h && xx >= 0 && xx < w;
                 const size_t o = in ? (size_t)yy * pitch + xx : 0;
                 const size_t ob = in ? (size_t)yy * w + xx : 0;
-                const float f0 = in ? rbf(F[o]) : 0.f, f1 = in ? rbf(C[o]) : 0.f, f2 = in ? rbf(Rh[o]) : 0.f;
+                const float f0 = in ? F[o] : 0.f, f1 = in ? C[o] : 0.f, f2 = in ? Rh[o] : 0.f;
                 v[k][6] = f0;
                 v[k][7] = f1;
                 v[k][8] = f2;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    v[k][q] = in ? (O0 ? bf(O0[q * plane + ob]) : v[k][6 + q]) : 0.f;
-                    v[k][3 + q] = in ? (O1 ? bf(O1[q * plane + ob]) : v[k][6 + q]) : 0.f;
+                    v[k][q] = in ? (O0 ? O0[q * plane + ob] : v[k][6 + q]) : 0.f;
+                    v[k][3 + q] = in ? (O1 ? O1[q * plane + ob] : v[k][6 + q]) : 0.f;
                 }
                 v[k][9] = in ? tb : 0.f;
             }
@@ -209,11 +211,11 @@ in_conv_kernel(const float* const* __restrict__ phi, const float* const* __restr
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// One look-back frame: the FP32 fields (row pitch `pitch`) of every image rounded to BF16 planes
-// [image][3][h][w] (the rounding the first convolution applies to its inputs).
+// One look-back frame: the FP32 fields (row pitch `pitch`) of every image copied to dense FP32
+// planes [image][3][h][w].
 __global__ void frame_kernel(const float* const* __restrict__ phi, const float* const* __restrict__ c,
                              const float* const* __restrict__ rho, int pitch, int n, int h, int w,
-                             uint16_t* __restrict__ dst)
+                             float* __restrict__ dst)
 {
     const size_t plane = (size_t)h * w, total = (size_t)n * 3 * plane;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -223,7 +225,7 @@ __global__ void frame_kernel(const float* const* __restrict__ phi, const float* 
         const size_t pix = r - (size_t)q * plane;
         const int yy = (int)(pix / w), xx = (int)(pix - (size_t)yy * w);
         const float* src = q == 0 ? phi[img] : (q == 1 ? c[img] : rho[img]);
-        dst[i] = to_bf(src[(size_t)yy * pitch + xx]);
+        dst[i] = src[(size_t)yy * pitch + xx];
     }
 }
 
@@ -432,7 +434,7 @@ cudaError_t launch_cond(const double* mlp, const double* proj, double tau, float
 }
 
 cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const float* const* rho, int pitch,
-                           const uint16_t* old0, const uint16_t* old1, int n, int h, int w, float tau,
+                           const float* old0, const float* old1, int n, int h, int w, float tau,
                            const float* wgt, uint16_t* out, float* partials, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
@@ -441,7 +443,7 @@ cudaError_t launch_in_conv(const float* const* phi, const float* const* c, const
 }
 
 cudaError_t launch_frame(const float* const* phi, const float* const* c, const float* const* rho, int pitch, int n,
-                         int h, int w, uint16_t* dst, cudaStream_t s)
+                         int h, int w, float* dst, cudaStream_t s)
 {
     const size_t total = (size_t)n * 3 * h * w;
     const unsigned blocks = (unsigned)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);

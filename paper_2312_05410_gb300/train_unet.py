@@ -76,8 +76,12 @@ def make_model(seed: int = 0):
             W["out_beta"] = np.zeros(I.UNET_OUT, np.float32)
             self.p = torch.nn.ParameterDict({k: torch.nn.Parameter(torch.from_numpy(v.copy())) for k, v in W.items()})
 
-        def block(self, x, name):
-            y = F.conv2d(x, self.p[name], padding=1)
+        def block(self, x, name, fp32=False):
+            if fp32:  # the first convolution reads the FP32 fields with FP32 weights, as the kernel does
+                with torch.autocast("cuda", enabled=False):
+                    y = F.conv2d(x.float(), self.p[name].float(), padding=1)
+            else:
+                y = F.conv2d(x, self.p[name], padding=1)
             y = F.group_norm(y, 8, self.p[name + "_gamma"], self.p[name + "_beta"], eps=1e-5)
             return F.gelu(y, approximate="tanh")
 
@@ -88,7 +92,7 @@ def make_model(seed: int = 0):
             h = torch.sin(h @ p["mlp_w1"].t() + p["mlp_b1"])
             f = (h @ p["mlp_w2"].t() + p["mlp_b2"])[0]
             s = [p[f"proj{k}"] @ f for k in range(1, 5)]
-            z1 = self.block(x, "enc1")
+            z1 = self.block(x, "enc1", fp32=True)
             z2 = self.block(F.max_pool2d(z1, 2), "enc2")
             z3 = self.block(F.max_pool2d(z2, 2), "enc3")
             z4 = self.block(F.max_pool2d(z3, 2), "enc4")
