@@ -156,6 +156,18 @@ int pf_staging_mode(const pf_handle* h);
  * or PF_ERR_ARG for a smaller grid or a null handle. */
 int pf_set_tile_loop(pf_handle* h, int on);
 
+/*
+ * Host-buffer state transfer (the end-to-end path of a caller whose fields live in
+ * host memory): pf_load_host copies host arrays phi, c, rho (ny rows of nx floats,
+ * row pitch host_pitch >= nx floats) into the handle's current state; pf_store_host
+ * copies the current state out to such arrays.  Asynchronous on the handle's stream
+ * (use page-locked host memory for a copy that overlaps; the host arrays must stay
+ * valid until the stream reaches the copy).  Call them between pf_step calls.
+ * Nothing is allocated.  PF_ERR_ARG on a null pointer, PF_ERR_LAYOUT on a pitch below nx.
+ */
+int pf_load_host(pf_handle* h, const float* phi, const float* c, const float* rho, int host_pitch);
+int pf_store_host(pf_handle* h, float* phi, float* c, float* rho, int host_pitch);
+
 /* Clear the sticky device error word (async). */
 int pf_clear_error(pf_handle* h);
 

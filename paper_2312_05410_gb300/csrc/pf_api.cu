@@ -225,6 +225,24 @@ int build_graph(pf_handle* h, long gsteps)
     return PF_OK;
 }
 
+// Copy the state between caller host arrays (row pitch host_pitch floats) and the handle's fields.
+int host_copy(pf_handle* h, float* const* host, int host_pitch, bool to_device)
+{
+    if (!h || !host || !host[0] || !host[1] || !host[2]) return fail(PF_ERR_ARG, "null pointer");
+    if (host_pitch < h->nx) return fail(PF_ERR_LAYOUT, "host pitch %d < nx %d", host_pitch, h->nx);
+    const size_t rowd = size_t(h->pitch) * sizeof(float), rowh = size_t(host_pitch) * sizeof(float);
+    const size_t width = size_t(h->nx) * sizeof(float);
+    for (int q = 0; q < 3; ++q) {
+        float* dev = h->u[h->cur][q];
+        cudaError_t e = to_device ? cudaMemcpy2DAsync(dev, rowd, host[q], rowh, width, h->ny, cudaMemcpyHostToDevice,
+                                                      h->stream)
+                                  : cudaMemcpy2DAsync(host[q], rowh, dev, rowd, width, h->ny, cudaMemcpyDeviceToHost,
+                                                      h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, to_device ? "host-to-device copy" : "device-to-host copy");
+    }
+    return PF_OK;
+}
+
 long graph_block(const pf_params* p)
 {
     if (p->diag_every <= 0) return 256;
@@ -473,6 +491,18 @@ int pf_set_tile_loop(pf_handle* h, int on)
     }
     h->ring = on != 0;
     return prev;
+}
+
+int pf_load_host(pf_handle* h, const float* phi, const float* c, const float* rho, int host_pitch)
+{
+    float* host[3] = {const_cast<float*>(phi), const_cast<float*>(c), const_cast<float*>(rho)};
+    return host_copy(h, host, host_pitch, true);
+}
+
+int pf_store_host(pf_handle* h, float* phi, float* c, float* rho, int host_pitch)
+{
+    float* host[3] = {phi, c, rho};
+    return host_copy(h, host, host_pitch, false);
 }
 
 int pf_clear_error(pf_handle* h)

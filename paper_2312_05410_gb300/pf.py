@@ -77,6 +77,8 @@ def _load():
     L.pf_set_wait_limit.argtypes, L.pf_set_wait_limit.restype = [vp, C.c_int], C.c_int
     L.pf_staging_mode.argtypes, L.pf_staging_mode.restype = [vp], C.c_int
     L.pf_set_tile_loop.argtypes, L.pf_set_tile_loop.restype = [vp, C.c_int], C.c_int
+    L.pf_load_host.argtypes, L.pf_load_host.restype = [vp, vp, vp, vp, C.c_int], C.c_int
+    L.pf_store_host.argtypes, L.pf_store_host.restype = [vp, vp, vp, vp, C.c_int], C.c_int
     L.pf_destroy.argtypes, L.pf_destroy.restype = [vp], C.c_int
     L.pf_diag_workspace_size.argtypes, L.pf_diag_workspace_size.restype = [C.c_int, C.c_int], sz
     L.pf_diag_error_offset.argtypes, L.pf_diag_error_offset.restype = [C.c_int, C.c_int], sz
@@ -308,6 +310,16 @@ class Sim:
 
     def set_step(self, step: int):
         _check(pf_set_step(self.h, step))
+
+    def load_host(self, phi, c, rho):
+        """pf_load_host: (ny, nx) float32 host arrays or CPU tensors (pinned for an overlapping copy)."""
+        ptr = [int(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data for a in (phi, c, rho)]
+        _check(lib.pf_load_host(self.h, *ptr, int(phi.shape[1])))
+
+    def store_host(self, phi, c, rho):
+        """pf_store_host into (ny, nx) float32 host arrays or CPU tensors."""
+        ptr = [int(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data for a in (phi, c, rho)]
+        _check(lib.pf_store_host(self.h, *ptr, int(phi.shape[1])))
 
     def numpy(self):
         """(phi, c, rho) of the current state as float32 numpy arrays (synchronises)."""

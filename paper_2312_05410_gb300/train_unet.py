@@ -139,13 +139,16 @@ def train(pf, runs: int = 200, budget_s: float = 1800.0, batch: int = 8, lr: flo
         return sum(((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(3))
 
     def validate():
-        tot, cnt = 0.0, 0
+        """Held-out relative squared error per field (phi, c, rho), one jump from DNS frames."""
+        num, den = torch.zeros(3), torch.zeros(3)
         with torch.no_grad(), torch.autocast("cuda", dtype=torch.bfloat16):
             for i in range(0, len(val), 16):
                 x, y = sample(val[i:i + 16])
-                tot += float(loss_fn(net(x, 1.0).float(), y)) * len(val[i:i + 16])
-                cnt += len(val[i:i + 16])
-        return tot / cnt / 3
+                pred = net(x, 1.0).float()
+                for q in range(3):
+                    num[q] += float(((pred[:, q] - y[:, q]) ** 2).sum())
+                    den[q] += float((y[:, q] ** 2).sum())
+        return (num / den).tolist()
 
     t0 = time.time()
     step = epoch = 0
@@ -168,8 +171,8 @@ def train(pf, runs: int = 200, budget_s: float = 1800.0, batch: int = 8, lr: flo
                 break
         epoch += 1
         v = validate()
-        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss) / 3:.3e} "
-            f"val rel-sq {v:.3e} (rel L2 {math.sqrt(v):.3e})")
+        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss.detach()) / 3:.3e} "
+            f"val rel L2 phi {math.sqrt(v[0]):.3e} c {math.sqrt(v[1]):.3e} rho {math.sqrt(v[2]):.3e}")
     return {k: v.detach().float().cpu().numpy() for k, v in net.p.items()}
 
 

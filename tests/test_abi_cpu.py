@@ -116,6 +116,19 @@ def test_static_diagnostics_error_paths_report_their_reason(pf):
         assert text in pf.last_error(), (text, pf.last_error())
 
 
+def test_new_entry_points_reject_null_handles_before_any_cuda_call(pf):
+    import ctypes as C
+    lib = pf.lib
+    assert lib.pf_hybrid_workspace_size(None) == 0
+    hp = pf.HybridParams(2000, 2000, 1000, 2000.0, -1.5, 1.5, -0.5, 1.5, -0.5, 1.5)
+    st = pf.HybridStats()
+    assert lib.pf_hybrid_run(None, None, C.byref(hp), 100, None, 0, C.byref(st)) == pf.PF_ERR_ARG
+    assert "null" in lib.pf_hybrid_last_error().decode()
+    assert lib.pf_unet_reset_frames(None) == pf.PF_ERR_ARG
+    assert lib.pf_unet_frame(None, 1, None, None, None, 256) == pf.PF_ERR_ARG
+    assert pf.pf_set_tile_loop(None, True) == pf.PF_ERR_ARG
+
+
 def _ens_init(pf, plist, shapes, work_bytes=None, ptr=FAKE):
     import ctypes as C
 

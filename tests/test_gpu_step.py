@@ -261,6 +261,34 @@ def test_tile_loop_is_refused_on_small_grids(pf):
     sim.close()
 
 
+def test_host_buffer_load_step_store(pf):
+    """pf_load_host / pf_step / pf_store_host with pinned host arrays: the same state as the device path,
+    bit for bit, and nothing outside the nx model columns of the host rows is touched."""
+    import torch
+
+    p = O.with_dt(I.default_params(v_angle_deg=60.0))
+    st = I.film_state(I.FilmSpec(150, 70, 20.0, seed=31), p)
+    other = I.film_state(I.FilmSpec(150, 70, 10.0, seed=32), p)
+    sim = pf.Sim(p, *other, history_rows=1)        # a different state, overwritten by the load
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in st]
+    host_out = [torch.full((70, 152), 7.0).pin_memory() for _ in range(3)]
+    sim.load_host(*host_in)
+    sim.step(40)
+    ptrs = [int(t.data_ptr()) for t in host_out]
+    assert pf.lib.pf_store_host(sim.h, *ptrs, 152) == 0
+    sim.stream.synchronize()
+    sim.close()
+    ref = pf.Sim(p, *st, history_rows=1)
+    ref.step(40)
+    want = ref.numpy()
+    ref.close()
+    for h, w in zip(host_out, want):
+        a = h.numpy()
+        assert np.array_equal(a[:, :150], w)
+        assert np.all(a[:, 150:] == 7.0)
+    assert pf.lib.pf_load_host(None, None, None, None, 150) == pf.PF_ERR_ARG
+
+
 def test_standalone_diagnostics_entry_point(pf):
     import torch
 
