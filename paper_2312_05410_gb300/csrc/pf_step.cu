@@ -556,15 +556,17 @@ struct RingGeo {
     static constexpr size_t BYTES = (size_t(9) * Geo<TY, S>::PLANE + Geo<TY, S>::GUARD) * sizeof(float) + 128;
 };
 
-// Ring state of one CTA: the staging buffers, their mbarriers and phases.
+// Ring state of one CTA: the staging buffers, their mbarriers (8 bytes apart) and, as bit masks
+// indexed by buffer, the phase each mbarrier waits for next and whether the buffer's tile came by
+// TMA (scalars rather than arrays: a runtime buffer index into an array would go through the stack).
 template <int TY, int S>
 struct Ring {
     float* U;  // buffer b at U + b * 3 PLANE
     float* B;  // u* and the guard rows
-    unsigned mb[2];
-    unsigned phase[2] = {0u, 0u};
-    bool tma[2] = {false, false};
+    unsigned mb0;
+    unsigned phase = 0u, tma = 0u;
     __device__ float* buf(int b) const { return U + b * 3 * Geo<TY, S>::PLANE; }
+    __device__ unsigned mb(int b) const { return mb0 + 8u * (unsigned)b; }
 };
 
 template <int TY, int S>
@@ -574,11 +576,10 @@ __device__ __forceinline__ Ring<TY, S> ring_setup(uint64_t* mbar)
     Ring<TY, S> r;
     r.U = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
     r.B = r.U + 6 * Geo<TY, S>::PLANE;
-    r.mb[0] = (unsigned)__cvta_generic_to_shared(&mbar[0]);
-    r.mb[1] = (unsigned)__cvta_generic_to_shared(&mbar[1]);
+    r.mb0 = (unsigned)__cvta_generic_to_shared(&mbar[0]);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb[0]) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb[1]) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb(0)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb(1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -590,15 +591,16 @@ __device__ __forceinline__ Ring<TY, S> ring_setup(uint64_t* mbar)
 template <int TY, int S>
 __device__ __forceinline__ bool ring_wait(Ring<TY, S>& r, int b, int cap, int* err)
 {
-    if (r.tma[b]) {
-        const unsigned done = poll_phase(r.mb[b], r.phase[b], cap);
+    if ((r.tma >> b) & 1u) {
+        const unsigned par = (r.phase >> b) & 1u;
+        const unsigned done = poll_phase(r.mb(b), par, cap);
         if (__syncthreads_or(!done)) {
             if (threadIdx.x == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
-            poll_phase(r.mb[b], r.phase[b], 1 << 22);
+            poll_phase(r.mb(b), par, 1 << 22);
             asm volatile("cp.async.wait_all;" ::: "memory");
             return false;
         }
-        r.phase[b] ^= 1u;
+        r.phase ^= 1u << b;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
@@ -613,12 +615,13 @@ __device__ __forceinline__ void ring_issue(Ring<TY, S>& r, int b, const StepCons
                                            const StepMaps* maps)
 {
     constexpr int LY = Geo<TY, S>::LY;
-    r.tma[b] = maps && gx0 >= 0 && gx0 + LX <= k.nx && gy0 >= 0 && gy0 + LY <= k.ny;
-    if (r.tma[b]) {
+    const bool by_tma = maps && gx0 >= 0 && gx0 + LX <= k.nx && gy0 >= 0 && gy0 + LY <= k.ny;
+    r.tma = by_tma ? (r.tma | (1u << b)) : (r.tma & ~(1u << b));
+    if (by_tma) {
         if (threadIdx.x == 0) {
             // order the generic-proxy reads of this buffer before the asynchronous-proxy writes
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tma<TY, S>(maps, gx0, gy0, r.buf(b), r.mb[b]);
+            issue_tma<TY, S>(maps, gx0, gy0, r.buf(b), r.mb(b));
         }
     } else {
         issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, r.buf(b));
@@ -647,7 +650,7 @@ step_kernel_ring(const StepConst k, const float* __restrict__ phi0, const float*
         corner(t, gx0, gy0);
         ring_issue<TY, S>(r, 0, k, gx0, gy0, phi0, c0, rho0, mp);
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int i = 0; t < ntiles; ++i) {
         const int b = i & 1;
         if (!ring_wait<TY, S>(r, b, k.wait_cap, err)) return;
@@ -681,7 +684,7 @@ ens_step_kernel_ring(const EnsTile* __restrict__ tiles, const EnsRun* __restrict
         const EnsRun& run = runs[e.run];
         ring_issue<TY, S>(r, 0, run.k, e.x0 - HALO, e.y0 - HALO, run.f[a][0], run.f[a][1], run.f[a][2], nullptr);
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int i = 0; t < ntiles; ++i) {
         const int b = i & 1;
         ring_wait<TY, S>(r, b, 0, nullptr);  // per-thread copies only: no bounded TMA wait
