@@ -218,7 +218,7 @@ def test_staging_wait_timeout_is_reported_and_recoverable(pf, loop):
     state = I.film_state(I.FilmSpec(1120, 960, 16.0, seed=4), p)  # above 2^20 cells: TMA-staged tiles
     sim = pf.Sim(p, *state)
     assert pf.pf_staging_mode(sim.h) == 1
-    assert pf.pf_set_tile_loop(sim.h, loop) == 1
+    assert pf.pf_set_tile_loop(sim.h, loop) == 0
     assert pf.pf_set_wait_limit(sim.h, 0) == 0
     sim.step(1)
     rc, _ = pf.pf_diag(sim.h)
@@ -245,7 +245,7 @@ def test_tile_loop_equals_one_cta_per_tile_bitwise(pf, nx, ny):
     out = []
     for loop in (1, 0):
         sim = pf.Sim(p, *state, history_rows=1)
-        assert pf.pf_set_tile_loop(sim.h, loop) == 1
+        assert pf.pf_set_tile_loop(sim.h, loop) == 0
         sim.step(3)
         sim.step(600)
         out.append(sim.numpy())
