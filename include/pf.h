@@ -149,6 +149,15 @@ int pf_set_wait_limit(pf_handle* h, int polls);
  * driver without tensor-map support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
 
+/* Steps per kernel launch: 1 (the default), or 2: a CTA stages a 64 x (TY + 16) window
+ * of the state once and runs both explicit midpoint steps on it in shared memory, writing
+ * 48 x TY cells of u^{n+2}.  Two steps are taken in one launch only where no diagnostic
+ * record falls between them (an even diag_every reached from an even step, or no
+ * diagnostics).  Both settings give identical results; on GB300 two per launch measured
+ * the same time per step at 512^2 and more at 64^2.  Returns the previous setting, or
+ * PF_ERR_ARG. */
+int pf_set_steps_per_launch(pf_handle* h, int steps);
+
 /* Grids above 2^20 cells (56 x 24 tiles): on = 1 steps them with a persistent kernel
  * in which every resident CTA walks a share of the tiles and stages the next tile (TMA
  * for interior tiles) while it computes one; on = 0 (the default) launches one CTA per

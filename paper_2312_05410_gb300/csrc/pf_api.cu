@@ -148,6 +148,9 @@ struct pf_handle {
     bool ring;              // large grids: the persistent tile loop (TILE_LARGE tiles, next tile staged ahead)
     bool tma;               // interior tiles staged by TMA through maps[buffer]
     pf::StepMaps maps[2];   // tensor maps of u[0] and u[1]
+    int spl;                // steps per launch: 1, or 2 (two steps per launch where the diagnostics allow)
+    bool tma2;              // the two-step kernel's interior tiles staged by TMA through maps2[buffer]
+    pf::StepMaps maps2[2];  // tensor maps of u[0] and u[1] with the two-step kernel's taller box
     cudaGraphExec_t gexec;
     long gsteps;  // steps per graph replay (0: no graph yet)
 };
@@ -167,6 +170,24 @@ int do_step(pf_handle* h)
     return PF_OK;
 }
 
+int do_step2(pf_handle* h)
+{
+    const int a = h->cur, b = 1 - h->cur;
+    cudaError_t e = pf::launch_step2(h->k, h->p.phi_mode, h->mob, h->u[a][0], h->u[a][1], h->u[a][2], h->u[b][0],
+                                     h->u[b][1], h->u[b][2], h->stream, h->tma2 ? &h->maps2[a] : nullptr, h->err);
+    if (e != cudaSuccess) return cuda_fail(e, "two-step launch");
+    h->cur = b;
+    return PF_OK;
+}
+
+// Two steps in one launch from the current step: on when selected, at least two steps are left,
+// and no diagnostic record falls between the two (an even period from an even step).
+bool two_steps_now(const pf_handle* h, long left)
+{
+    if (h->spl != 2 || left < 2) return false;
+    return h->p.diag_every <= 0 || (h->p.diag_every % 2 == 0 && h->step % 2 == 0);
+}
+
 int do_record(pf_handle* h)
 {
     cudaError_t e = pf::launch_diag(h->d, h->u[h->cur][0], h->u[h->cur][1], h->u[h->cur][2], h->partials, h->err,
@@ -178,20 +199,29 @@ int do_record(pf_handle* h)
 // Enqueue steps [h->step, h->step + n) one launch at a time (no graph).
 int run_plain(pf_handle* h, long n)
 {
-    for (long s = 0; s < n; ++s) {
+    for (long s = 0; s < n;) {
         if (h->p.diag_every > 0 && h->step % h->p.diag_every == 0) {
             int rc = do_record(h);
             if (rc) return rc;
         }
-        int rc = do_step(h);
-        if (rc) return rc;
-        ++h->step;
+        if (two_steps_now(h, n - s)) {
+            int rc = do_step2(h);
+            if (rc) return rc;
+            h->step += 2;
+            s += 2;
+        } else {
+            int rc = do_step(h);
+            if (rc) return rc;
+            ++h->step;
+            ++s;
+        }
     }
     return PF_OK;
 }
 
 // Capture a graph of gsteps steps starting from buffer 0 at a step index aligned
-// to the diagnostic period (gsteps is even, so the graph ends in buffer 0).
+// to the diagnostic period (gsteps is even, and a multiple of 4 with two steps per
+// launch, so the graph has an even number of launches and ends in buffer 0).
 int build_graph(pf_handle* h, long gsteps)
 {
     cudaStream_t cap;
@@ -243,12 +273,15 @@ int host_copy(pf_handle* h, float* const* host, int host_pitch, bool to_device)
     return PF_OK;
 }
 
-long graph_block(const pf_params* p)
+long graph_block(const pf_handle* h)
 {
+    const pf_params* p = &h->p;
     if (p->diag_every <= 0) return 256;
     long g = p->diag_every;
     while (g < 64) g *= 2;  // small periods: several records per replay
-    return (g % 2) ? 2 * g : g;
+    if (g % 2) g *= 2;
+    if (h->spl == 2 && g % 4) g *= 2;  // an even number of two-step launches
+    return g;
 }
 
 }  // namespace
@@ -361,6 +394,13 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
     h->tma =
              pf::make_step_maps(h->u[0][0], h->u[0][1], h->u[0][2], nx, ny, pitch, h->tile, &h->maps[0]) &&
              pf::make_step_maps(h->u[1][0], h->u[1][1], h->u[1][2], nx, ny, pitch, h->tile, &h->maps[1]);
+    // one step per launch: two per launch (opt-in) measured no faster at 512^2 and slower at 64^2
+    h->spl = 1;
+    const int TY2 = pf::step2_tile_height();
+    h->tma2 = pf::make_maps_box(h->u[0][0], h->u[0][1], h->u[0][2], nx, ny, pitch, pf::step2_box_rows(),
+                                pf::step2_tile_width() - 8, TY2 - 8, &h->maps2[0]) &&
+              pf::make_maps_box(h->u[1][0], h->u[1][1], h->u[1][2], nx, ny, pitch, pf::step2_box_rows(),
+                                pf::step2_tile_width() - 8, TY2 - 8, &h->maps2[1]);
     h->gexec = nullptr;
     h->gsteps = 0;
     cudaError_t e = pf::launch_reset(h->hist, cap, 0, h->err, h->stream);
@@ -376,7 +416,7 @@ int pf_step(pf_handle* h, long n)
 {
     if (!h) return fail(PF_ERR_ARG, "null handle");
     if (n < 0) return fail(PF_ERR_ARG, "negative step count");
-    const long G = graph_block(&h->p);
+    const long G = graph_block(h);
     long left = n;
     while (left > 0) {
         const bool replay_ok = left >= G && (h->gexec != nullptr || n >= 2 * G);
@@ -479,6 +519,19 @@ int pf_set_wait_limit(pf_handle* h, int polls)
 }
 
 int pf_staging_mode(const pf_handle* h) { return h ? (h->tma ? 1 : 0) : -1; }
+
+int pf_set_steps_per_launch(pf_handle* h, int steps)
+{
+    if (!h) return fail(PF_ERR_ARG, "null handle");
+    if (steps != 1 && steps != 2) return fail(PF_ERR_ARG, "steps per launch must be 1 or 2 (got %d)", steps);
+    const int prev = h->spl;
+    if (steps != h->spl && h->gexec) {  // the captured graph holds the other schedule
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    h->spl = steps;
+    return prev;
+}
 
 int pf_set_tile_loop(pf_handle* h, int on)
 {

@@ -85,19 +85,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 // Tiled FP32 maps of the three planes of one state: dims (nx, ny), row stride pitch*4 bytes,
-// box 64 x (tile height + 8) -- the staged window of one CTA.
-bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
-                    StepMaps* out)
+// box 64 x box_rows -- the staged window of one CTA.  An interior tile exists only if the tile at
+// (interior_x, interior_y) keeps its whole staged window inside the grid; otherwise the TMA path
+// would never be taken and no maps are made.
+bool make_maps_box(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int box_rows,
+                   int interior_x, int interior_y, StepMaps* out)
 {
-    const int TY = tile_height(tile), LY = TY + 8;
-    // an interior tile exists only if the second tile column and row keep their whole staged window
-    // inside the grid (x0 = 56, y0 = TY, 4-cell halo); otherwise the TMA path would never be taken
-    if (nx < 56 + 60 || ny < TY + LY - 4) return false;
+    if (nx < interior_x + 64 || ny < interior_y + box_rows) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {cuuint64_t(nx), cuuint64_t(ny)};
     const cuuint64_t strides[1] = {cuuint64_t(pitch) * sizeof(float)};
-    const cuuint32_t box[2] = {64u, cuuint32_t(LY)};
+    const cuuint32_t box[2] = {64u, cuuint32_t(box_rows)};
     const cuuint32_t elem[2] = {1u, 1u};
     const float* f[3] = {phi, c, rho};
     CUtensorMap* m[3] = {&out->phi, &out->c, &out->rho};
@@ -107,6 +106,15 @@ bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, 
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     return true;
+}
+
+// Maps of the one-step kernel's window (4-cell halo): the second tile column (x0 = 56) and row
+// (y0 = TY) are the first whose windows may lie inside the grid.
+bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
+                    StepMaps* out)
+{
+    const int TY = tile_height(tile), LY = TY + 8;
+    return make_maps_box(phi, c, rho, nx, ny, pitch, LY, 56 - 4, TY - 4, out);
 }
 
 }  // namespace pf

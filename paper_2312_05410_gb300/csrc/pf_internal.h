@@ -61,6 +61,10 @@ struct StepMaps {
 // Encode the maps for a state (false: the driver refused, use the cp.async staging).
 bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
                     StepMaps* out);
+// The same with an explicit box height (rows) and the first interior tile's corner (x, y): false also
+// when no tile of that geometry is interior (the maps would never be used).
+bool make_maps_box(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int box_rows,
+                   int interior_x, int interior_y, StepMaps* out);
 
 // Error-word bits set by kernels (bit 0: NaN/Inf seen by diagnostics).
 constexpr int ERR_BIT_TIMEOUT = 2;  // a bounded wait for a TMA copy ran out
@@ -74,6 +78,14 @@ cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob,
                         float* phi1, float* c1, float* rho1, cudaStream_t s,
                         const StepMaps* maps = nullptr, int* err = nullptr);
 size_t step_smem_bytes(int tile);
+// Two explicit midpoint steps in one launch (48 x step2_tile_height() output tiles from a 64 x
+// step2_box_rows() staged window; maps: box of step2_box_rows() rows, or NULL).
+cudaError_t launch_step2(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,
+                         const float* rho0, float* phi1, float* c1, float* rho1, cudaStream_t s,
+                         const StepMaps* maps, int* err);
+int step2_box_rows();
+int step2_tile_width();
+int step2_tile_height();
 // One fused step by the persistent 56 x 24 tile loop (maps: those of TILE_LARGE, or NULL for
 // per-thread staging only).
 cudaError_t launch_step_ring(const StepConst& k, int phi_mode, int mob, const float* phi0, const float* c0,

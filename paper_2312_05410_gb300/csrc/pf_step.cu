@@ -163,10 +163,11 @@ __device__ __forceinline__ void chem(const StepConst& k, f2 f, f2 c, f2 sf, f2 s
 // One Runge-Kutta stage for the rows [r0, r0+n) of the lane's column pair.
 // In: staged planes (phi, c, rho) at I, I+PLANE, I+2 PLANE, already offset to the lane's pair.
 // Base: the state the update starts from (the input itself for stage 1, u^n for stage 2).
-// FINAL = false: u* = base + dt/2 R(in) into the planes at Out; true: u^{n+1} to global memory.
-// Every lane runs all L + 2 iterations (shuffles need the whole warp); rows past n are
+// MODE 0: u* = in + dt/2 R(in) into the planes at Out; MODE 1: u^{n+1} = base + dt R(in) to
+// global memory; MODE 2: the same u^{n+1} into the planes at Out (the first of two steps in one
+// launch).  Every lane runs all L + 2 iterations (shuffles need the whole warp); rows past n are
 // computed from guard/halo data and not stored.
-template <int L, int PX, int PLANE, int PHI_MODE, int MOB, bool FINAL>
+template <int L, int PX, int PLANE, int PHI_MODE, int MOB, int MODE>
 __device__ __forceinline__ void stage(const StepConst& k, const float* __restrict__ I,
                                       const float* __restrict__ Base, float* __restrict__ Out, int r0, int n,
                                       float* __restrict__ g_phi, float* __restrict__ g_c, float* __restrict__ g_rho,
@@ -182,6 +183,7 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
     fw[1] = ld2(Fi + (r0 - 1) * PX);
     cw[0] = ld2(Ci + (r0 - 2) * PX);
     cw[1] = ld2(Ci + (r0 - 1) * PX);
+    constexpr bool FINAL = MODE != 0;  // a full-dt update from the base state
     const float hdt = FINAL ? k.dt : 0.5f * k.dt;
 #pragma unroll
     for (int j = 0; j < L + 2; ++j) {
@@ -250,7 +252,7 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         const f2 oc = fmaKV(hdt, mulK(rc, k.cR), bc);
         const f2 orr = fmaKV(hdt, Rr, br);
         if (i < n) {
-            if (!FINAL) {
+            if (MODE != 1) {
                 const int o = (r0 + i) * PX;
                 st2(Out + o, of);
                 st2(Out + PLANE + o, oc);
@@ -351,12 +353,11 @@ __device__ __forceinline__ void compute_tile(const StepConst& k, int gx0, int gy
 // reflected ghost rows of phi and c, the reservoir row of rho above the top, zero rows beyond.
 // nx % 4 == 0: every aligned 16-byte group is one asynchronous copy (cp.async, not waited for
 // here); other widths: plain loads and stores.
-template <int TY, int S>
-__device__ __forceinline__ void issue_plain(const StepConst& k, int gx0, int gy0, const float* __restrict__ phi0,
-                                            const float* __restrict__ c0, const float* __restrict__ rho0,
-                                            float* __restrict__ U)
+template <class G>
+__device__ __forceinline__ void issue_plain_g(const StepConst& k, int gx0, int gy0, const float* __restrict__ phi0,
+                                              const float* __restrict__ c0, const float* __restrict__ rho0,
+                                              float* __restrict__ U)
 {
-    using G = Geo<TY, S>;
     constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
     const int tid = threadIdx.x;
     const int nx = k.nx, ny = k.ny, pitch = k.pitch;
@@ -408,12 +409,20 @@ __device__ __forceinline__ void issue_plain(const StepConst& k, int gx0, int gy0
     }
 }
 
+template <int TY, int S>
+__device__ __forceinline__ void issue_plain(const StepConst& k, int gx0, int gy0, const float* __restrict__ phi0,
+                                            const float* __restrict__ c0, const float* __restrict__ rho0,
+                                            float* __restrict__ U)
+{
+    issue_plain_g<Geo<TY, S>>(k, gx0, gy0, phi0, c0, rho0, U);
+}
+
 // Thread 0 only: three TMA box copies (64 x LY per field) of the window with corner (gx0, gy0)
 // into U, completing on the mbarrier at shared address mb (armed here for their bytes).
-template <int TY, int S>
-__device__ __forceinline__ void issue_tma(const StepMaps* maps, int gx0, int gy0, float* U, unsigned mb)
+template <class G>
+__device__ __forceinline__ void issue_tma_g(const StepMaps* maps, int gx0, int gy0, float* U, unsigned mb)
 {
-    constexpr int PLANE = Geo<TY, S>::PLANE;
+    constexpr int PLANE = G::PLANE;
     constexpr unsigned bytes = 3u * PLANE * sizeof(float);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
     const CUtensorMap* tm[3] = {&maps->phi, &maps->c, &maps->rho};
@@ -426,6 +435,12 @@ __device__ __forceinline__ void issue_tma(const StepMaps* maps, int gx0, int gy0
             "l"(reinterpret_cast<uint64_t>(tm[f])), "r"(gx0), "r"(gy0), "r"(mb)
             : "memory");
     }
+}
+
+template <int TY, int S>
+__device__ __forceinline__ void issue_tma(const StepMaps* maps, int gx0, int gy0, float* U, unsigned mb)
+{
+    issue_tma_g<Geo<TY, S>>(maps, gx0, gy0, U, mb);
 }
 
 // Bounded poll of mbarrier phase `parity` by the calling thread: 1 if it completed within cap polls.
@@ -706,6 +721,137 @@ ens_step_kernel_ring(const EnsTile* __restrict__ tiles, const EnsRun* __restrict
     }
 }
 
+// ---- two explicit midpoint steps per launch (temporal blocking in shared memory)
+//
+// For grids that live in L2 the cost of a step is mostly its chain of launch, staging and store
+// (a copy-only form of the one-step kernel takes 2.6 of its 4.95 us at 512^2).  This kernel pays
+// that chain once for two steps: a CTA stages a 64 x (TY + 16) window of u^n (8-cell halo), then
+// runs four stage passes, each consuming 2 cells of validity on every side:
+//   A  u*      = u^n + dt/2 R(u^n)      rows [2, LY-2)   -> B
+//   B  u^{n+1} = u^n + dt R(u*)         rows [4, LY-4)   -> U2 (shared memory)
+//   C  u**     = u^{n+1} + dt/2 R(u^{n+1})  rows [6, LY-6) -> B
+//   D  u^{n+2} = u^{n+1} + dt R(u**)    rows [8, 8+TY)   -> global memory, columns [8, 56): 48 per tile
+// with the ghost rows of each shared-memory state filled where the tile touches the bottom or top.
+// Every pass is stage(), the code of the one-step kernel, so two steps here equal two one-step
+// launches bit for bit.
+constexpr int HALO2 = 8;
+constexpr int TXO2 = LX - 2 * HALO2;  // 48 output columns per tile
+
+template <int TY, int S>
+struct Geo2 {
+    static constexpr int LY = TY + 2 * HALO2;  // staged rows
+    static constexpr int PX = LX;
+    static constexpr int PLANE = LY * PX;
+    static constexpr int THREADS = 32 * S;
+    static constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+    static constexpr int LA = cdiv(TY + 12, S), LB = cdiv(TY + 8, S), LC = cdiv(TY + 4, S), LD = cdiv(TY, S);
+    static constexpr int GUARD = (LA + 4) * PX;  // rows read past the last plane by a segment's tail
+    static constexpr size_t BYTES = (size_t(9) * PLANE + GUARD) * sizeof(float) + 128;  // u^n, u*, u^{n+1}
+};
+
+// Ghost rows of a staged state P (3 planes of LY rows, window rows from gy0) at the bottom and top
+// of the domain, by the boundary rules of the staging: phi and c mirrored two rows deep, rho
+// mirrored one row at the bottom and the reservoir value above the top.
+template <class G>
+__device__ __forceinline__ void ghost_rows(const StepConst& k, int gy0, float* __restrict__ P)
+{
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    const int ny = k.ny;
+    if (gy0 >= 0 && gy0 + LY <= ny) return;  // the window holds no row outside the domain
+    for (int idx = threadIdx.x; idx < 3 * 2 * LX; idx += G::THREADS) {
+        const int fld = idx / (2 * LX), rem = idx - fld * (2 * LX);
+        const int d = rem / LX, x = rem - d * LX;  // ghost depth d + 1
+        float* Q = P + fld * PLANE + x;
+        const int gb = -1 - d, lb = gb - gy0, sb = reflect(gb, ny) - gy0;
+        if (lb >= 0 && lb < LY && sb >= 0 && sb < LY && (fld < 2 || d == 0)) Q[lb * PX] = Q[sb * PX];
+        const int gt = ny + d, lt = gt - gy0, st = reflect(gt, ny) - gy0;
+        if (lt >= 0 && lt < LY) {
+            if (fld == 2)
+                Q[lt * PX] = (d == 0) ? k.rho_top : 0.f;
+            else if (st >= 0 && st < LY)
+                Q[lt * PX] = Q[st * PX];
+        }
+    }
+}
+
+template <int TY, int S, int PHI_MODE, int MOB, bool TMA>
+__global__ void __launch_bounds__(Geo2<TY, S>::THREADS, 3)
+step2_kernel(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
+             const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
+             float* __restrict__ rho1, const __grid_constant__ StepMaps maps, int* __restrict__ err)
+{
+    using G = Geo2<TY, S>;
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    extern __shared__ __align__(128) float smraw[];
+    float* const U = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+    float* const B = U + 3 * PLANE;   // u* and u**
+    float* const U2 = U + 6 * PLANE;  // u^{n+1} (followed by the guard rows)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gx0 = blockIdx.x * TXO2 - HALO2, gy0 = blockIdx.y * TY - HALO2;
+    const int nx = k.nx, ny = k.ny, pitch = k.pitch;
+
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    bool staged = false;
+    if (TMA && gx0 >= 0 && gx0 + LX <= nx && gy0 >= 0 && gy0 + LY <= ny) {
+        __shared__ __align__(8) uint64_t mbar;
+        const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) issue_tma_g<G>(&maps, gx0, gy0, U, mb);
+        const unsigned done = poll_phase(mb, 0, k.wait_cap);
+        if (__syncthreads_or(!done)) {
+            if (tid == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
+            poll_phase(mb, 0, 1 << 22);  // let the copies in flight land before leaving
+            return;
+        }
+        staged = true;
+    }
+    if (!staged) {
+        issue_plain_g<G>(k, gx0, gy0, phi0, c0, rho0, U);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __syncthreads();
+
+    const int dlo = -gy0 > 0 ? -gy0 : 0;              // staged rows holding domain rows: [dlo, dhi)
+    const int dhi = ny - gy0 < LY ? ny - gy0 : LY;
+    const int lo2 = 2 * lane;
+    auto lo = [&](int m) { return dlo > m ? dlo : m; };
+    auto hi = [&](int m) { return dhi < LY - m ? dhi : LY - m; };
+    int r0, n;
+    // A: u* of step 1
+    segment(lo(2), hi(2), S, warp, r0, n);
+    stage<G::LA, PX, PLANE, PHI_MODE, MOB, 0>(k, U + lo2, nullptr, B + lo2, r0, n, nullptr, nullptr, nullptr, 0, 0,
+                                              false, false);
+    __syncthreads();
+    ghost_rows<G>(k, gy0, B);
+    __syncthreads();
+    // B: u^{n+1} into shared memory
+    segment(lo(4), hi(4), S, warp, r0, n);
+    stage<G::LB, PX, PLANE, PHI_MODE, MOB, 2>(k, B + lo2, U + lo2, U2 + lo2, r0, n, nullptr, nullptr, nullptr, 0, 0,
+                                              false, false);
+    __syncthreads();
+    ghost_rows<G>(k, gy0, U2);
+    __syncthreads();
+    // C: u* of step 2
+    segment(lo(6), hi(6), S, warp, r0, n);
+    stage<G::LC, PX, PLANE, PHI_MODE, MOB, 0>(k, U2 + lo2, nullptr, B + lo2, r0, n, nullptr, nullptr, nullptr, 0, 0,
+                                              false, false);
+    __syncthreads();
+    ghost_rows<G>(k, gy0, B);
+    __syncthreads();
+    // D: u^{n+2} to global memory on the 48 x TY output cells
+    segment(lo(HALO2), hi(HALO2), S, warp, r0, n);
+    const int gx = gx0 + lo2;
+    const bool store_x = (lo2 >= HALO2) && (lo2 < HALO2 + TXO2) && gx < nx;
+    const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
+    stage<G::LD, PX, PLANE, PHI_MODE, MOB, 1>(k, B + lo2, U2 + lo2, nullptr, r0, n, phi1, c1, rho1, g_off, pitch,
+                                              store_x, gx + 1 < nx);
+}
+
 // Opt the kernel into its dynamic shared-memory size (once per kernel function).
 template <class Kern>
 cudaError_t configure_smem(Kern kern, bool& configured, size_t smem)
@@ -861,6 +1007,34 @@ cudaError_t launch_ens_ring_t(const EnsTile* tiles, const EnsRun* runs, int ntil
     return cudaLaunchKernelEx(&cfg, kern, tiles, runs, ntiles, parity);
 }
 
+#ifndef PF_STEP2_TY
+#define PF_STEP2_TY 16
+#endif
+
+template <int PHI_MODE, int MOB>
+cudaError_t launch_step2_t(const StepConst& k, const float* f0, const float* c0, const float* r0, float* f1,
+                           float* c1, float* r1, cudaStream_t s, const StepMaps* maps, int* err)
+{
+    constexpr int TY = PF_STEP2_TY, S = 4;
+    using G = Geo2<TY, S>;
+    const dim3 grid((k.nx + TXO2 - 1) / TXO2, (k.ny + TY - 1) / TY);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::BYTES, s, attr);
+    StepMaps none = {};
+    if (maps) {
+        auto kern = step2_kernel<TY, S, PHI_MODE, MOB, true>;
+        static bool configured = false;
+        cudaError_t e = configure_smem(kern, configured, G::BYTES);
+        if (e != cudaSuccess) return e;
+        return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1, *maps, err);
+    }
+    auto kern = step2_kernel<TY, S, PHI_MODE, MOB, false>;
+    static bool configured = false;
+    cudaError_t e = configure_smem(kern, configured, G::BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1, none, err);
+}
+
 template <int TY, int S>
 cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
@@ -938,6 +1112,24 @@ cudaError_t launch_step_ring(const StepConst& k, int phi_mode, int mob, const fl
     if (mob == MOB_BULK) return launch_ring_t<1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
     return launch_ring_t<1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
 }
+
+cudaError_t launch_step2(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
+                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
+                         int* err)
+{
+    if (phi_mode == 0) {
+        if (mob == MOB_UNIFORM) return launch_step2_t<0, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+        if (mob == MOB_BULK) return launch_step2_t<0, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+        return launch_step2_t<0, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    }
+    if (mob == MOB_UNIFORM) return launch_step2_t<1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    if (mob == MOB_BULK) return launch_step2_t<1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+    return launch_step2_t<1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+}
+
+int step2_box_rows() { return PF_STEP2_TY + 2 * HALO2; }
+int step2_tile_width() { return TXO2; }
+int step2_tile_height() { return PF_STEP2_TY; }
 
 cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
                          const float* r0, float* f1, float* c1, float* r1, cudaStream_t s)

@@ -77,6 +77,7 @@ def _load():
     L.pf_set_wait_limit.argtypes, L.pf_set_wait_limit.restype = [vp, C.c_int], C.c_int
     L.pf_staging_mode.argtypes, L.pf_staging_mode.restype = [vp], C.c_int
     L.pf_set_tile_loop.argtypes, L.pf_set_tile_loop.restype = [vp, C.c_int], C.c_int
+    L.pf_set_steps_per_launch.argtypes, L.pf_set_steps_per_launch.restype = [vp, C.c_int], C.c_int
     L.pf_load_host.argtypes, L.pf_load_host.restype = [vp, vp, vp, vp, C.c_int], C.c_int
     L.pf_store_host.argtypes, L.pf_store_host.restype = [vp, vp, vp, vp, C.c_int], C.c_int
     L.pf_destroy.argtypes, L.pf_destroy.restype = [vp], C.c_int
@@ -211,6 +212,10 @@ def pf_set_wait_limit(h, polls: int) -> int:
 
 def pf_staging_mode(h) -> int:
     return int(lib.pf_staging_mode(h))
+
+
+def pf_set_steps_per_launch(h, steps: int) -> int:
+    return int(lib.pf_set_steps_per_launch(h, int(steps)))
 
 
 def pf_set_tile_loop(h, on: bool) -> int:

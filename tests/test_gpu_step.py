@@ -254,6 +254,43 @@ def test_tile_loop_equals_one_cta_per_tile_bitwise(pf, nx, ny):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("nx,ny,diag_every,steps", [(64, 64, 0, 1001), (37, 23, 0, 37), (512, 512, 1000, 2000),
+                                                     (130, 70, 10, 251), (1, 5, 0, 7), (200, 9, 7, 60),
+                                                     (116, 40, 4, 130), (1000, 1000, 0, 515)])
+def test_two_steps_per_launch_equal_one_bitwise(pf, nx, ny, diag_every, steps):
+    """Two explicit midpoint steps per launch (u^{n+1} kept in shared memory) against one step per launch:
+    identical fields and diagnostic history, for ragged sizes, graph replays, odd step counts and even and
+    odd diagnostic periods (where a record would fall between two steps, single steps are taken)."""
+    p = O.with_dt(I.default_params(v_angle_deg=70.0, diag_every=diag_every))
+    state = I.film_state(I.FilmSpec(nx, ny, max(2.0, ny / 3.0), seed=nx * 7 + ny), p)
+    out = []
+    for spl in (2, 1):
+        sim = pf.Sim(p, *state, history_rows=8)
+        assert pf.pf_set_steps_per_launch(sim.h, spl) == 1
+        sim.step(3)
+        sim.step(steps - 3)
+        out.append((sim.numpy(), sim.history()))
+        sim.close()
+    (a, ha), (b, hb) = out
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    np.testing.assert_array_equal(ha, hb)
+
+
+def test_two_step_wait_timeout_is_reported(pf):
+    """The two-step kernel's bounded TMA wait (512^2: interior tiles are TMA-staged) run out: PF_ERR_TIMEOUT."""
+    p = O.with_dt(I.default_params())
+    state = I.film_state(I.FilmSpec(512, 512, 16.0, seed=1), p)
+    sim = pf.Sim(p, *state, history_rows=1)
+    assert pf.pf_set_steps_per_launch(sim.h, 2) == 1
+    assert pf.pf_set_wait_limit(sim.h, 0) == 0
+    sim.step(2)
+    rc, _ = pf.pf_diag(sim.h)
+    assert rc == pf.PF_ERR_TIMEOUT
+    sim.close()
+    assert pf.pf_set_steps_per_launch(None, 2) == pf.PF_ERR_ARG
+
+
 def test_tile_loop_is_refused_on_small_grids(pf):
     p = O.with_dt(I.default_params())
     sim = pf.Sim(p, *I.film_state(I.FilmSpec(512, 512, 16.0, seed=1), p), history_rows=1)
