@@ -239,13 +239,21 @@ int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
  *   (layout as for pf_init); work is 256-byte aligned.  Errors as pf_init.
  * pf_ens_step: advance every run n steps (async on the stream); the caller's
  *   fields hold the new states when the stream reaches the end of the call.
- * pf_ens_autotune: time trial_steps (even, >= 2) steps with each compiled tile
- *   kind and keep the fastest; these are real steps of the simulation (4 x
- *   (trial_steps + 2) in total).  chosen (may be NULL) receives the tile kind,
- *   seconds_per_step (may be NULL, 4 doubles) the timings.  Synchronises.
- * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x24), 2 (56x16), or
+ * pf_ens_autotune: time trial_steps (even, >= 2) steps with each tile kind the
+ *   ensemble can run and keep the fastest; these are real steps of the simulation
+ *   (trial_steps + 2 per kind tried).  chosen (may be NULL) receives the tile kind,
+ *   seconds_per_step (may be NULL, 5 doubles) the timings (0 for a kind not tried).
+ *   Synchronises.
+ * pf_ens_set_tile / pf_ens_get_tile: tile kind 0 (56x8), 1 (56x24), 2 (56x16),
  *   3: 56x24 tiles walked by a persistent kernel (one CTA per resident slot) that
- *   stages the next tile while it computes one.  All kinds give identical results.
+ *   stages the next tile while it computes one, or 4: one cooperative launch that
+ *   advances every run through up to 100 steps (a graph replay holds one such launch),
+ *   its resident CTAs walking the 56x24 tiles of a step and meeting at a grid-wide
+ *   barrier (a counter in the workspace, bounded polls) between steps; kind 4 needs
+ *   every run's nx to be a multiple of 4 (PF_ERR_ARG otherwise).  All kinds give
+ *   identical results.
+ * pf_ens_set_wait_limit: polls of kind 4's barrier wait before it reports a timeout
+ *   (default 2^22); a wait that runs out makes pf_ens_diag return PF_ERR_TIMEOUT.
  * pf_ens_diag: pf_diag of run `run` (synchronises).
  */
 typedef struct pf_ens pf_ens;
@@ -256,6 +264,7 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
 int pf_ens_step(pf_ens* e, long n);
 int pf_ens_autotune(pf_ens* e, int trial_steps, int* chosen, double* seconds_per_step);
 int pf_ens_set_tile(pf_ens* e, int tile);
+int pf_ens_set_wait_limit(pf_ens* e, int polls);
 int pf_ens_get_tile(const pf_ens* e);
 long pf_ens_get_step(const pf_ens* e);
 int pf_ens_diag(pf_ens* e, int run, double out[4]);

@@ -38,7 +38,7 @@ struct EnsLayout {
     size_t runs;                // EnsRun[nruns]
     size_t tiles[pf::NUM_TILE_TABLES];
     int ntiles[pf::NUM_TILE_TABLES];
-    size_t partials, out, err, total;
+    size_t partials, out, err, bar, total;
 };
 
 bool ens_layout(int nruns, const int* nx, const int* ny, const int* pitch, EnsLayout& L)
@@ -68,6 +68,8 @@ bool ens_layout(int nruns, const int* nx, const int* ny, const int* pitch, EnsLa
     off = al256(off + 4 * sizeof(double));
     L.err = off;
     off = al256(off + sizeof(int));
+    L.bar = off;  // grid-barrier counter of the persistent kind
+    off = al256(off + sizeof(unsigned));
     L.total = off;
     return true;
 }
@@ -97,6 +99,9 @@ struct pf_ens {
     double* partials;
     double* out;
     int* err;
+    unsigned* bar;    // grid-barrier counter of the persistent kind
+    int wait_cap;     // polls of a barrier wait before it reports a timeout
+    bool persist_ok;  // every run has nx % 4 == 0: the persistent kind can run
     cudaStream_t stream;
     cudaGraphExec_t gexec;
     int gtile;
@@ -105,11 +110,25 @@ struct pf_ens {
 
 namespace {
 
-int ens_launch(pf_ens* e)
+// n steps of every run from buffer `parity` on stream s: one persistent launch for the persistent
+// kind, else n one-step launches.
+cudaError_t ens_enqueue(pf_ens* e, long n, int parity, cudaStream_t s)
 {
     const int tab = pf::tile_table(e->tile);
-    cudaError_t c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab],
-                                        e->parity, e->stream);
+    if (e->tile == pf::TILE_LARGE_PERSIST)
+        return pf::launch_ens_persistent(e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab], parity, int(n),
+                                         e->bar, e->wait_cap, e->err, s);
+    for (long k = 0; k < n; ++k) {
+        cudaError_t c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab],
+                                            int((parity + k) & 1), s);
+        if (c != cudaSuccess) return c;
+    }
+    return cudaSuccess;
+}
+
+int ens_launch(pf_ens* e)
+{
+    cudaError_t c = ens_enqueue(e, 1, e->parity, e->stream);
     if (c != cudaSuccess) return efail(PF_ERR_CUDA, "ensemble step launch: %s", cudaGetErrorString(c));
     e->parity = 1 - e->parity;
     return PF_OK;
@@ -130,12 +149,8 @@ int ens_graph(pf_ens* e, long G)
         return efail(PF_ERR_CUDA, "begin capture: %s", cudaGetErrorString(c));
     }
     int rc = PF_OK;
-    for (long s = 0; s < G && rc == PF_OK; ++s) {
-        c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[pf::tile_table(e->tile)], e->runs,
-                                e->ntiles[pf::tile_table(e->tile)],
-                                int(s & 1), cap);
-        if (c != cudaSuccess) rc = efail(PF_ERR_CUDA, "ensemble capture: %s", cudaGetErrorString(c));
-    }
+    c = ens_enqueue(e, G, 0, cap);
+    if (c != cudaSuccess) rc = efail(PF_ERR_CUDA, "ensemble capture: %s", cudaGetErrorString(c));
     cudaGraph_t g = nullptr;
     c = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
@@ -277,6 +292,10 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
     e->partials = reinterpret_cast<double*>(w + L.partials);
     e->out = reinterpret_cast<double*>(w + L.out);
     e->err = reinterpret_cast<int*>(w + L.err);
+    e->bar = reinterpret_cast<unsigned*>(w + L.bar);
+    e->wait_cap = 1 << 22;
+    e->persist_ok = true;
+    for (int r = 0; r < nruns; ++r) e->persist_ok &= (nx[r] % 4) == 0;
     e->gexec = nullptr;
     e->gtile = -1;
     e->gsteps = 0;
@@ -307,6 +326,15 @@ int pf_ens_step(pf_ens* e, long n)
             left -= G;
             continue;
         }
+        if (e->tile == pf::TILE_LARGE_PERSIST) {  // the rest (or up to one graph block) as one launch
+            const long m = left < G ? left : G;
+            cudaError_t c = ens_enqueue(e, m, e->parity, e->stream);
+            if (c != cudaSuccess) return efail(PF_ERR_CUDA, "persistent ensemble launch: %s", cudaGetErrorString(c));
+            e->parity ^= int(m & 1);
+            e->step += m;
+            left -= m;
+            continue;
+        }
         int rc = ens_launch(e);
         if (rc) return rc;
         ++e->step;
@@ -331,7 +359,21 @@ int pf_ens_set_tile(pf_ens* e, int tile)
 {
     if (!e) return efail(PF_ERR_ARG, "null handle");
     if (tile < 0 || tile >= pf::NUM_TILE_KINDS) return efail(PF_ERR_ARG, "tile kind %d out of range", tile);
+    if (tile == pf::TILE_LARGE_PERSIST && !e->persist_ok)
+        return efail(PF_ERR_ARG, "the persistent kind needs every run's nx to be a multiple of 4");
     e->tile = tile;
+    return PF_OK;
+}
+
+int pf_ens_set_wait_limit(pf_ens* e, int polls)
+{
+    if (!e) return efail(PF_ERR_ARG, "null handle");
+    if (polls < 0) return efail(PF_ERR_ARG, "the wait limit must be >= 0");
+    if (e->gexec) {  // a captured graph holds the old limit
+        cudaGraphExecDestroy(e->gexec);
+        e->gexec = nullptr;
+    }
+    e->wait_cap = polls;
     return PF_OK;
 }
 
@@ -350,13 +392,18 @@ int pf_ens_autotune(pf_ens* e, int trial_steps, int* chosen, double* seconds_per
     float best_ms = 0.f;
     int rc = PF_OK;
     for (int t = 0; t < pf::NUM_TILE_KINDS && rc == PF_OK; ++t) {
+        if (t == pf::TILE_LARGE_PERSIST && !e->persist_ok) {
+            if (seconds_per_step) seconds_per_step[t] = 0.0;  // not available for this ensemble
+            continue;
+        }
         e->tile = t;
         rc = ens_launch(e);  // warm the kernel (function attributes, caches)
         if (rc == PF_OK) rc = ens_launch(e);
         if (rc != PF_OK) break;
         e->step += 2;
         cudaEventRecord(a, e->stream);
-        for (int s = 0; s < trial_steps && rc == PF_OK; ++s) rc = ens_launch(e);
+        cudaError_t ce = ens_enqueue(e, trial_steps, e->parity, e->stream);  // trial_steps is even
+        if (ce != cudaSuccess) rc = efail(PF_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(ce));
         cudaEventRecord(b, e->stream);
         e->step += trial_steps;
         float ms = 0.f;
@@ -390,6 +437,7 @@ int pf_ens_diag(pf_ens* e, int run, double out[4])
     if (c == cudaSuccess) c = cudaMemcpy(out, e->out, 4 * sizeof(double), cudaMemcpyDeviceToHost);
     if (c == cudaSuccess) c = cudaMemcpy(&err, e->err, sizeof(int), cudaMemcpyDeviceToHost);
     if (c != cudaSuccess) return efail(PF_ERR_CUDA, "ensemble diagnostics: %s", cudaGetErrorString(c));
+    if (err & pf::ERR_BIT_TIMEOUT) return efail(PF_ERR_TIMEOUT, "a bounded grid-barrier wait ran out");
     if (err & 1) return efail(PF_ERR_NONFINITE, "a diagnostic pass saw a NaN or Inf");
     return PF_OK;
 }

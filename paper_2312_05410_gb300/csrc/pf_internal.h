@@ -34,8 +34,10 @@ enum MobKind { MOB_UNIFORM = 0, MOB_BULK = 1, MOB_SURF = 2 };
 // by tile_height(kind) rows; TILE_SMALL gives small grids many CTAs.  TILE_LARGE_RING is the
 // 56 x 24 tile walked by a persistent kernel that stages the next tile while computing one
 // (it uses TILE_LARGE's tile table and tensor maps).
-enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1, TILE_MEDIUM = 2, TILE_LARGE_RING = 3 };
-constexpr int NUM_TILE_KINDS = 4;
+// TILE_LARGE_PERSIST (ensembles only) is one cooperative launch over many steps, with a bounded
+// grid barrier between steps, on the same 56 x 24 tiles.
+enum TileKind { TILE_SMALL = 0, TILE_LARGE = 1, TILE_MEDIUM = 2, TILE_LARGE_RING = 3, TILE_LARGE_PERSIST = 4 };
+constexpr int NUM_TILE_KINDS = 5;
 constexpr int NUM_TILE_TABLES = 3;  // tile tables: TILE_SMALL, TILE_LARGE, TILE_MEDIUM
 int choose_tile(int nx, int ny);
 int tile_width();
@@ -53,6 +55,9 @@ struct EnsTile {
 };
 cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
                             int parity, cudaStream_t s);
+// nsteps steps of every run in one cooperative launch (TILE_LARGE tiles); clears *bar first.
+cudaError_t launch_ens_persistent(int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
+                                  int parity, int nsteps, unsigned* bar, int wait_cap, int* err, cudaStream_t s);
 
 // TMA descriptors of the three fields of one state, box = 64 columns x (tile height + 8) rows.
 struct StepMaps {

@@ -49,6 +49,9 @@
 #define PF_LARGE_TY 24
 #define PF_LARGE_S 4
 #endif
+#ifndef PF_MINB_LARGE
+#define PF_MINB_LARGE 4
+#endif
 
 namespace pf {
 namespace {
@@ -107,7 +110,9 @@ struct Geo {
     static constexpr int THREADS = 32 * S;    // S warps = S row segments
     // resident CTAs per SM the register budget is sized for: 5 for the short tile of small grids
     // (102 registers; the TMA-staged kernel there runs best at that cap), else 4 (4 warps) or 3
-    static constexpr int MINB = (TY == PF_SMALL_TY && S == PF_SMALL_S) ? PF_MINB_SMALL : (S <= 4 ? 4 : 3);
+    static constexpr int MINB = (TY == PF_SMALL_TY && S == PF_SMALL_S) ? PF_MINB_SMALL
+                              : (TY == PF_LARGE_TY && S == PF_LARGE_S) ? PF_MINB_LARGE
+                                                                       : (S <= 4 ? 4 : 3);
     static constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
     static constexpr int L1 = cdiv(TY + 4, S);  // longest stage-1 segment (u* rows)
     static constexpr int L2 = cdiv(TY, S);      // longest stage-2 segment (output rows)
@@ -721,6 +726,54 @@ ens_step_kernel_ring(const EnsTile* __restrict__ tiles, const EnsRun* __restrict
     }
 }
 
+// ---- the ensemble as one persistent launch over many steps
+//
+// One cooperative launch advances every run of an ensemble `nsteps` steps: as many CTAs as are
+// resident walk the 56 x 24 tile table (largest runs first), step after step, with a grid-wide
+// barrier between steps (a counter in global memory that every CTA increments once per step and
+// polls, with a bounded number of polls; the host clears it before the launch).  Staging is per-
+// thread cp.async.cg, which reads through L2, so a tile never sees a line cached in L1 from an
+// earlier step (the ensemble's runs must have nx % 4 == 0 for that path).  A barrier wait that
+// runs out sets ERR_BIT_TIMEOUT and the CTA leaves; the others then run out at their next barrier.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int cap, int* err, int* abort_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's stores of the step, ordered before its arrival (after the bar.sync)
+        atomicAdd(bar, 1u);
+        unsigned v = 0;
+        for (int it = 0;; ++it) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target || it >= cap) break;
+            __nanosleep(64);
+        }
+        *abort_flag = v < target;
+        if (v < target && err) atomicOr(err, ERR_BIT_TIMEOUT);
+        __threadfence();
+    }
+    __syncthreads();
+    return !*abort_flag;
+}
+
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
+ens_persistent_kernel(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ runs, int ntiles, int parity,
+                      int nsteps, unsigned* __restrict__ bar, int wait_cap, int* __restrict__ err)
+{
+    __shared__ int abort_flag;
+    for (int s = 0; s < nsteps; ++s) {
+        const int a = (parity + s) & 1;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const EnsTile e = tiles[t];
+            const EnsRun& r = runs[e.run];
+            step_tile<TY, S, PHI_MODE, MOB>(r.k, e.x0, e.y0, r.f[a][0], r.f[a][1], r.f[a][2], r.f[1 - a][0],
+                                            r.f[1 - a][1], r.f[1 - a][2]);
+            __syncthreads();  // the staging buffers are reused by the next tile
+        }
+        if (s + 1 < nsteps && !grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, wait_cap, err, &abort_flag)) return;
+    }
+}
+
 // ---- two explicit midpoint steps per launch (temporal blocking in shared memory)
 //
 // For grids that live in L2 the cost of a step is mostly its chain of launch, staging and store
@@ -1035,6 +1088,38 @@ cudaError_t launch_step2_t(const StepConst& k, const float* f0, const float* c0,
     return cudaLaunchKernelEx(&cfg, kern, k, f0, c0, r0, f1, c1, r1, none, err);
 }
 
+template <int PHI_MODE, int MOB>
+cudaError_t launch_ens_persistent_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, int parity, int nsteps,
+                                    unsigned* bar, int wait_cap, int* err, cudaStream_t s)
+{
+    constexpr int TY = PF_LARGE_TY, S = PF_LARGE_S;
+    using G = Geo<TY, S>;
+    auto kern = ens_persistent_kernel<TY, S, PHI_MODE, MOB>;
+    static bool configured = false;
+    static int grid_cache = 0;
+    static int ntiles_cache = -1;
+    cudaError_t e = configure_smem(kern, configured, G::BYTES);
+    if (e != cudaSuccess) return e;
+    if (ntiles != ntiles_cache) {
+        e = ring_grid(kern, G::THREADS, G::BYTES, ntiles, grid_cache);
+        if (e != cudaSuccess) return e;
+        ntiles_cache = ntiles;
+    }
+    e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_cache);
+    cfg.blockDim = dim3(G::THREADS);
+    cfg.dynamicSmemBytes = G::BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident at once: the barrier relies on it
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err);
+}
+
 template <int TY, int S>
 cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* f0, const float* c0,
                         const float* r0, float* f1, float* c1, float* r1, cudaStream_t s, const StepMaps* maps,
@@ -1079,7 +1164,7 @@ int tile_height(int tile)
     return tile == TILE_SMALL ? PF_SMALL_TY : (tile == TILE_MEDIUM ? PF_MEDIUM_TY : PF_LARGE_TY);
 }
 
-int tile_table(int tile) { return tile == TILE_LARGE_RING ? TILE_LARGE : tile; }
+int tile_table(int tile) { return (tile == TILE_LARGE_RING || tile == TILE_LARGE_PERSIST) ? TILE_LARGE : tile; }
 
 size_t step_smem_bytes(int tile)
 {
@@ -1125,6 +1210,24 @@ cudaError_t launch_step2(const StepConst& k, int phi_mode, int mob, const float*
     if (mob == MOB_UNIFORM) return launch_step2_t<1, MOB_UNIFORM>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
     if (mob == MOB_BULK) return launch_step2_t<1, MOB_BULK>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
     return launch_step2_t<1, MOB_SURF>(k, f0, c0, r0, f1, c1, r1, s, maps, err);
+}
+
+cudaError_t launch_ens_persistent(int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
+                                  int parity, int nsteps, unsigned* bar, int wait_cap, int* err, cudaStream_t s)
+{
+    if (ntiles <= 0 || nsteps <= 0) return cudaSuccess;
+    if (phi_mode == 0) {
+        if (mob == MOB_UNIFORM)
+            return launch_ens_persistent_t<0, MOB_UNIFORM>(tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err, s);
+        if (mob == MOB_BULK)
+            return launch_ens_persistent_t<0, MOB_BULK>(tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err, s);
+        return launch_ens_persistent_t<0, MOB_SURF>(tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err, s);
+    }
+    if (mob == MOB_UNIFORM)
+        return launch_ens_persistent_t<1, MOB_UNIFORM>(tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err, s);
+    if (mob == MOB_BULK)
+        return launch_ens_persistent_t<1, MOB_BULK>(tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err, s);
+    return launch_ens_persistent_t<1, MOB_SURF>(tiles, runs, ntiles, parity, nsteps, bar, wait_cap, err, s);
 }
 
 int step2_box_rows() { return PF_STEP2_TY + 2 * HALO2; }

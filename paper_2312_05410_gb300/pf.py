@@ -95,6 +95,7 @@ def _load():
     L.pf_ens_autotune.argtypes = [vp, C.c_int, ip, C.POINTER(C.c_double)]
     L.pf_ens_autotune.restype = C.c_int
     L.pf_ens_set_tile.argtypes, L.pf_ens_set_tile.restype = [vp, C.c_int], C.c_int
+    L.pf_ens_set_wait_limit.argtypes, L.pf_ens_set_wait_limit.restype = [vp, C.c_int], C.c_int
     L.pf_ens_get_tile.argtypes, L.pf_ens_get_tile.restype = [vp], C.c_int
     L.pf_ens_get_step.argtypes, L.pf_ens_get_step.restype = [vp], C.c_long
     L.pf_ens_diag.argtypes, L.pf_ens_diag.restype = [vp, C.c_int, C.POINTER(C.c_double)], C.c_int
@@ -396,12 +397,15 @@ class Ensemble:
 
     def autotune(self, trial_steps: int = 20):
         chosen = C.c_int(-1)
-        secs = (C.c_double * 4)()
+        secs = (C.c_double * 5)()
         self._check(lib.pf_ens_autotune(self.h, int(trial_steps), C.byref(chosen), secs))
         return chosen.value, list(secs)
 
     def set_tile(self, tile: int):
         self._check(lib.pf_ens_set_tile(self.h, int(tile)))
+
+    def set_wait_limit(self, polls: int):
+        self._check(lib.pf_ens_set_wait_limit(self.h, int(polls)))
 
     @property
     def tile(self) -> int:

@@ -74,6 +74,54 @@ def test_tile_shapes_give_identical_results(pf):
                 assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("steps", [1, 37, 250])
+def test_persistent_launch_equals_one_launch_per_step_bitwise(pf, steps):
+    """Tile kind 4: every run advanced by one cooperative launch per chunk of up to 100 steps (graph
+    replays of such launches for the full chunks), with a bounded grid barrier between steps, against one
+    launch per step (kind 0), bit for bit."""
+    ms = members([(128, 128), (192, 128), (64, 96), (256, 64), (112, 56)], seed=13)
+    out = []
+    for tile in (4, 0):
+        ens = pf.Ensemble(ms)
+        ens.set_tile(tile)
+        ens.step(steps)
+        out.append([ens.numpy(r) for r in range(len(ms))])
+        assert ens.step_index == steps
+        ens.close()
+    for ra, rb in zip(*out):
+        for a, b in zip(ra, rb):
+            assert np.array_equal(a, b)
+
+
+def test_persistent_launch_needs_widths_in_multiples_of_four(pf):
+    ens = pf.Ensemble(members([(128, 128), (37, 23)], seed=14))
+    with pytest.raises(pf.PFError) as e:
+        ens.set_tile(4)
+    assert e.value.code == pf.PF_ERR_ARG
+    chosen, secs = ens.autotune(2)
+    assert chosen != 4 and secs[4] == 0.0
+    ens.close()
+
+
+def test_persistent_barrier_timeout_is_reported(pf):
+    """A grid-barrier wait limited to zero polls runs out on the CTAs that arrive early; pf_ens_diag reports
+    PF_ERR_TIMEOUT and the context stays usable."""
+    ms = members([(256, 256), (192, 128)], seed=15)
+    ens = pf.Ensemble(ms)
+    ens.set_tile(4)
+    ens.set_wait_limit(0)
+    ens.step(3)
+    with pytest.raises(pf.PFError) as e:
+        ens.diag(0)
+    assert e.value.code == pf.PF_ERR_TIMEOUT
+    ens.close()
+    ok = pf.Ensemble(ms)
+    ok.set_tile(4)
+    ok.step(3)
+    ok.diag(0)
+    ok.close()
+
+
 def test_small_runs_match_the_oracle(pf):
     ms = members([(48, 40), (37, 23), (96, 32)], seed=3)
     ens = pf.Ensemble(ms)
@@ -91,12 +139,12 @@ def test_autotune_picks_a_tile_and_keeps_stepping_the_runs(pf):
     ms = members(SHAPES[:3])
     ens = pf.Ensemble(ms)
     chosen, secs = ens.autotune(4)
-    assert chosen in (0, 1, 2, 3) and ens.tile == chosen
-    assert len(secs) == 4 and all(s > 0 for s in secs)
-    assert ens.step_index == 4 * (4 + 2)
+    assert chosen in (0, 1, 2, 3, 4) and ens.tile == chosen
+    assert len(secs) == 5 and all(s > 0 for s in secs)
+    assert ens.step_index == 5 * (4 + 2)
     ens.step(2)
     for r, m in enumerate(ms):
-        for a, b in zip(ens.numpy(r), single(pf, m, 4 * 6 + 2)):
+        for a, b in zip(ens.numpy(r), single(pf, m, 5 * 6 + 2)):
             assert np.array_equal(a, b)
     ens.close()
 
