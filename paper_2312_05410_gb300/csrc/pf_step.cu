@@ -170,13 +170,17 @@ __device__ __forceinline__ void chem(const StepConst& k, f2 f, f2 c, f2 sf, f2 s
 // Base: the state the update starts from (the input itself for stage 1, u^n for stage 2).
 // MODE 0: u* = in + dt/2 R(in) into the planes at Out; MODE 1: u^{n+1} = base + dt R(in) to
 // global memory; MODE 2: the same u^{n+1} into the planes at Out (the first of two steps in one
-// launch).  Every lane runs all L + 2 iterations (shuffles need the whole warp); rows past n are
-// computed from guard/halo data and not stored.
+// launch); MODE 3: as MODE 1, with the base u^n read from global memory at the output cell (b_phi,
+// b_c, b_rho; the staged window is then free while this stage runs).  Every lane runs all L + 2
+// iterations (shuffles need the whole warp); rows past n are computed from guard/halo data and not
+// stored.
 template <int L, int PX, int PLANE, int PHI_MODE, int MOB, int MODE>
 __device__ __forceinline__ void stage(const StepConst& k, const float* __restrict__ I,
                                       const float* __restrict__ Base, float* __restrict__ Out, int r0, int n,
                                       float* __restrict__ g_phi, float* __restrict__ g_c, float* __restrict__ g_rho,
-                                      size_t g_off, int pitch, bool store_x, bool pair_full)
+                                      size_t g_off, int pitch, bool store_x, bool pair_full,
+                                      const float* __restrict__ b_phi = nullptr, const float* __restrict__ b_c = nullptr,
+                                      const float* __restrict__ b_rho = nullptr)
 {
     const float* Fi = I;
     const float* Ci = I + PLANE;
@@ -243,7 +247,21 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
 
         const int i = j - 2;  // output row r0 + i
         f2 bf, bc, br;
-        if (FINAL) {
+        if (MODE == 3) {  // only stored cells need their base
+            bf = bc = br = F2(0.f);
+            if (store_x && i < n) {
+                const size_t g = g_off + size_t(i) * pitch;
+                if (pair_full) {
+                    bf = __ldg(reinterpret_cast<const f2*>(b_phi + g));
+                    bc = __ldg(reinterpret_cast<const f2*>(b_c + g));
+                    br = __ldg(reinterpret_cast<const f2*>(b_rho + g));
+                } else {
+                    bf.x = __ldg(b_phi + g);
+                    bc.x = __ldg(b_c + g);
+                    br.x = __ldg(b_rho + g);
+                }
+            }
+        } else if (FINAL) {
             const int o = (r0 + i) * PX;
             bf = ld2(Base + o);
             bc = ld2(Base + PLANE + o);
@@ -257,7 +275,7 @@ __device__ __forceinline__ void stage(const StepConst& k, const float* __restric
         const f2 oc = fmaKV(hdt, mulK(rc, k.cR), bc);
         const f2 orr = fmaKV(hdt, Rr, br);
         if (i < n) {
-            if (MODE != 1) {
+            if (MODE == 0 || MODE == 2) {
                 const int o = (r0 + i) * PX;
                 st2(Out + o, of);
                 st2(Out + PLANE + o, oc);
@@ -286,41 +304,25 @@ __device__ __forceinline__ void segment(int lo, int hi, int S, int s, int& r0, i
     n = lo + ((s + 1) * H) / S - r0;
 }
 
-// The two Runge-Kutta stages of one staged tile (window corner (gx0, gy0), u^n in U, u* in B):
-// stage 1 into B, the ghost rows of u* where the tile touches the bottom or top, stage 2 to global
-// memory.  STAGES = 1: one forward-Euler update u + dt R(u) straight to global memory.
-template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2>
-__device__ __forceinline__ void compute_tile(const StepConst& k, int gx0, int gy0, const float* __restrict__ U,
-                                             float* __restrict__ B, float* __restrict__ phi1,
-                                             float* __restrict__ c1, float* __restrict__ rho1)
+// Stage 1 of one staged tile (window corner (gx0, gy0), u^n in U): u* on the staged rows [2, LY-2)
+// inside the domain into B, then the ghost rows of u* where the tile touches the bottom or top.
+// Ends with a barrier: U is no longer read after it.
+template <int TY, int S, int PHI_MODE, int MOB>
+__device__ __forceinline__ void tile_stage1(const StepConst& k, int gx0, int gy0, const float* __restrict__ U,
+                                            float* __restrict__ B)
 {
     using G = Geo<TY, S>;
     constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nx = k.nx, ny = k.ny, pitch = k.pitch;
-    // staged rows holding domain rows: [dlo, dhi)
-    const int dlo = -gy0 > 0 ? -gy0 : 0;
+    const int ny = k.ny;
+    const int dlo = -gy0 > 0 ? -gy0 : 0;  // staged rows holding domain rows: [dlo, dhi)
     const int dhi = ny - gy0 < LY ? ny - gy0 : LY;
-    const int lo2 = 2 * lane;  // the lane's pair column
+    const int lo2 = 2 * lane;
     int r0, n;
-
-    if (STAGES == 1) {  // u + dt R(u) on the output rows, straight to global memory
-        segment(dlo > HALO ? dlo : HALO, dhi < HALO + TY ? dhi : HALO + TY, S, warp, r0, n);
-        const int gx = gx0 + lo2;
-        const bool store_x = (lo2 >= HALO) && (lo2 < HALO + TXO) && gx < nx;
-        const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
-        stage<G::L2, PX, PLANE, PHI_MODE, MOB, true>(k, U + lo2, U + lo2, nullptr, r0, n, phi1, c1, rho1, g_off,
-                                                     pitch, store_x, gx + 1 < nx);
-        return;
-    }
-
-    // ---- stage 1: u* on staged rows [2, LY-2) inside the domain
     segment(dlo > 2 ? dlo : 2, dhi < LY - 2 ? dhi : LY - 2, S, warp, r0, n);
-    stage<G::L1, PX, PLANE, PHI_MODE, MOB, false>(k, U + lo2, nullptr, B + lo2, r0, n, nullptr, nullptr, nullptr, 0,
-                                                  0, false, false);
+    stage<G::L1, PX, PLANE, PHI_MODE, MOB, 0>(k, U + lo2, nullptr, B + lo2, r0, n, nullptr, nullptr, nullptr, 0, 0,
+                                              false, false);
     __syncthreads();
-
-    // ---- ghost rows of u* where the tile touches the bottom or top of the domain
     const bool bottom = dlo > 0, top = dhi <= LY - 3;
     if (bottom || top) {
         for (int idx = tid; idx < 3 * 2 * LX; idx += G::THREADS) {
@@ -343,15 +345,61 @@ __device__ __forceinline__ void compute_tile(const StepConst& k, int gx0, int gy
         }
         __syncthreads();
     }
+}
 
-    // ---- stage 2: u^{n+1} on the output rows [4, 4+TY) inside the domain
+// Stage 2 of one tile: u^{n+1} on the output rows [4, 4+TY) inside the domain, from u* in B and the
+// base u^n staged in U (MODE 1) or read from global memory at the output cells (MODE 3: b_*).
+template <int TY, int S, int PHI_MODE, int MOB, int MODE = 1>
+__device__ __forceinline__ void tile_stage2(const StepConst& k, int gx0, int gy0, const float* __restrict__ U,
+                                            const float* __restrict__ B, float* __restrict__ phi1,
+                                            float* __restrict__ c1, float* __restrict__ rho1,
+                                            const float* b_phi = nullptr, const float* b_c = nullptr,
+                                            const float* b_rho = nullptr)
+{
+    using G = Geo<TY, S>;
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = k.nx, ny = k.ny, pitch = k.pitch;
+    const int dlo = -gy0 > 0 ? -gy0 : 0;
+    const int dhi = ny - gy0 < LY ? ny - gy0 : LY;
+    const int lo2 = 2 * lane;
+    int r0, n;
     segment(dlo > HALO ? dlo : HALO, dhi < HALO + TY ? dhi : HALO + TY, S, warp, r0, n);
     const int gx = gx0 + lo2;  // global column of the pair's first cell
     const bool store_x = (lo2 >= HALO) && (lo2 < HALO + TXO) && gx < nx;
     const bool pair_full = gx + 1 < nx;
     const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
-    stage<G::L2, PX, PLANE, PHI_MODE, MOB, true>(k, B + lo2, U + lo2, nullptr, r0, n, phi1, c1, rho1, g_off, pitch,
-                                                 store_x, pair_full);
+    stage<G::L2, PX, PLANE, PHI_MODE, MOB, MODE>(k, B + lo2, U + lo2, nullptr, r0, n, phi1, c1, rho1, g_off, pitch,
+                                                 store_x, pair_full, b_phi, b_c, b_rho);
+}
+
+// The two Runge-Kutta stages of one staged tile (window corner (gx0, gy0), u^n in U, u* in B):
+// stage 1 into B, the ghost rows of u* where the tile touches the bottom or top, stage 2 to global
+// memory.  STAGES = 1: one forward-Euler update u + dt R(u) straight to global memory.
+template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2>
+__device__ __forceinline__ void compute_tile(const StepConst& k, int gx0, int gy0, const float* __restrict__ U,
+                                             float* __restrict__ B, float* __restrict__ phi1,
+                                             float* __restrict__ c1, float* __restrict__ rho1)
+{
+    using G = Geo<TY, S>;
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    if (STAGES == 1) {  // u + dt R(u) on the output rows, straight to global memory
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int nx = k.nx, ny = k.ny, pitch = k.pitch;
+        const int dlo = -gy0 > 0 ? -gy0 : 0;
+        const int dhi = ny - gy0 < LY ? ny - gy0 : LY;
+        const int lo2 = 2 * lane;
+        int r0, n;
+        segment(dlo > HALO ? dlo : HALO, dhi < HALO + TY ? dhi : HALO + TY, S, warp, r0, n);
+        const int gx = gx0 + lo2;
+        const bool store_x = (lo2 >= HALO) && (lo2 < HALO + TXO) && gx < nx;
+        const size_t g_off = (size_t)(gy0 + r0) * pitch + (gx < 0 ? 0 : gx);
+        stage<G::L2, PX, PLANE, PHI_MODE, MOB, 1>(k, U + lo2, U + lo2, nullptr, r0, n, phi1, c1, rho1, g_off, pitch,
+                                                  store_x, gx + 1 < nx);
+        return;
+    }
+    tile_stage1<TY, S, PHI_MODE, MOB>(k, gx0, gy0, U, B);
+    tile_stage2<TY, S, PHI_MODE, MOB>(k, gx0, gy0, U, B, phi1, c1, rho1);
 }
 
 // Per-thread staging of the window with corner (gx0, gy0) of u^n into U: periodic wrap in x,
@@ -563,164 +611,149 @@ ens_step_kernel(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ ru
 // ---- persistent tile loops for large grids and ensembles
 //
 // CTA b takes tiles b, b + G, b + 2G, ... of the row-major tile order (G = the grid: as many CTAs
-// as are resident at once), and while it computes tile i the staging of tile i+1 is in flight
-// into the second of two staging buffers: interior tiles by TMA (thread 0, an mbarrier per
-// buffer), the others by per-thread cp.async.  The arithmetic per tile is compute_tile's, so the
-// results equal the one-tile-per-CTA kernels bit for bit.  Shared memory: two staged windows and
-// u* (76.7 KB at 56 x 24), 3 CTAs per SM.  When nx % 4 != 0 the per-thread staging is synchronous
-// (no overlap), with the same results.
-constexpr int RING_MINB = 3;
-
+// as are resident at once).  There is one staging buffer, as in the one-tile-per-CTA kernel, so
+// 4 CTAs stay resident per SM: stage 1 reads the staged window; stage 2 reads u* and takes its base
+// values u^n from global memory at the output cells (L2 holds them: the window was just staged),
+// so as soon as stage 1 is done the buffer takes the next tile's staging -- TMA for interior tiles
+// (thread 0, one mbarrier, after a fence.proxy.async ordering the buffer's generic reads before the
+// asynchronous writes), per-thread cp.async otherwise -- which lands while stage 2 runs.  The
+// per-cell arithmetic is that of the one-tile-per-CTA kernel, so the results are the same bit
+// for bit.
 template <int TY, int S>
 struct RingGeo {
-    static constexpr size_t BYTES = (size_t(9) * Geo<TY, S>::PLANE + Geo<TY, S>::GUARD) * sizeof(float) + 128;
+    static constexpr size_t BYTES = Geo<TY, S>::BYTES + 128;  // + slack to align the TMA destination
 };
 
-// Ring state of one CTA: the staging buffers, their mbarriers (8 bytes apart) and, as bit masks
-// indexed by buffer, the phase each mbarrier waits for next and whether the buffer's tile came by
-// TMA (scalars rather than arrays: a runtime buffer index into an array would go through the stack).
-template <int TY, int S>
+// Ring state of one CTA: the staging buffer, u*, the mbarrier, the phase it waits for next and
+// whether the staged tile came by TMA.
 struct Ring {
-    float* U;  // buffer b at U + b * 3 PLANE
-    float* B;  // u* and the guard rows
-    unsigned mb0;
-    unsigned phase = 0u, tma = 0u;
-    __device__ float* buf(int b) const { return U + b * 3 * Geo<TY, S>::PLANE; }
-    __device__ unsigned mb(int b) const { return mb0 + 8u * (unsigned)b; }
+    float* U;
+    float* B;
+    unsigned mb;
+    unsigned phase = 0u;
+    bool tma = false;
 };
 
 template <int TY, int S>
-__device__ __forceinline__ Ring<TY, S> ring_setup(uint64_t* mbar)
+__device__ __forceinline__ Ring ring_setup(uint64_t* mbar)
 {
     extern __shared__ __align__(128) float smraw[];
-    Ring<TY, S> r;
+    Ring r;
     r.U = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
-    r.B = r.U + 6 * Geo<TY, S>::PLANE;
-    r.mb0 = (unsigned)__cvta_generic_to_shared(&mbar[0]);
+    r.B = r.U + 3 * Geo<TY, S>::PLANE;
+    r.mb = (unsigned)__cvta_generic_to_shared(mbar);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb(0)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb(1)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.mb) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     return r;
 }
 
-// Wait until buffer b holds its tile.  false: a TMA wait ran out (ERR_BIT_TIMEOUT set, the
-// copies in flight drained with a bound): the whole CTA must leave.
-template <int TY, int S>
-__device__ __forceinline__ bool ring_wait(Ring<TY, S>& r, int b, int cap, int* err)
+// Wait until the buffer holds its tile.  false: a TMA wait ran out (ERR_BIT_TIMEOUT set, the copies
+// in flight drained with a bound): the whole CTA must leave.
+__device__ __forceinline__ bool ring_wait(Ring& r, int cap, int* err)
 {
-    if ((r.tma >> b) & 1u) {
-        const unsigned par = (r.phase >> b) & 1u;
-        const unsigned done = poll_phase(r.mb(b), par, cap);
+    if (r.tma) {
+        const unsigned done = poll_phase(r.mb, r.phase, cap);
         if (__syncthreads_or(!done)) {
             if (threadIdx.x == 0 && err) atomicOr(err, ERR_BIT_TIMEOUT);
-            poll_phase(r.mb(b), par, 1 << 22);
+            poll_phase(r.mb, r.phase, 1 << 22);
             asm volatile("cp.async.wait_all;" ::: "memory");
             return false;
         }
-        r.phase ^= 1u << b;
+        r.phase ^= 1u;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     return true;
 }
 
-// Stage the window with corner (gx0, gy0) into buffer b: TMA for interior windows when maps are
-// given, else per-thread cp.async.  The buffer's last readers passed a barrier before this.
+// Stage the window with corner (gx0, gy0) into the buffer: TMA for interior windows when maps are
+// given, else per-thread cp.async.  Every reader of the buffer passed a barrier before this.
 template <int TY, int S>
-__device__ __forceinline__ void ring_issue(Ring<TY, S>& r, int b, const StepConst& k, int gx0, int gy0,
-                                           const float* phi0, const float* c0, const float* rho0,
-                                           const StepMaps* maps)
+__device__ __forceinline__ void ring_issue(Ring& r, const StepConst& k, int gx0, int gy0, const float* phi0,
+                                           const float* c0, const float* rho0, const StepMaps* maps)
 {
     constexpr int LY = Geo<TY, S>::LY;
-    const bool by_tma = maps && gx0 >= 0 && gx0 + LX <= k.nx && gy0 >= 0 && gy0 + LY <= k.ny;
-    r.tma = by_tma ? (r.tma | (1u << b)) : (r.tma & ~(1u << b));
-    if (by_tma) {
+    r.tma = maps && gx0 >= 0 && gx0 + LX <= k.nx && gy0 >= 0 && gy0 + LY <= k.ny;
+    if (r.tma) {
         if (threadIdx.x == 0) {
-            // order the generic-proxy reads of this buffer before the asynchronous-proxy writes
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_tma<TY, S>(maps, gx0, gy0, r.buf(b), r.mb(b));
+            issue_tma<TY, S>(maps, gx0, gy0, r.U, r.mb);
         }
     } else {
-        issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, r.buf(b));
+        issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, r.U);
     }
 }
 
 // One step of one run over all its 56 x TY tiles (maps NULL: no TMA).
 template <int TY, int S, int PHI_MODE, int MOB>
-__global__ void __launch_bounds__(Geo<TY, S>::THREADS, RING_MINB)
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
 step_kernel_ring(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
                  const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
                  float* __restrict__ rho1, const __grid_constant__ StepMaps maps, int use_maps, int* __restrict__ err)
 {
-    __shared__ __align__(8) uint64_t mbar[2];
-    Ring<TY, S> r = ring_setup<TY, S>(mbar);
+    __shared__ __align__(8) uint64_t mbar;
+    Ring r = ring_setup<TY, S>(&mbar);
     const int ntx = (k.nx + TXO - 1) / TXO, ntiles = ntx * ((k.ny + TY - 1) / TY);
     const StepMaps* mp = use_maps ? &maps : nullptr;
-    auto corner = [&](int t, int& gx0, int& gy0) {
-        const int ty = t / ntx;
-        gx0 = (t - ty * ntx) * TXO - HALO;
-        gy0 = ty * TY - HALO;
-    };
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    int t = blockIdx.x, gx0, gy0;
+    int t = blockIdx.x;
     if (t < ntiles) {
-        corner(t, gx0, gy0);
-        ring_issue<TY, S>(r, 0, k, gx0, gy0, phi0, c0, rho0, mp);
+        const int ty = t / ntx;
+        ring_issue<TY, S>(r, k, (t - ty * ntx) * TXO - HALO, ty * TY - HALO, phi0, c0, rho0, mp);
     }
 #pragma unroll 1
-    for (int i = 0; t < ntiles; ++i) {
-        const int b = i & 1;
-        if (!ring_wait<TY, S>(r, b, k.wait_cap, err)) return;
+    while (t < ntiles) {
+        if (!ring_wait(r, k.wait_cap, err)) return;
+        const int ty = t / ntx;
+        const int gx0 = (t - ty * ntx) * TXO - HALO, gy0 = ty * TY - HALO;
+        tile_stage1<TY, S, PHI_MODE, MOB>(k, gx0, gy0, r.U, r.B);
         const int tn = t + gridDim.x;
         if (tn < ntiles) {
-            int nx0, ny0;
-            corner(tn, nx0, ny0);
-            ring_issue<TY, S>(r, b ^ 1, k, nx0, ny0, phi0, c0, rho0, mp);
+            const int tyn = tn / ntx;
+            ring_issue<TY, S>(r, k, (tn - tyn * ntx) * TXO - HALO, tyn * TY - HALO, phi0, c0, rho0, mp);
         } else {
             asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         }
-        corner(t, gx0, gy0);
-        compute_tile<TY, S, PHI_MODE, MOB>(k, gx0, gy0, r.buf(b), r.B, phi1, c1, rho1);
-        __syncthreads();
+        tile_stage2<TY, S, PHI_MODE, MOB, 3>(k, gx0, gy0, r.U, r.B, phi1, c1, rho1, phi0, c0, rho0);
+        __syncthreads();  // u* is rewritten by the next tile's stage 1
         t = tn;
     }
 }
 
 // One step of every run of an ensemble over its tile table (per-thread staging only).
 template <int TY, int S, int PHI_MODE, int MOB>
-__global__ void __launch_bounds__(Geo<TY, S>::THREADS, RING_MINB)
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
 ens_step_kernel_ring(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ runs, int ntiles, int parity)
 {
-    __shared__ __align__(8) uint64_t mbar[2];
-    Ring<TY, S> r = ring_setup<TY, S>(mbar);
+    __shared__ __align__(8) uint64_t mbar;
+    Ring r = ring_setup<TY, S>(&mbar);
     const int a = parity;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     int t = blockIdx.x;
     if (t < ntiles) {
         const EnsTile e = tiles[t];
         const EnsRun& run = runs[e.run];
-        ring_issue<TY, S>(r, 0, run.k, e.x0 - HALO, e.y0 - HALO, run.f[a][0], run.f[a][1], run.f[a][2], nullptr);
+        ring_issue<TY, S>(r, run.k, e.x0 - HALO, e.y0 - HALO, run.f[a][0], run.f[a][1], run.f[a][2], nullptr);
     }
 #pragma unroll 1
-    for (int i = 0; t < ntiles; ++i) {
-        const int b = i & 1;
-        ring_wait<TY, S>(r, b, 0, nullptr);  // per-thread copies only: no bounded TMA wait
+    while (t < ntiles) {
+        ring_wait(r, 0, nullptr);  // per-thread copies only: no bounded TMA wait
+        const EnsTile e = tiles[t];
+        const EnsRun& run = runs[e.run];
+        tile_stage1<TY, S, PHI_MODE, MOB>(run.k, e.x0 - HALO, e.y0 - HALO, r.U, r.B);
         const int tn = t + gridDim.x;
         if (tn < ntiles) {
-            const EnsTile e = tiles[tn];
-            const EnsRun& run = runs[e.run];
-            ring_issue<TY, S>(r, b ^ 1, run.k, e.x0 - HALO, e.y0 - HALO, run.f[a][0], run.f[a][1], run.f[a][2],
-                              nullptr);
+            const EnsTile en = tiles[tn];
+            const EnsRun& rn = runs[en.run];
+            ring_issue<TY, S>(r, rn.k, en.x0 - HALO, en.y0 - HALO, rn.f[a][0], rn.f[a][1], rn.f[a][2], nullptr);
         } else {
             asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         }
-        const EnsTile e = tiles[t];
-        const EnsRun& run = runs[e.run];
-        compute_tile<TY, S, PHI_MODE, MOB>(run.k, e.x0 - HALO, e.y0 - HALO, r.buf(b), r.B, run.f[1 - a][0],
-                                           run.f[1 - a][1], run.f[1 - a][2]);
+        tile_stage2<TY, S, PHI_MODE, MOB, 3>(run.k, e.x0 - HALO, e.y0 - HALO, r.U, r.B, run.f[1 - a][0],
+                                             run.f[1 - a][1], run.f[1 - a][2], run.f[a][0], run.f[a][1], run.f[a][2]);
         __syncthreads();
         t = tn;
     }
