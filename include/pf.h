@@ -160,8 +160,8 @@ int pf_set_steps_per_launch(pf_handle* h, int steps);
 
 /* Grids above 2^20 cells (56 x 24 tiles): on = 1 steps them with a persistent kernel
  * in which every resident CTA walks a share of the tiles and stages the next tile (TMA
- * for interior tiles) while it computes one; on = 0 (the default) launches one CTA per
- * tile, which measured faster on GB300 (4 CTAs per SM against the loop's 3).  Both give
+ * for interior tiles) while it computes the current one's second stage; on = 0 (the
+ * default) launches one CTA per tile, which measured faster on GB300.  Both give
  * identical results.  Returns the previous setting (0 or 1), or PF_ERR_ARG for a
  * smaller grid or a null handle. */
 int pf_set_tile_loop(pf_handle* h, int on);
