@@ -422,6 +422,7 @@ int pf_adjoint(const pf_params* p, int nx, int ny, int pitch, const float* phi0,
                float* g_c0, float* g_rho0, double* g_params, float* final_phi, float* final_c, float* final_rho,
                void* work, size_t work_bytes, void* stream)
 {
+    pf::TraceRange trace("pf_adjoint");
     using namespace pf;
     if (!p || !phi0 || !c0 || !rho0 || !w_phi || !w_c || !g_phi0 || !g_c0 || !g_rho0 || !g_params || !work)
         return afail(PF_ERR_ARG, "null pointer");

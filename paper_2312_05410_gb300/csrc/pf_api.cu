@@ -414,6 +414,7 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
 
 int pf_step(pf_handle* h, long n)
 {
+    pf::TraceRange trace("pf_step");
     if (!h) return fail(PF_ERR_ARG, "null handle");
     if (n < 0) return fail(PF_ERR_ARG, "negative step count");
     const long G = graph_block(h);

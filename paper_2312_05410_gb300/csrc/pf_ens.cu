@@ -310,6 +310,7 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
 
 int pf_ens_step(pf_ens* e, long n)
 {
+    pf::TraceRange trace("pf_ens_step");
     if (!e) return efail(PF_ERR_ARG, "null handle");
     if (n < 0) return efail(PF_ERR_ARG, "negative step count");
     const long G = ENS_GRAPH_STEPS;

@@ -108,6 +108,7 @@ size_t pf_hybrid_workspace_size(const pf_ens* e)
 int pf_hybrid_run(pf_ens* e, pf_unet* u, const pf_hybrid_params* hp, long total_steps, void* work, size_t work_bytes,
                   pf_hybrid_stats* stats)
 {
+    pf::TraceRange trace("pf_hybrid_run");
     if (!e || !u || !hp || !stats) return hfail(PF_ERR_ARG, "null pointer");
     if (total_steps < 0) return hfail(PF_ERR_ARG, "negative step count");
     if (hp->dns_stretch < 1 || hp->jump_steps < 1 || hp->frame_every < 1 || !(hp->dt_ref_steps > 0.0))

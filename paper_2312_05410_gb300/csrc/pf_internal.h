@@ -2,11 +2,22 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "pf.h"
 
 namespace pf {
+
+// A named NVTX range over a C-ABI call (what the call enqueues, on the host timeline): profilers can
+// select its kernels, e.g. ncu --nvtx --nvtx-include "pf_unet_jump/".  Without a tool attached the
+// NVTX calls return at once.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // FP32 constants of one explicit midpoint step, folded from pf_params on the host.
 struct StepConst {

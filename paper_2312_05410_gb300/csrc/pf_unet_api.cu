@@ -342,6 +342,7 @@ int pf_unet_init(const float* const* weights, int nweights, int batch, int nx, i
 
 int pf_unet_jump(pf_unet* u, int n, float* const* phi, float* const* c, float* const* rho, int pitch, double tau)
 {
+    pf::TraceRange trace("pf_unet_jump");
     if (!u || !phi || !c || !rho) return ufail(PF_ERR_ARG, "null pointer");
     if (n != u->n) return ufail(PF_ERR_ARG, "batch %d, the handle was built for %d", n, u->n);
     if (pitch < u->w) return ufail(PF_ERR_LAYOUT, "pitch %d < nx %d", pitch, u->w);

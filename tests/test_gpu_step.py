@@ -49,7 +49,7 @@ def test_small_film_100_and_2000_steps(pf):
     assert ref2000[0].sum() > state[0].astype(np.float64).sum() + 10
 
 
-@pytest.mark.parametrize("nx,ny", [(37, 23), (65, 64), (130, 70), (64, 33), (1, 5), (3, 2), (200, 9)])
+@pytest.mark.parametrize("nx,ny", [(37, 23), (65, 64), (130, 70), (64, 33), (1, 5), (3, 2), (200, 9), (511, 513)])
 def test_odd_and_ragged_sizes(pf, nx, ny):
     p = O.with_dt(I.default_params(v_angle_deg=65.0))
     state = I.film_state(I.FilmSpec(nx, ny, ny / 3.0, seed=nx * 1000 + ny), p)
@@ -324,6 +324,50 @@ def test_host_buffer_load_step_store(pf):
         assert np.array_equal(a[:, :150], w)
         assert np.all(a[:, 150:] == 7.0)
     assert pf.lib.pf_load_host(None, None, None, None, 150) == pf.PF_ERR_ARG
+
+
+@pytest.mark.parametrize("nx,ny,spl,loop", [(37, 23, 1, 0), (511, 513, 1, 0), (511, 513, 2, 0), (130, 70, 2, 0),
+                                            (1100, 1000, 1, 0), (1100, 1000, 1, 1), (1101, 960, 1, 1),
+                                            (1101, 960, 1, 0)])
+def test_guard_bands_stay_untouched(pf, nx, ny, spl, loop):
+    """Out-of-bounds writes would land in canaries: the caller's fields sit inside buffers with 8 canary rows
+    above and below and canary columns from nx to the padded pitch (and the workspace has a canary tail).
+    After steps through the chosen kernel path, every canary still holds its value and the state equals
+    the one of plain fields."""
+    import torch
+
+    G, CAN = 8, -12345.5
+    p = O.with_dt(I.default_params(v_angle_deg=70.0, diag_every=10))
+    st = I.film_state(I.FilmSpec(nx, ny, max(2.0, ny / 3.0), seed=nx + 3 * ny), p)
+    pitch = pf.padded_pitch(nx)
+    bufs = []
+    for a in st:
+        t = torch.full((ny + 2 * G, pitch), CAN, dtype=torch.float32, device="cuda")
+        t[G:G + ny, :nx] = torch.from_numpy(a).cuda()
+        bufs.append(t)
+    need = pf.pf_workspace_size(nx, ny, pitch, 8)
+    work = torch.full((need + 256 + 4096,), 0x5A, dtype=torch.uint8, device="cuda")
+    wp = (work.data_ptr() + 255) // 256 * 256
+    tail = work[wp - work.data_ptr() + need:].clone()
+    stream = torch.cuda.current_stream().cuda_stream
+    rc, h = pf.pf_init(p, nx, ny, pitch, *(t[G:].data_ptr() for t in bufs), wp, need, 8, stream)
+    assert rc == 0, pf.last_error()
+    if spl == 2:
+        assert pf.pf_set_steps_per_launch(h, 2) == 1
+    if loop:
+        assert pf.pf_set_tile_loop(h, 1) == 0
+    assert pf.pf_step(h, 3) == 0 and pf.pf_step(h, 40) == 0
+    torch.cuda.synchronize()
+    assert pf.pf_destroy(h) == 0
+    for t in bufs:
+        assert torch.all(t[:G] == CAN) and torch.all(t[G + ny:] == CAN)
+        assert torch.all(t[G:G + ny, nx:] == CAN)
+    assert torch.equal(work[wp - work.data_ptr() + need:], tail)
+    ref = pf.Sim(p, *st, history_rows=8)
+    ref.step(43)
+    for t, w in zip(bufs, ref.numpy()):
+        assert np.array_equal(t[G:G + ny, :nx].cpu().numpy(), w)
+    ref.close()
 
 
 def test_standalone_diagnostics_entry_point(pf):
