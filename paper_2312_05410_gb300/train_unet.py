@@ -109,7 +109,7 @@ def make_model(seed: int = 0):
 
 
 def train(pf, runs: int = 200, budget_s: float = 1800.0, batch: int = 8, lr: float = 1e-3, seed: int = 0,
-          held_out: int = 4, log=print) -> dict:
+          held_out: int = 4, field_weights=(1.0, 1.0, 1.0), log=print) -> dict:
     import torch
 
     torch.manual_seed(seed)
@@ -135,8 +135,8 @@ def train(pf, runs: int = 200, budget_s: float = 1800.0, batch: int = 8, lr: flo
                 x, y = torch.flip(x, dims=(-1,)), torch.flip(y, dims=(-1,))
         return x, y
 
-    def loss_fn(pred, y):
-        return sum(((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(3))
+    def loss_fn(pred, y):  # relative squared error of each field, weighted
+        return sum(field_weights[q] * ((pred[:, q] - y[:, q]) ** 2).sum() / (y[:, q] ** 2).sum() for q in range(3))
 
     def validate():
         """Held-out relative squared error per field (phi, c, rho), one jump from DNS frames."""
@@ -171,7 +171,7 @@ def train(pf, runs: int = 200, budget_s: float = 1800.0, batch: int = 8, lr: flo
                 break
         epoch += 1
         v = validate()
-        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss.detach()) / 3:.3e} "
+        log(f"epoch {epoch} step {step} t {time.time() - t0:.0f}s train {float(loss.detach()) / sum(field_weights):.3e} "
             f"val rel L2 phi {math.sqrt(v[0]):.3e} c {math.sqrt(v[1]):.3e} rho {math.sqrt(v[2]):.3e}")
     return {k: v.detach().float().cpu().numpy() for k, v in net.p.items()}
 
@@ -183,11 +183,13 @@ def main():
     ap.add_argument("--budget", type=float, default=1800.0)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--field-weights", type=float, nargs=3, default=(1.0, 1.0, 1.0),
+                    help="loss weights of the relative squared errors of phi, c, rho")
     args = ap.parse_args()
     from . import build as B
     B.build()
     from . import pf
-    W = train(pf, args.runs, args.budget, args.batch, args.lr)
+    W = train(pf, args.runs, args.budget, args.batch, args.lr, field_weights=tuple(args.field_weights))
     np.savez(args.out, **W)
     print(f"wrote {args.out}")
 
