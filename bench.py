@@ -68,7 +68,7 @@ WORKLOADS = {
                        K=50, bytes_per_cell_update=84,
                        desc="adjoint 256x256, 1000 steps, checkpoint every 50, gradient of a final-state loss"),
     "hybrid256": dict(kind="hybrid", n_runs=16, side=256, seed=5, steps=100000, dns_stretch=2000, jump=2000,
-                      frame_every=1000,
+                      frame_every=1000, lead_5pct=40000,
                       desc="hybrid DNS / U-Net: 16 runs of 256x256, 2000 DNS steps alternating with one U-Net jump "
                            "of 2000 steps (look-back frames 1000 steps apart), to 100000 steps"),
     "ensemble64": dict(kind="ensemble", n_runs=64, seed=3, steps=10000,
@@ -201,10 +201,11 @@ class EnsembleRun:
         self.cells = sum(ny * nx for ny, nx in self.ens.shapes)
         self.nsteps = W["steps"]
         self.chosen, self.tune = self.ens.autotune(10)
-        self.launches = self.nsteps
+        per = pf.ENS_STEPS_PER_PERSISTENT_LAUNCH if self.chosen == 4 else 1
+        self.launches = -(-self.nsteps // per)
         sides = sorted({nx for _, nx in self.ens.shapes})
         self.config = {"runs": len(ms), "sides": sides, "total_cells": self.cells, "timesteps_per_run": self.nsteps,
-                       "tile_kind": self.chosen, "autotune_s_per_step": self.tune,
+                       "tile_kind": f"{self.chosen}: {pf.TILE_KINDS[self.chosen]}", "autotune_s_per_step": self.tune,
                        "launch": "one fused launch per step for all runs, CUDA graph replays"}
 
     def reset_counters(self):
@@ -305,6 +306,11 @@ class HybridPair:
         self.net = pf.UNet(weights, W["n_runs"], side, side, stream=self.stream)
         self.solver = pf.Hybrid(self.hyb, self.net, dns_stretch=W["dns_stretch"], jump_steps=W["jump"],
                                 frame_every=W["frame_every"])
+        # the same alternation after a DNS lead-in: the schedule measured to keep phi and c within 5 %
+        self.lead = W.get("lead_5pct", 0)
+        self.lead_solver = pf.Hybrid(self.hyb, self.net, dns_stretch=W["dns_stretch"], jump_steps=W["jump"],
+                                     frame_every=W["frame_every"], dns_lead=self.lead) if self.lead else None
+        self.lead_stats = self.lead_errors = None
         self.h_fields = [t for run in self.hyb.fields for t in run]
         self.d_fields = [t for run in self.dns.fields for t in run]
         self.init = [t.clone() for t in self.h_fields]
@@ -333,7 +339,7 @@ class HybridPair:
                        "lookback": "3 frames 1000 steps apart", "cycles": self.cycles,
                        "unet": "32-64-128-256, BF16 tensor-core convolutions, "
                                + ("trained weights" if self.trained else "seeded untrained weights"),
-                       "dns_tile": ("56x8", "56x24", "56x16")[self.tile] + " (autotuned)",
+                       "dns_tile": pf.TILE_KINDS[self.tile] + " (autotuned)",
                        "launch": "pf_hybrid_run: fused ensemble step launches (graph replays), 2 frame kernels, "
                                  "28 U-Net launches and one plausibility check per cycle"}
 
@@ -347,6 +353,9 @@ class HybridPair:
 
     def run_hybrid(self):
         self.stats = self.solver.run(self.nsteps)
+
+    def run_lead(self):
+        self.lead_stats = self.lead_solver.run(self.nsteps)
 
     def run_dns(self):
         self.dns.step(self.nsteps)
@@ -407,15 +416,16 @@ def time_hybrid_against_dns(pair, steps, warmup, flush) -> dict:
     state, flushes L2, and brackets each run with CUDA events on the launch stream."""
     import torch
 
+    arms = [(pair.reset_hybrid, pair.run_hybrid, []), (pair.reset_dns, pair.run_dns, [])]
+    if pair.lead_solver is not None:  # first in each repeat: its errors use the final DNS state of the last repeat
+        arms.insert(0, (pair.reset_hybrid, pair.run_lead, []))
     for _ in range(warmup):
-        pair.reset_hybrid()
-        pair.run_hybrid()
-        pair.reset_dns()
-        pair.run_dns()
+        for reset, run, _ in arms:
+            reset()
+            run()
     torch.cuda.synchronize()
-    th, td = [], []
     for _ in range(steps):
-        for reset, run, acc in ((pair.reset_hybrid, pair.run_hybrid, th), (pair.reset_dns, pair.run_dns, td)):
+        for reset, run, acc in arms:
             reset()
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -424,8 +434,15 @@ def time_hybrid_against_dns(pair, steps, warmup, flush) -> dict:
             b.record(pair.stream)
             torch.cuda.synchronize()
             acc.append(a.elapsed_time(b) / 1e3)
-    return {"hybrid_s": statistics.median(th), "plain_dns_s": statistics.median(td), "hybrid_runs_s": th,
-            "plain_dns_runs_s": td}
+            if run == pair.run_lead:
+                pair.lead_errors = pair.errors()
+    th, td = arms[-2][2], arms[-1][2]
+    out = {"hybrid_s": statistics.median(th), "plain_dns_s": statistics.median(td), "hybrid_runs_s": th,
+           "plain_dns_runs_s": td}
+    if pair.lead_solver is not None:
+        out["lead_s"] = statistics.median(arms[0][2])
+        out["lead_runs_s"] = arms[0][2]
+    return out
 
 
 def hybrid_block(pair, timing: dict, peaks: dict) -> dict:
@@ -440,7 +457,19 @@ def hybrid_block(pair, timing: dict, peaks: dict) -> dict:
             "rel_l2_vs_dns": {"phi": err["phi"], "c": err["c"], "rho": err["rho"]},
             "s2_rel_l2_vs_dns": err["s2"], "jump_ms": pair.jump_s * 1e3, "jump_tflops": jump_tf,
             "jump_tensor_frac_of_bf16_peak": jump_tf / peaks["bf16_tflops"], "weights": pair.weights_desc,
-            "config": pair.config}
+            "config": pair.config, "with_dns_lead": lead_block(pair, timing)}
+
+
+def lead_block(pair, timing: dict):
+    """The same alternation after a DNS lead-in (the paper starts its hybrid with the solver alone),
+    timed in the same loop as plain DNS: speed-up and errors against plain DNS."""
+    if pair.lead_solver is None:
+        return None
+    e, st = pair.lead_errors, pair.lead_stats
+    return {"dns_lead": pair.lead, "hybrid_s": timing["lead_s"], "speedup_vs_dns": timing["plain_dns_s"] / timing["lead_s"],
+            "jumps": st["jumps"], "dns_fallbacks": st["fallbacks"], "dns_steps": st["dns_steps"],
+            "rel_l2_vs_dns": {"phi": e["phi"], "c": e["c"], "rho": e["rho"]}, "s2_rel_l2_vs_dns": e["s2"],
+            "phi_and_c_within_5pct": bool(e["phi"] <= 0.05 and e["c"] <= 0.05)}
 
 
 def measure(R, steps, warmup, flush, local, reset_extra=None):

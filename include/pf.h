@@ -418,7 +418,9 @@ const char* pf_unet_last_error(void);
  * simulation alternate with leaps of the neural operator over the time the DNS
  * would have taken).  Every run of ensemble `e` must have the U-Net's grid
  * (batch = number of runs, one row pitch for all), and both handles must use the
- * same stream.  pf_hybrid_run advances every run `total_steps` steps by cycles of
+ * same stream.  pf_hybrid_run advances every run `total_steps` steps: first
+ * `dns_lead` DNS steps (the paper starts its hybrid with the solver alone; the
+ * deposited film's early growth amplifies a perturbation most), then cycles of
  *   1. `dns_stretch` DNS steps (pf_ens_step), pushing the state as a look-back frame
  *      (pf_unet_frame) 2 frame_every and frame_every steps before the stretch ends;
  *   2. a backup of every run's state, then one jump (pf_unet_jump) standing for
@@ -437,6 +439,7 @@ typedef struct pf_hybrid_params {
     long frame_every;     /* steps between the look-back frames */
     double dt_ref_steps;  /* the network's time unit in steps */
     double phi_lo, phi_hi, c_lo, c_hi, rho_lo, rho_hi;  /* plausible ranges of a prediction */
+    long dns_lead;        /* DNS steps before the first cycle, >= 0 (part of total_steps) */
 } pf_hybrid_params;
 typedef struct pf_hybrid_stats {
     long jumps, fallbacks, dns_steps;

@@ -3,7 +3,8 @@
 // The paper's hybrid solver ("Hybrid" in Results; "U-Net with temporal
 // conditioning", Methods) alternates stretches of direct numerical simulation
 // with leaps of the neural operator over the time the DNS would have taken.
-// Here a batch of equal-size runs advances in lockstep:
+// Here a batch of equal-size runs advances in lockstep: `dns_lead` DNS steps
+// first (the paper runs its solver alone for the first steps), then cycles of
 //   1. DNS stretch: `dns_stretch` explicit steps of every run (one fused ensemble
 //      launch per step, graph replays), with the state pushed as a look-back
 //      frame of the surrogate `2 frame_every` and `frame_every` steps before its end;
@@ -113,6 +114,7 @@ int pf_hybrid_run(pf_ens* e, pf_unet* u, const pf_hybrid_params* hp, long total_
     if (total_steps < 0) return hfail(PF_ERR_ARG, "negative step count");
     if (hp->dns_stretch < 1 || hp->jump_steps < 1 || hp->frame_every < 1 || !(hp->dt_ref_steps > 0.0))
         return hfail(PF_ERR_ARG, "stretch, jump, frame spacing and dt_ref must be positive");
+    if (hp->dns_lead < 0) return hfail(PF_ERR_ARG, "negative DNS lead-in");
     if (hp->dns_stretch < 2 * hp->frame_every)
         return hfail(PF_ERR_ARG, "the stretch (%ld) must hold the two look-back frames %ld steps apart", hp->dns_stretch,
                      hp->frame_every);
@@ -132,7 +134,11 @@ int pf_hybrid_run(pf_ens* e, pf_unet* u, const pf_hybrid_params* hp, long total_
     stats->fallbacks = 0;
     stats->dns_steps = 0;
     pf_unet_reset_frames(u);
-    long t = 0;
+    long t = hp->dns_lead < total_steps ? hp->dns_lead : total_steps;
+    if (t > 0) {
+        if ((rc = ens_steps(e, t))) return rc;
+        stats->dns_steps += t;
+    }
     const long cycle = hp->dns_stretch + hp->jump_steps;
     while (t + cycle <= total_steps) {
         // 1. the DNS stretch, with the two look-back frames pushed on the way

@@ -45,11 +45,16 @@ class Params(C.Structure):
         return p
 
 
+# Ensemble tile kinds (pf_ens_set_tile), by index.
+TILE_KINDS = ("56x8", "56x24", "56x16", "56x24, persistent tile walk", "56x24, cooperative launch of up to 100 steps")
+ENS_STEPS_PER_PERSISTENT_LAUNCH = 100
+
+
 class HybridParams(C.Structure):
     """Mirror of struct pf_hybrid_params."""
     _fields_ = [("dns_stretch", C.c_long), ("jump_steps", C.c_long), ("frame_every", C.c_long),
                 ("dt_ref_steps", C.c_double)] + [(n, C.c_double) for n in (
-                    "phi_lo", "phi_hi", "c_lo", "c_hi", "rho_lo", "rho_hi")]
+                    "phi_lo", "phi_hi", "c_lo", "c_hi", "rho_lo", "rho_hi")] + [("dns_lead", C.c_long)]
 
 
 class HybridStats(C.Structure):
@@ -677,18 +682,19 @@ class UNet:
 
 class Hybrid:
     """The hybrid DNS / U-Net solver (pf_hybrid_run): an Ensemble of equal grids and a UNet of the same
-    batch and grid, sharing one stream.  Each cycle runs `dns_stretch` DNS steps (pushing look-back
+    batch and grid, sharing one stream.  The first `dns_lead` steps are DNS alone; then each cycle
+    runs `dns_stretch` DNS steps (pushing look-back
     frames `2 frame_every` and `frame_every` steps before its end), backs the state up, jumps
     `jump_steps` steps with the U-Net and falls back to DNS for the jumped steps when a prediction
     fails the plausibility ranges."""
 
     def __init__(self, ens: "Ensemble", net: "UNet", dns_stretch: int = 2000, jump_steps: int = 2000,
                  frame_every: int = 1000, dt_ref_steps: float = 2000.0, phi_range=(-1.5, 1.5),
-                 c_range=(-0.5, 1.5), rho_range=(-0.5, 1.5)):
+                 c_range=(-0.5, 1.5), rho_range=(-0.5, 1.5), dns_lead: int = 0):
         import torch
         self.ens, self.net = ens, net
         self.params = HybridParams(int(dns_stretch), int(jump_steps), int(frame_every), float(dt_ref_steps),
-                                   *phi_range, *c_range, *rho_range)
+                                   *phi_range, *c_range, *rho_range, int(dns_lead))
         size = int(lib.pf_hybrid_workspace_size(ens.h))
         self.work = torch.empty(size + 256, dtype=torch.uint8, device="cuda")
         self._wp = (self.work.data_ptr() + 255) // 256 * 256

@@ -375,3 +375,70 @@ def test_committed_weights_drive_the_hybrid_close_to_dns(pf):
     net.close()
     hyb.close()
     dns.close()
+
+
+def test_hybrid_dns_lead_in_runs_the_solver_alone_first(pf):
+    """dns_lead: the first steps are DNS only, counted in total_steps.  With identity jumps the hybrid equals
+    DNS of the lead-in plus the stretches; a lead-in at least as long as the run is plain DNS; a negative
+    one is refused."""
+    import oracle as O
+    from paper_2312_05410_gb300 import inputs as I2
+    ms = []
+    for m in I2.hybrid_members(2, 128, seed=8):
+        p = O.with_dt(I2.default_params(v_mag=m["v_mag"]))
+        ms.append((p, *I2.film_state(m["spec"], p)))
+    W = I2.unet_weights(0)
+    W["out_gamma"][:] = 0.0
+    W["out_beta"][:] = 0.0
+    for lead, total, expect, dns_steps in ((300, 1100, {"jumps": 2, "fallbacks": 0, "dns_steps": 500}, 500),
+                                           (1200, 1100, {"jumps": 0, "fallbacks": 0, "dns_steps": 1100}, 1100)):
+        ens = pf.Ensemble(ms)
+        ens.set_tile(0)
+        net = pf.UNet(W, 2, 128, 128, stream=ens.stream)
+        st = pf.Hybrid(ens, net, dns_stretch=100, jump_steps=300, frame_every=50, dns_lead=lead).run(total)
+        assert st == expect, (lead, st)
+        hyb = [tuple(t.clone() for t in run) for run in ens.fields]
+        with pytest.raises(pf.PFError):
+            pf.Hybrid(ens, net, dns_stretch=100, jump_steps=300, frame_every=50, dns_lead=-1).run(total)
+        net.close()
+        ens.close()
+        ref = pf.Ensemble(ms)
+        ref.set_tile(0)
+        ref.step(dns_steps)
+        for a, b in zip(hyb, ref.fields):
+            for x, y in zip(a, b):
+                assert torch.equal(x, y)
+        ref.close()
+
+
+def test_hybrid_lead_in_with_the_committed_weights_is_dns_then_the_cycles(pf):
+    """With the trained surrogate, a lead-in of L steps gives bit for bit what L DNS steps followed by a
+    hybrid run without lead-in give (no look-back frame is taken during the lead-in)."""
+    import os
+    import oracle as O
+    from paper_2312_05410_gb300 import inputs as I2
+    path = os.path.join(os.path.dirname(pf.__file__), "weights", "unet_lb3_hybrid256.npz")
+    with np.load(path) as z:
+        W = {k: z[k] for k in z.files}
+    ms = []
+    for m in I2.hybrid_members(16, 256, seed=5)[:2]:
+        p = O.with_dt(I2.default_params(v_mag=m["v_mag"]))
+        ms.append((p, *I2.film_state(m["spec"], p)))
+    out = []
+    for split in (False, True):
+        ens = pf.Ensemble(ms)
+        ens.set_tile(1)
+        net = pf.UNet(W, 2, 256, 256, stream=ens.stream)
+        if split:
+            ens.step(3000)
+            st = pf.Hybrid(ens, net).run(9000)
+        else:
+            st = pf.Hybrid(ens, net, dns_lead=3000).run(12000)
+        assert st["jumps"] == 2 and st["fallbacks"] == 0, st
+        torch.cuda.synchronize()
+        out.append([tuple(t.clone() for t in run) for run in ens.fields])
+        net.close()
+        ens.close()
+    for a, b in zip(*out):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
