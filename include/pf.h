@@ -143,10 +143,12 @@ int pf_set_step(pf_handle* h, long step);
  * of 0 makes every wait give up at once, to exercise that path. */
 int pf_set_wait_limit(pf_handle* h, int polls);
 
-/* 1 when interior tiles are staged by TMA (tensor maps encoded at pf_init; grids with
- * at least one interior tile: nx >= 116 and ny >= 20 up to 2^20 cells, ny >= 52
- * above), 0 when every tile uses per-thread asynchronous copies (smaller grids, or a
- * driver without tensor-map support); -1 on NULL. */
+/* 1 when tiles are staged by TMA (tensor maps encoded at pf_init; grids with at least
+ * one interior tile: nx >= 116 and ny >= 20 up to 2^20 cells, ny >= 52 above): every
+ * tile whose window lies inside the grid in x, the bottom and top tiles included (their
+ * ghost rows are set in shared memory after the copy); tiles that wrap in x use
+ * per-thread copies.  0 when every tile uses per-thread asynchronous copies (smaller
+ * grids, or a driver without tensor-map support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
 
 /* Steps per kernel launch: 1 (the default), or 2: a CTA stages a 64 x (TY + 16) window
@@ -252,8 +254,14 @@ int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
  *   barrier (a counter in the workspace, bounded polls) between steps; kind 4 needs
  *   every run's nx to be a multiple of 4 (PF_ERR_ARG otherwise).  All kinds give
  *   identical results.
- * pf_ens_set_wait_limit: polls of kind 4's barrier wait before it reports a timeout
- *   (default 2^22); a wait that runs out makes pf_ens_diag return PF_ERR_TIMEOUT.
+ * pf_ens_set_wait_limit: polls of kind 4's barrier wait, and of the TMA staging wait
+ *   of kinds 0 and 1, before it reports a timeout (default 2^22); a wait that runs out
+ *   makes pf_ens_diag return PF_ERR_TIMEOUT.
+ * pf_ens_set_tma: 1 (the default) stages the tiles of kinds 0 and 1 that lie inside
+ *   their run's grid in x by TMA, every run's tensor maps travelling with the launch as
+ *   a kernel parameter (ensembles of up to 80 runs; maps encoded at pf_ens_init);
+ *   0: per-thread copies for every tile.  Identical results.  Returns PF_OK.
+ * pf_ens_staging_mode: 1 if the current tile kind stages by TMA, 0 if not, -1 on NULL.
  * pf_ens_diag: pf_diag of run `run` (synchronises).
  */
 typedef struct pf_ens pf_ens;
@@ -265,6 +273,8 @@ int pf_ens_step(pf_ens* e, long n);
 int pf_ens_autotune(pf_ens* e, int trial_steps, int* chosen, double* seconds_per_step);
 int pf_ens_set_tile(pf_ens* e, int tile);
 int pf_ens_set_wait_limit(pf_ens* e, int polls);
+int pf_ens_set_tma(pf_ens* e, int on);
+int pf_ens_staging_mode(const pf_ens* e);
 int pf_ens_get_tile(const pf_ens* e);
 long pf_ens_get_step(const pf_ens* e);
 int pf_ens_diag(pf_ens* e, int run, double out[4]);

@@ -102,6 +102,9 @@ struct pf_ens {
     unsigned* bar;    // grid-barrier counter of the persistent kind
     int wait_cap;     // polls of a barrier wait before it reports a timeout
     bool persist_ok;  // every run has nx % 4 == 0: the persistent kind can run
+    std::vector<pf::EnsMaps> maps;  // [2 kind + buffer], kinds 0 (short) and 1 (large tile): TMA staging
+    bool tma_ok[2];                 // the kind's maps are encoded for every run it can stage by TMA
+    bool use_tma;                   // pf_ens_set_tma
     cudaStream_t stream;
     cudaGraphExec_t gexec;
     int gtile;
@@ -112,18 +115,45 @@ namespace {
 
 // n steps of every run from buffer `parity` on stream s: one persistent launch for the persistent
 // kind, else n one-step launches.
+bool ens_tma(const pf_ens* e)
+{
+    return e->use_tma && (e->tile == pf::TILE_SMALL || e->tile == pf::TILE_LARGE) && e->tma_ok[e->tile];
+}
+
 cudaError_t ens_enqueue(pf_ens* e, long n, int parity, cudaStream_t s)
 {
     const int tab = pf::tile_table(e->tile);
     if (e->tile == pf::TILE_LARGE_PERSIST)
         return pf::launch_ens_persistent(e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab], parity, int(n),
                                          e->bar, e->wait_cap, e->err, s);
+    const bool tma = ens_tma(e);
     for (long k = 0; k < n; ++k) {
-        cudaError_t c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab],
-                                            int((parity + k) & 1), s);
+        const int b = int((parity + k) & 1);
+        cudaError_t c = pf::launch_ens_step(e->tile, e->phi_mode, e->mob, e->tiles[tab], e->runs, e->ntiles[tab], b,
+                                            s, tma ? &e->maps[2 * e->tile + b] : nullptr, e->err);
         if (c != cudaSuccess) return c;
     }
     return cudaSuccess;
+}
+
+// Tensor maps of both buffers of every run for the short and the large tile: a run gets maps when
+// some tile of it can be TMA-staged (nx >= 64, ny >= the window height); a kind whose maps the
+// driver refuses for any such run stages per thread.
+void ens_encode_maps(pf_ens* e)
+{
+    e->maps.assign(4, pf::EnsMaps{});
+    for (int kind = 0; kind < 2; ++kind) {
+        const int LY = pf::tile_height(kind) + 8;
+        bool ok = e->nruns <= pf::ENS_TMA_MAX_RUNS;
+        for (int b = 0; b < 2 && ok; ++b)
+            for (int r = 0; r < e->nruns && ok; ++r) {
+                if (e->nx[r] < 64 || e->ny[r] < LY) continue;
+                const pf::EnsRun& R = e->host_runs[r];
+                ok = pf::make_maps_box(R.f[b][0], R.f[b][1], R.f[b][2], e->nx[r], e->ny[r], e->pitch[r], LY, 0, 0,
+                                       &e->maps[2 * kind + b].run[r]);
+            }
+        e->tma_ok[kind] = ok;
+    }
 }
 
 int ens_launch(pf_ens* e)
@@ -296,6 +326,8 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
     e->wait_cap = 1 << 22;
     e->persist_ok = true;
     for (int r = 0; r < nruns; ++r) e->persist_ok &= (nx[r] % 4) == 0;
+    e->use_tma = true;
+    ens_encode_maps(e);
     e->gexec = nullptr;
     e->gtile = -1;
     e->gsteps = 0;
@@ -375,8 +407,27 @@ int pf_ens_set_wait_limit(pf_ens* e, int polls)
         e->gexec = nullptr;
     }
     e->wait_cap = polls;
+    // the TMA staging wait reads its limit from each run's constants (stream-ordered update)
+    for (int r = 0; r < e->nruns; ++r) e->host_runs[r].k.wait_cap = polls;
+    cudaError_t c = cudaMemcpyAsync(e->runs, e->host_runs.data(), sizeof(pf::EnsRun) * e->nruns,
+                                    cudaMemcpyHostToDevice, e->stream);
+    if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);  // the host table may change again
+    if (c != cudaSuccess) return efail(PF_ERR_CUDA, "run table update: %s", cudaGetErrorString(c));
     return PF_OK;
 }
+
+int pf_ens_set_tma(pf_ens* e, int on)
+{
+    if (!e) return efail(PF_ERR_ARG, "null handle");
+    if (e->gexec) {  // a captured graph holds the other kernel
+        cudaGraphExecDestroy(e->gexec);
+        e->gexec = nullptr;
+    }
+    e->use_tma = on != 0;
+    return PF_OK;
+}
+
+int pf_ens_staging_mode(const pf_ens* e) { return e ? (ens_tma(e) ? 1 : 0) : -1; }
 
 int pf_ens_get_tile(const pf_ens* e) { return e ? e->tile : -1; }
 

@@ -64,8 +64,12 @@ struct EnsRun {
 struct EnsTile {
     int run, x0, y0;
 };
+struct EnsMaps;
+// One step of every run (tile kind `tile`).  maps (may be NULL): the current buffer's maps of every
+// run, for TMA staging of the tiles inside their run's grid in x (short and large tiles); err: the
+// word that records a TMA wait that ran out.
 cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
-                            int parity, cudaStream_t s);
+                            int parity, cudaStream_t s, const EnsMaps* maps = nullptr, int* err = nullptr);
 // nsteps steps of every run in one cooperative launch (TILE_LARGE tiles); clears *bar first.
 cudaError_t launch_ens_persistent(int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
                                   int parity, int nsteps, unsigned* bar, int wait_cap, int* err, cudaStream_t s);
@@ -74,6 +78,14 @@ cudaError_t launch_ens_persistent(int phi_mode, int mob, const EnsTile* tiles, c
 struct StepMaps {
     CUtensorMap phi, c, rho;
 };
+// Tensor maps of one buffer of every run, passed by value with a launch (3 x 128 B per run): the
+// most runs whose maps fit the 32,764-byte kernel-parameter space with room to spare.  Larger
+// ensembles stage every tile per thread.
+constexpr int ENS_TMA_MAX_RUNS = 80;
+struct EnsMaps {
+    StepMaps run[ENS_TMA_MAX_RUNS];
+};
+static_assert(sizeof(EnsMaps) + 64 <= 32764, "ensemble maps exceed the kernel-parameter space");
 // Encode the maps for a state (false: the driver refused, use the cp.async staging).
 bool make_step_maps(const float* phi, const float* c, const float* rho, int nx, int ny, int pitch, int tile,
                     StepMaps* out);

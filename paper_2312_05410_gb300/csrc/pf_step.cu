@@ -52,6 +52,10 @@
 #ifndef PF_MINB_LARGE
 #define PF_MINB_LARGE 4
 #endif
+// Single runs: TMA staging of the bottom and top tiles as well (1), or of interior tiles only (0).
+#ifndef PF_SINGLE_TMA_EDGES
+#define PF_SINGLE_TMA_EDGES 1
+#endif
 
 namespace pf {
 namespace {
@@ -496,6 +500,31 @@ __device__ __forceinline__ void issue_tma(const StepMaps* maps, int gx0, int gy0
     issue_tma_g<Geo<TY, S>>(maps, gx0, gy0, U, mb);
 }
 
+// Ghost rows of a TMA-staged window of u^n (corner row gy0).  The copy fills rows outside the domain
+// with zeros; rows -2, -1, ny, ny+1 are then set as the per-thread staging sets them: mirrored from
+// the domain rows inside the window, rho at row ny the reservoir value.  Rows farther out stay zero,
+// as there.  Needs ny >= LY (the mirrored rows lie in the window); all threads, after the wait.
+template <class G>
+__device__ __forceinline__ void tma_ghost_rows(const StepConst& k, int gy0, float* __restrict__ U)
+{
+    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    const int ny = k.ny;
+    for (int idx = threadIdx.x; idx < 3 * 4 * LX; idx += G::THREADS) {
+        const int fld = idx / (4 * LX), rem = idx - fld * (4 * LX);
+        const int g = rem / LX, x = rem - g * LX;
+        const int gy = g < 2 ? -1 - g : ny + (g - 2);  // -1, -2, ny, ny + 1
+        const int ly = gy - gy0;
+        if (ly < 0 || ly >= LY) continue;
+        float* Q = U + fld * PLANE + x;
+        if (fld == 2 && gy == ny) {
+            Q[ly * PX] = k.rho_top;
+            continue;
+        }
+        const int sy = reflect(gy, ny) - gy0;
+        if (sy >= 0 && sy < LY) Q[ly * PX] = Q[sy * PX];
+    }
+}
+
 // Bounded poll of mbarrier phase `parity` by the calling thread: 1 if it completed within cap polls.
 __device__ __forceinline__ unsigned poll_phase(unsigned mb, unsigned parity, int cap)
 {
@@ -510,7 +539,7 @@ __device__ __forceinline__ unsigned poll_phase(unsigned mb, unsigned parity, int
 // One step of the output tile with corner (x0, y0) of one run (the whole CTA).
 // STAGES = 2: the explicit midpoint step; STAGES = 1: one forward-Euler update
 // u + dt R(u) with the dt held in k (the adjoint uses it for u* with dt/2).
-template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2, bool TMA = false>
+template <int TY, int S, int PHI_MODE, int MOB, int STAGES = 2, bool TMA = false, bool TMA_EDGES = true>
 __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, const float* __restrict__ phi0,
                                           const float* __restrict__ c0, const float* __restrict__ rho0,
                                           float* __restrict__ phi1, float* __restrict__ c1, float* __restrict__ rho1,
@@ -532,9 +561,10 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
     // Wait for the previous step's grid (programmatic dependent launch) before reading.
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    // ---- interior tiles: three TMA box copies (64 x LY each) completing on one mbarrier
+    // ---- tiles inside the grid in x: three TMA box copies (64 x LY each) completing on one
+    // mbarrier; rows outside the domain arrive as zeros and get their ghost values after the wait
     bool staged = false;
-    if (TMA && gx0 >= 0 && gx0 + LX <= nx && gy0 >= 0 && gy0 + LY <= ny) {
+    if (TMA && gx0 >= 0 && gx0 + LX <= nx && ny >= LY && (TMA_EDGES || (gy0 >= 0 && gy0 + LY <= ny))) {
         __shared__ __align__(8) uint64_t mbar;
         const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
         if (tid == 0) {
@@ -550,9 +580,10 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
             poll_phase(mb, 0, 1 << 22);  // let the copies in flight land before leaving
             return;
         }
+        if (gy0 < 0 || gy0 + LY > ny) tma_ghost_rows<G>(k, gy0, U);  // ordered by the barrier below
         staged = true;
     }
-    // ---- other tiles: stage u^n with its ghost rows
+    // ---- tiles that wrap in x: stage u^n with its ghost rows
     if (!staged) {
         issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, U);
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -581,8 +612,8 @@ step_kernel_tma(const StepConst k, const float* __restrict__ phi0, const float* 
                 const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
                 float* __restrict__ rho1, const __grid_constant__ StepMaps maps, int* __restrict__ err)
 {
-    step_tile<TY, S, PHI_MODE, MOB, 2, true>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1,
-                                             &maps, err);
+    step_tile<TY, S, PHI_MODE, MOB, 2, true, PF_SINGLE_TMA_EDGES != 0>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0,
+                                                                      rho0, phi1, c1, rho1, &maps, err);
 }
 
 // One forward-Euler update of one run (dt taken from k).
@@ -606,6 +637,20 @@ ens_step_kernel(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ ru
     const int a = parity, b = 1 - parity;
     step_tile<TY, S, PHI_MODE, MOB>(r.k, t.x0, t.y0, r.f[a][0], r.f[a][1], r.f[a][2], r.f[b][0], r.f[b][1],
                                     r.f[b][2]);
+}
+
+// The same with TMA staging: every run's tensor maps of the current buffer travel with the launch as
+// one kernel parameter (the form TMA reads without a tensor-map proxy fence).
+template <int TY, int S, int PHI_MODE, int MOB>
+__global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
+ens_step_kernel_tma(const EnsTile* __restrict__ tiles, const EnsRun* __restrict__ runs, int parity,
+                    const __grid_constant__ EnsMaps maps, int* __restrict__ err)
+{
+    const EnsTile t = tiles[blockIdx.x];
+    const EnsRun& r = runs[t.run];
+    const int a = parity, b = 1 - parity;
+    step_tile<TY, S, PHI_MODE, MOB, 2, true>(r.k, t.x0, t.y0, r.f[a][0], r.f[a][1], r.f[a][2], r.f[b][0], r.f[b][1],
+                                             r.f[b][2], &maps.run[t.run], err);
 }
 
 // ---- persistent tile loops for large grids and ensembles
@@ -1008,15 +1053,26 @@ cudaError_t launch_euler_t(const StepConst& k, const float* f0, const float* c0,
 }
 
 template <int TY, int S, int PHI_MODE, int MOB>
-cudaError_t launch_ens_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, int parity, cudaStream_t s)
+cudaError_t launch_ens_t(const EnsTile* tiles, const EnsRun* runs, int ntiles, int parity, cudaStream_t s,
+                         const EnsMaps* maps, int* err)
 {
     using G = Geo<TY, S>;
+    const dim3 grid(ntiles);
+    cudaLaunchAttribute attr[1];
+    if constexpr ((TY == PF_LARGE_TY && S == PF_LARGE_S) || (TY == PF_SMALL_TY && S == PF_SMALL_S)) {
+        if (maps) {
+            auto kern = ens_step_kernel_tma<TY, S, PHI_MODE, MOB>;
+            static bool configured = false;
+            cudaError_t e = configure_smem(kern, configured, G::TMA_BYTES);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::TMA_BYTES, s, attr);
+            return cudaLaunchKernelEx(&cfg, kern, tiles, runs, parity, *maps, err);
+        }
+    }
     auto kern = ens_step_kernel<TY, S, PHI_MODE, MOB>;
     static bool configured = false;
-    const dim3 grid(ntiles);
     cudaError_t e = configure_smem(kern, configured, G::BYTES);
     if (e != cudaSuccess) return e;
-    cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = pdl_config(grid, G::THREADS, G::BYTES, s, attr);
     return cudaLaunchKernelEx(&cfg, kern, tiles, runs, parity);
 }
@@ -1170,16 +1226,16 @@ cudaError_t launch_tile(const StepConst& k, int phi_mode, int mob, const float* 
 
 template <int TY, int S>
 cudaError_t launch_ens_tile(int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
-                            int parity, cudaStream_t s)
+                            int parity, cudaStream_t s, const EnsMaps* maps, int* err)
 {
     if (phi_mode == 0) {
-        if (mob == MOB_UNIFORM) return launch_ens_t<TY, S, 0, MOB_UNIFORM>(tiles, runs, ntiles, parity, s);
-        if (mob == MOB_BULK) return launch_ens_t<TY, S, 0, MOB_BULK>(tiles, runs, ntiles, parity, s);
-        return launch_ens_t<TY, S, 0, MOB_SURF>(tiles, runs, ntiles, parity, s);
+        if (mob == MOB_UNIFORM) return launch_ens_t<TY, S, 0, MOB_UNIFORM>(tiles, runs, ntiles, parity, s, maps, err);
+        if (mob == MOB_BULK) return launch_ens_t<TY, S, 0, MOB_BULK>(tiles, runs, ntiles, parity, s, maps, err);
+        return launch_ens_t<TY, S, 0, MOB_SURF>(tiles, runs, ntiles, parity, s, maps, err);
     }
-    if (mob == MOB_UNIFORM) return launch_ens_t<TY, S, 1, MOB_UNIFORM>(tiles, runs, ntiles, parity, s);
-    if (mob == MOB_BULK) return launch_ens_t<TY, S, 1, MOB_BULK>(tiles, runs, ntiles, parity, s);
-    return launch_ens_t<TY, S, 1, MOB_SURF>(tiles, runs, ntiles, parity, s);
+    if (mob == MOB_UNIFORM) return launch_ens_t<TY, S, 1, MOB_UNIFORM>(tiles, runs, ntiles, parity, s, maps, err);
+    if (mob == MOB_BULK) return launch_ens_t<TY, S, 1, MOB_BULK>(tiles, runs, ntiles, parity, s, maps, err);
+    return launch_ens_t<TY, S, 1, MOB_SURF>(tiles, runs, ntiles, parity, s, maps, err);
 }
 
 }  // namespace
@@ -1282,7 +1338,7 @@ cudaError_t launch_euler(const StepConst& k, int phi_mode, int mob, const float*
 }
 
 cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tiles, const EnsRun* runs, int ntiles,
-                            int parity, cudaStream_t s)
+                            int parity, cudaStream_t s, const EnsMaps* maps, int* err)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (tile == TILE_LARGE_RING) {
@@ -1296,10 +1352,11 @@ cudaError_t launch_ens_step(int tile, int phi_mode, int mob, const EnsTile* tile
         return launch_ens_ring_t<1, MOB_SURF>(tiles, runs, ntiles, parity, s);
     }
     if (tile == TILE_SMALL)
-        return launch_ens_tile<PF_SMALL_TY, PF_SMALL_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
-    if (tile == TILE_MEDIUM)
-        return launch_ens_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
-    return launch_ens_tile<PF_LARGE_TY, PF_LARGE_S>(phi_mode, mob, tiles, runs, ntiles, parity, s);
+        return launch_ens_tile<PF_SMALL_TY, PF_SMALL_S>(phi_mode, mob, tiles, runs, ntiles, parity, s, maps, err);
+    if (tile == TILE_MEDIUM)  // no TMA form: per-thread staging
+        return launch_ens_tile<PF_MEDIUM_TY, PF_MEDIUM_S>(phi_mode, mob, tiles, runs, ntiles, parity, s, nullptr,
+                                                          nullptr);
+    return launch_ens_tile<PF_LARGE_TY, PF_LARGE_S>(phi_mode, mob, tiles, runs, ntiles, parity, s, maps, err);
 }
 
 }  // namespace pf

@@ -101,6 +101,8 @@ def _load():
     L.pf_ens_autotune.restype = C.c_int
     L.pf_ens_set_tile.argtypes, L.pf_ens_set_tile.restype = [vp, C.c_int], C.c_int
     L.pf_ens_set_wait_limit.argtypes, L.pf_ens_set_wait_limit.restype = [vp, C.c_int], C.c_int
+    L.pf_ens_set_tma.argtypes, L.pf_ens_set_tma.restype = [vp, C.c_int], C.c_int
+    L.pf_ens_staging_mode.argtypes, L.pf_ens_staging_mode.restype = [vp], C.c_int
     L.pf_ens_get_tile.argtypes, L.pf_ens_get_tile.restype = [vp], C.c_int
     L.pf_ens_get_step.argtypes, L.pf_ens_get_step.restype = [vp], C.c_long
     L.pf_ens_diag.argtypes, L.pf_ens_diag.restype = [vp, C.c_int, C.POINTER(C.c_double)], C.c_int
@@ -411,6 +413,15 @@ class Ensemble:
 
     def set_wait_limit(self, polls: int):
         self._check(lib.pf_ens_set_wait_limit(self.h, int(polls)))
+
+    def set_tma(self, on: bool):
+        """TMA staging of the short and large tiles inside each run's grid in x (default on)."""
+        self._check(lib.pf_ens_set_tma(self.h, int(bool(on))))
+
+    @property
+    def staging_mode(self) -> int:
+        """1 if the current tile kind stages by TMA, else 0."""
+        return int(lib.pf_ens_staging_mode(self.h))
 
     @property
     def tile(self) -> int:

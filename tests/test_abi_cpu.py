@@ -127,6 +127,8 @@ def test_new_entry_points_reject_null_handles_before_any_cuda_call(pf):
     assert lib.pf_unet_reset_frames(None) == pf.PF_ERR_ARG
     assert lib.pf_unet_frame(None, 1, None, None, None, 256) == pf.PF_ERR_ARG
     assert pf.pf_set_tile_loop(None, True) == pf.PF_ERR_ARG
+    assert lib.pf_ens_set_tma(None, 1) == pf.PF_ERR_ARG
+    assert lib.pf_ens_staging_mode(None) == -1
 
 
 def _ens_init(pf, plist, shapes, work_bytes=None, ptr=FAKE):

@@ -59,6 +59,69 @@ def test_every_run_matches_the_single_run_path_bitwise(pf, steps):
     ens.close()
 
 
+TMA_SHAPES = [(128, 128), (192, 128), (64, 96), (37, 23), (256, 64), (112, 56), (300, 40), (150, 70), (132, 200)]
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+def test_tma_staging_equals_per_thread_staging_bitwise(pf, tile):
+    """Tile kinds 0 and 1 stage every tile that lies inside its run's grid in x by TMA (every run's maps
+    travel with the launch), the bottom and top tiles included: their rows outside the domain arrive as
+    zeros and get the ghost values in shared memory.  Per-thread staging of every tile must give the same
+    states bit for bit.  The runs include widths that are not multiples of 56 or of 4, grids narrower
+    than a window (per-thread only) and grids shorter than the large tile's window."""
+    ms = members(TMA_SHAPES, seed=16)
+    out = []
+    for tma in (True, False):
+        ens = pf.Ensemble(ms)
+        ens.set_tile(tile)
+        ens.set_tma(tma)
+        assert ens.staging_mode == (1 if tma else 0)
+        ens.step(37)
+        out.append([ens.numpy(r) for r in range(len(ms))])
+        ens.close()
+    for r, (ra, rb) in enumerate(zip(*out)):
+        for a, b in zip(ra, rb):
+            assert np.array_equal(a, b), r
+
+
+def test_single_runs_with_tma_edges_equal_per_thread_staging(pf):
+    """A single run TMA-stages its bottom and top tiles too; against the ensemble with per-thread staging
+    of every tile (the same per-cell arithmetic), bit for bit after 250 steps."""
+    ms = members([(128, 128), (256, 64), (300, 40), (132, 200)], seed=18)
+    ens = pf.Ensemble(ms)
+    ens.set_tma(False)
+    ens.step(250)
+    for r, m in enumerate(ms):
+        sim = pf.Sim(m[0], *m[1:])
+        assert pf.pf_staging_mode(sim.h) == 1
+        sim.step(250)
+        ref = sim.numpy()
+        sim.close()
+        for a, b in zip(ens.numpy(r), ref):
+            assert np.array_equal(a, b), r
+    ens.close()
+
+
+def test_tma_staging_timeout_is_reported(pf):
+    """A TMA staging wait limited to zero polls runs out; the CTA lets its copies land and leaves,
+    pf_ens_diag reports PF_ERR_TIMEOUT, and the context stays usable."""
+    ms = members([(256, 256), (192, 128)], seed=17)
+    ens = pf.Ensemble(ms)
+    ens.set_tile(1)
+    assert ens.staging_mode == 1
+    ens.set_wait_limit(0)
+    ens.step(3)
+    with pytest.raises(pf.PFError) as e:
+        ens.diag(0)
+    assert e.value.code == pf.PF_ERR_TIMEOUT
+    ens.close()
+    ok = pf.Ensemble(ms)
+    ok.set_tile(1)
+    ok.step(3)
+    ok.diag(0)
+    ok.close()
+
+
 def test_tile_shapes_give_identical_results(pf):
     ms = members(SHAPES[:4])
     results = []
