@@ -64,15 +64,6 @@ __device__ __forceinline__ int refl(int j, int ny)
     for (int it = 0; it < 4 && (j < 0 || j >= ny); ++it) j = j < 0 ? -1 - j : 2 * ny - 1 - j;
     return j < 0 ? 0 : (j >= ny ? ny - 1 : j);
 }
-__device__ __forceinline__ float mirror_at(const float* f, int j, int i, int nx, int ny, int pitch)
-{
-    return f[(size_t)refl(j, ny) * pitch + wrapx(i, nx)];
-}
-__device__ __forceinline__ float rho_at(const float* r, int j, int i, int nx, int ny, int pitch, float rho_top)
-{
-    if (j >= ny) return rho_top;
-    return r[(size_t)refl(j, ny) * pitch + wrapx(i, nx)];
-}
 
 __device__ __forceinline__ double warp_sum(double v)
 {

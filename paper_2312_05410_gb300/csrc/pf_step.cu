@@ -125,6 +125,12 @@ struct Geo {
     static constexpr size_t TMA_BYTES = BYTES + 128;  // + slack to align the TMA destinations to 128 bytes
 };
 
+// Every tile kind's staged window (TMA alignment slack included) fits one CTA's shared memory.
+static_assert(Geo<PF_SMALL_TY, PF_SMALL_S>::TMA_BYTES <= 227 * 1024 &&
+                  Geo<PF_MEDIUM_TY, PF_MEDIUM_S>::TMA_BYTES <= 227 * 1024 &&
+                  Geo<PF_LARGE_TY, PF_LARGE_S>::TMA_BYTES <= 227 * 1024,
+              "a tile's shared memory exceeds the per-CTA limit");
+
 // West and east neighbours of the lane's pair (x, x+1): x-1 from the lane below, x+2 from the lane above.
 __device__ __forceinline__ float west(f2 C) { return __shfl_up_sync(FULL, C.y, 1); }
 __device__ __forceinline__ float east(f2 C) { return __shfl_down_sync(FULL, C.x, 1); }
@@ -546,7 +552,7 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
                                           const StepMaps* maps = nullptr, int* err = nullptr)
 {
     using G = Geo<TY, S>;
-    constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
+    constexpr int PLANE = G::PLANE, LY = G::LY;
     extern __shared__ __align__(128) float smraw[];
     // TMA destinations need a 128-byte aligned base; that launch reserves the extra bytes
     float* const sm = TMA ? reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127))
@@ -554,9 +560,9 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
     float* const U = sm;               // u^n: phi, c, rho
     float* const B = sm + 3 * PLANE;   // u*:  phi, c, rho (followed by the guard rows)
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int gx0 = x0 - HALO, gy0 = y0 - HALO;
-    const int nx = k.nx, ny = k.ny, pitch = k.pitch;
+    const int nx = k.nx, ny = k.ny;
 
     // Wait for the previous step's grid (programmatic dependent launch) before reading.
     asm volatile("griddepcontrol.wait;" ::: "memory");

@@ -89,13 +89,6 @@ uint16_t host_bf16(float f)
     u += 0x7fffu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
 }
-float host_rbf(float f)
-{
-    const uint32_t u = (uint32_t)host_bf16(f) << 16;
-    float r;
-    std::memcpy(&r, &u, 4);
-    return r;
-}
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
