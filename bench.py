@@ -46,6 +46,31 @@ from paper_2312_05410_gb300.dist import aggregate  # noqa: E402
 METRIC = "DNS cell-updates/s (%HBM peak)"
 UNIT = "cell-updates/s"
 BYTES_PER_CELL_UPDATE = 24  # read phi, c, rho + write phi, c, rho, FP32
+# FP32 FMA peak of a GB300: a probe of independent packed fma.rn.f32x2 chains on all 152 SMs, CUDA events,
+# SM clock sampled at 2070 MHz (the scalar form measured 78.4)
+FMA_PEAK_TFLOPS = 79.5
+
+
+def step_flops(p: dict) -> int:
+    """FP32 FLOPs (FMA = 2) of one fused step per cell, counted from the kernel's expression tree: 80 per
+    Runge-Kutta stage for the Cahn-Hilliard phi with a uniform mobility; the bulk interpolation of the
+    mobility adds 6, the surface term 5 more (and one exp2), the Allen-Cahn phi saves 5."""
+    per_stage = 80
+    if p.get("MA_surf", 0.0) != 0.0 or p.get("MB_surf", 0.0) != 0.0:
+        per_stage += 11
+    elif p.get("MA_bulk", 1.0) != p.get("MB_bulk", 1.0):
+        per_stage += 6
+    if p.get("phi_mode", 0) == 1:
+        per_stage -= 5
+    return 2 * per_stage
+
+
+def alu_roofline(flops_per_cell: int, cells: int, per_launch_s: float) -> dict:
+    """The fused step against the FP32 FMA peak: algorithmic FLOPs per launch / launch duration."""
+    achieved = flops_per_cell * cells / per_launch_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FMA_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FMA_PEAK_TFLOPS, "flops_per_cell_update": flops_per_cell,
+            "peak_source": "measured FP32 FMA probe (packed f32x2, 152 SMs, 2070 MHz)"}
 
 WORKLOADS = {
     "paper512": dict(spec=I.PAPER_512["spec"], params=I.PAPER_512["params"], steps=50000,
@@ -516,6 +541,7 @@ def secondary_line(pf, name, args, flush, local, peaks) -> dict:
             "ms_per_run": secs / args.steps * 1e3, "runs": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"]},
+            "alu_roofline": alu_roofline(step_flops(I.default_params(**W.get("params", {}))), R.cells, per_launch),
             "clocks": clk, "config": R.config}
 
 
@@ -631,6 +657,8 @@ def run_native(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": peaks["source"], "algorithmic_bytes_per_cell_update": bpc},
+        "alu_roofline": (alu_roofline(step_flops(I.default_params(**W.get("params", {}))), cells, per_launch_s)
+                         if kind != "adjoint" else None),
         "gpu_launches": launches * args.steps,
         "e2e": {"value": all_units / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
