@@ -286,7 +286,10 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
     }
     e->runs = reinterpret_cast<pf::EnsRun*>(w + L.runs);
     e->stream = static_cast<cudaStream_t>(stream);
-    // tile tables: largest runs first, so the tail of a launch is short tiles of small runs
+    // tile tables: largest runs first, so the tail of a launch is short tiles of small runs.  In a run whose
+    // width is a multiple of 4 the last tile column starts at nx - 56, overlapping its neighbour (which
+    // computes the same values for the shared cells), so its window reaches only 4 columns past the edge
+    // and can be staged by TMA (the kernels' tile_x0 does the same for single runs).
     std::vector<int> order(nruns);
     for (int r = 0; r < nruns; ++r) order[r] = r;
     for (int i = 1; i < nruns; ++i)
@@ -300,7 +303,10 @@ int pf_ens_init(int nruns, const pf_params* params, const int* nx, const int* ny
         const int TW = pf::tile_width(), TH = pf::tile_height(t);
         for (int r : order)
             for (int y = 0; y < ny[r]; y += TH)
-                for (int x = 0; x < nx[r]; x += TW) tabs[t].push_back(pf::EnsTile{r, x, y});
+                for (int x = 0; x < nx[r]; x += TW) {
+                    const bool shift = nx[r] % 4 == 0 && nx[r] >= TW && x + TW > nx[r];
+                    tabs[t].push_back(pf::EnsTile{r, shift ? nx[r] - TW : x, y});
+                }
         e->tiles[t] = reinterpret_cast<pf::EnsTile*>(w + L.tiles[t]);
         e->ntiles[t] = int(tabs[t].size());
         if (!tabs[t].empty())

@@ -145,6 +145,25 @@ __device__ __forceinline__ int reflect(int gy, int ny)
     return gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
 }
 
+// Source row of window row gy for field fld under the staging rules: the row itself inside the
+// domain, phi and c mirrored two rows deep at the bottom and top, rho mirrored two rows deep at the
+// bottom and the reservoir value at row ny (-2), mirrored at ny + 1; -1: zero (rows farther out).
+__device__ __forceinline__ int staged_src_row(int fld, int gy, int ny)
+{
+    if (gy < -2 || gy > ny + 1) return -1;
+    if (fld == 2 && gy == ny) return -2;
+    return reflect(gy, ny);
+}
+
+// First output column of tile column bx.  In a grid whose width is a multiple of 4 the last tile
+// column starts at nx - 56 (overlapping its neighbour, whose cells it recomputes bit for bit), so
+// its window reaches only 4 columns past the edge, as the first column's does.
+__device__ __forceinline__ int tile_x0(int bx, int nx)
+{
+    const int x0 = bx * TXO;
+    return ((nx & 3) == 0 && nx >= TXO && x0 + TXO > nx) ? nx - TXO : x0;
+}
+
 // Chemical potentials and mobility of one pair, from its phi and c and their
 // four-neighbour sums (f: phi, c: composition, sf / sc: neighbour sums).
 template <int MOB>
@@ -434,12 +453,7 @@ __device__ __forceinline__ void issue_plain_g(const StepConst& k, int gx0, int g
         return gx < 0 ? gx + nx : gx;
     };
     // source row of staged row ly for field fld; -1: zero, -2: reservoir value
-    auto src_row = [&](int fld, int ly) {
-        const int gy = gy0 + ly;
-        if (gy < -2 || gy > ny + 1) return -1;
-        if (fld == 2 && gy == ny) return -2;
-        return reflect(gy, ny);
-    };
+    auto src_row = [&](int fld, int ly) { return staged_src_row(fld, gy0 + ly, ny); };
     if ((nx & 3) == 0) {
         // x0 and nx are multiples of 4: each aligned group of 4 staged columns is
         // wholly inside [0, nx) or wholly wrapped
@@ -510,8 +524,9 @@ __device__ __forceinline__ void issue_tma(const StepMaps* maps, int gx0, int gy0
 // with zeros; rows -2, -1, ny, ny+1 are then set as the per-thread staging sets them: mirrored from
 // the domain rows inside the window, rho at row ny the reservoir value.  Rows farther out stay zero,
 // as there.  Needs ny >= LY (the mirrored rows lie in the window); all threads, after the wait.
+// Columns [xskip, xskip + 4) are left alone (a wrap fixup sets them in every row).
 template <class G>
-__device__ __forceinline__ void tma_ghost_rows(const StepConst& k, int gy0, float* __restrict__ U)
+__device__ __forceinline__ void tma_ghost_rows(const StepConst& k, int gy0, float* __restrict__ U, int xskip)
 {
     constexpr int PX = G::PX, PLANE = G::PLANE, LY = G::LY;
     const int ny = k.ny;
@@ -520,7 +535,7 @@ __device__ __forceinline__ void tma_ghost_rows(const StepConst& k, int gy0, floa
         const int g = rem / LX, x = rem - g * LX;
         const int gy = g < 2 ? -1 - g : ny + (g - 2);  // -1, -2, ny, ny + 1
         const int ly = gy - gy0;
-        if (ly < 0 || ly >= LY) continue;
+        if (ly < 0 || ly >= LY || (x >= xskip && x < xskip + 4)) continue;
         float* Q = U + fld * PLANE + x;
         if (fld == 2 && gy == ny) {
             Q[ly * PX] = k.rho_top;
@@ -528,6 +543,55 @@ __device__ __forceinline__ void tma_ghost_rows(const StepConst& k, int gy0, floa
         }
         const int sy = reflect(gy, ny) - gy0;
         if (sy >= 0 && sy < LY) Q[ly * PX] = Q[sy * PX];
+    }
+}
+
+// The 4 staged columns that a TMA box reaching past an x edge fills with zeros: [0, 4) of a window
+// from x = -4 (values of columns nx-4 .. nx-1), [60, 64) of a window ending at nx + 4 (columns 0 .. 3),
+// every row by the staging rules.  Each thread loads its share into registers before the wait for
+// the copy (the loads overlap it) and stores them after.
+template <class G>
+struct WrapCols {
+    static constexpr int N = 3 * G::LY * 4;
+    static constexpr int PER = (N + G::THREADS - 1) / G::THREADS;
+};
+
+template <class G>
+__device__ __forceinline__ void wrap_load(const StepConst& k, int gy0, bool left, const float* __restrict__ phi0,
+                                          const float* __restrict__ c0, const float* __restrict__ rho0,
+                                          float (&v)[WrapCols<G>::PER])
+{
+    constexpr int LY = G::LY;
+    const int ny = k.ny, pitch = k.pitch, xs = left ? k.nx - 4 : 0;
+#pragma unroll
+    for (int i = 0; i < WrapCols<G>::PER; ++i) {
+        const int idx = threadIdx.x + i * G::THREADS;
+        float val = 0.f;
+        if (idx < WrapCols<G>::N) {
+            const int fld = idx / (LY * 4), rem = idx - fld * (LY * 4);
+            const int ly = rem >> 2, cc = rem & 3;
+            const int sr = staged_src_row(fld, gy0 + ly, ny);
+            const float* F = fld == 0 ? phi0 : (fld == 1 ? c0 : rho0);
+            if (sr >= 0) val = __ldg(F + (size_t)sr * pitch + xs + cc);
+            else if (sr == -2) val = k.rho_top;
+        }
+        v[i] = val;
+    }
+}
+
+template <class G>
+__device__ __forceinline__ void wrap_store(bool left, const float (&v)[WrapCols<G>::PER], float* __restrict__ U)
+{
+    constexpr int LY = G::LY, PX = G::PX, PLANE = G::PLANE;
+    const int xd = left ? 0 : LX - 4;
+#pragma unroll
+    for (int i = 0; i < WrapCols<G>::PER; ++i) {
+        const int idx = threadIdx.x + i * G::THREADS;
+        if (idx < WrapCols<G>::N) {
+            const int fld = idx / (LY * 4), rem = idx - fld * (LY * 4);
+            const int ly = rem >> 2, cc = rem & 3;
+            U[fld * PLANE + ly * PX + xd + cc] = v[i];
+        }
     }
 }
 
@@ -567,10 +631,15 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
     // Wait for the previous step's grid (programmatic dependent launch) before reading.
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    // ---- tiles inside the grid in x: three TMA box copies (64 x LY each) completing on one
-    // mbarrier; rows outside the domain arrive as zeros and get their ghost values after the wait
+    // ---- TMA staging: three box copies (64 x LY each) completing on one mbarrier, for windows inside
+    // the grid in x and (widths a multiple of 4) windows reaching 4 columns past an x edge.  Cells
+    // outside the grid arrive as zeros; the wrapped columns and the ghost rows are set after the wait.
+    const bool xin = gx0 >= 0 && gx0 + LX <= nx;
+    const bool wleft = gx0 == -HALO, wright = gx0 + LX == nx + HALO;
+    const bool xwrap = (wleft || wright) && (nx & 3) == 0 && nx >= LX;
+    const bool tma_ok = TMA_EDGES ? (xin || xwrap) : (xin && gy0 >= 0 && gy0 + LY <= ny);
     bool staged = false;
-    if (TMA && gx0 >= 0 && gx0 + LX <= nx && ny >= LY && (TMA_EDGES || (gy0 >= 0 && gy0 + LY <= ny))) {
+    if (TMA && ny >= LY && tma_ok) {
         __shared__ __align__(8) uint64_t mbar;
         const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
         if (tid == 0) {
@@ -579,6 +648,8 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
         }
         __syncthreads();
         if (tid == 0) issue_tma<TY, S>(maps, gx0, gy0, U, mb);
+        float wv[WrapCols<G>::PER];
+        if (!xin) wrap_load<G>(k, gy0, wleft, phi0, c0, rho0, wv);
         // bounded wait on phase 0; every thread votes so the whole CTA leaves together on a timeout
         const unsigned done = poll_phase(mb, 0, k.wait_cap);
         if (__syncthreads_or(!done)) {
@@ -586,10 +657,13 @@ __device__ __forceinline__ void step_tile(const StepConst& k, int x0, int y0, co
             poll_phase(mb, 0, 1 << 22);  // let the copies in flight land before leaving
             return;
         }
-        if (gy0 < 0 || gy0 + LY > ny) tma_ghost_rows<G>(k, gy0, U);  // ordered by the barrier below
+        // disjoint cells: the wrapped columns in every row, the ghost rows in the other columns;
+        // ordered before the stages by the barrier below
+        if (!xin) wrap_store<G>(wleft, wv, U);
+        if (gy0 < 0 || gy0 + LY > ny) tma_ghost_rows<G>(k, gy0, U, xin ? LX : (wleft ? 0 : LX - 4));
         staged = true;
     }
-    // ---- tiles that wrap in x: stage u^n with its ghost rows
+    // ---- other tiles: stage u^n with its ghost rows
     if (!staged) {
         issue_plain<TY, S>(k, gx0, gy0, phi0, c0, rho0, U);
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -608,7 +682,7 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
             const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
             float* __restrict__ rho1)
 {
-    step_tile<TY, S, PHI_MODE, MOB>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
+    step_tile<TY, S, PHI_MODE, MOB>(k, tile_x0(blockIdx.x, k.nx), blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
 }
 
 // The same, with interior tiles staged through the tensor maps of the source state.
@@ -618,8 +692,8 @@ step_kernel_tma(const StepConst k, const float* __restrict__ phi0, const float* 
                 const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
                 float* __restrict__ rho1, const __grid_constant__ StepMaps maps, int* __restrict__ err)
 {
-    step_tile<TY, S, PHI_MODE, MOB, 2, true, PF_SINGLE_TMA_EDGES != 0>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0,
-                                                                      rho0, phi1, c1, rho1, &maps, err);
+    step_tile<TY, S, PHI_MODE, MOB, 2, true, PF_SINGLE_TMA_EDGES != 0>(k, tile_x0(blockIdx.x, k.nx), blockIdx.y * TY,
+                                                                      phi0, c0, rho0, phi1, c1, rho1, &maps, err);
 }
 
 // One forward-Euler update of one run (dt taken from k).
@@ -629,7 +703,8 @@ euler_kernel(const StepConst k, const float* __restrict__ phi0, const float* __r
              const float* __restrict__ rho0, float* __restrict__ phi1, float* __restrict__ c1,
              float* __restrict__ rho1)
 {
-    step_tile<TY, S, PHI_MODE, MOB, 1>(k, blockIdx.x * TXO, blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
+    step_tile<TY, S, PHI_MODE, MOB, 1>(k, tile_x0(blockIdx.x, k.nx), blockIdx.y * TY, phi0, c0, rho0, phi1, c1,
+                                       rho1);
 }
 
 // One step of every run of an ensemble: CTA b takes tile b of the table; runs
