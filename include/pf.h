@@ -146,8 +146,10 @@ int pf_set_wait_limit(pf_handle* h, int polls);
 /* 1 when tiles are staged by TMA (tensor maps encoded at pf_init; grids with at least
  * one interior tile: nx >= 116 and ny >= 20 up to 2^20 cells, ny >= 52 above): every
  * tile whose window lies inside the grid in x, the bottom and top tiles included (their
- * ghost rows are set in shared memory after the copy); tiles that wrap in x use
- * per-thread copies.  0 when every tile uses per-thread asynchronous copies (smaller
+ * ghost rows are set in shared memory after the copy), and in grids whose width is a
+ * multiple of 4 the tiles that wrap in x (the last tile column starts at nx - 56, and
+ * the 4 wrapped columns are set after the copy); other wrapping tiles use per-thread
+ * copies.  0 when every tile uses per-thread asynchronous copies (smaller
  * grids, or a driver without tensor-map support); -1 on NULL. */
 int pf_staging_mode(const pf_handle* h);
 
@@ -256,11 +258,14 @@ int pf_diagnostics_static(const pf_params* p, int nx, int ny, int pitch,
  *   identical results.
  * pf_ens_set_wait_limit: polls of kind 4's barrier wait, and of the TMA staging wait
  *   of kinds 0 and 1, before it reports a timeout (default 2^22); a wait that runs out
- *   makes pf_ens_diag return PF_ERR_TIMEOUT.
- * pf_ens_set_tma: 1 (the default) stages the tiles of kinds 0 and 1 that lie inside
- *   their run's grid in x by TMA, every run's tensor maps travelling with the launch as
- *   a kernel parameter (ensembles of up to 80 runs; maps encoded at pf_ens_init);
- *   0: per-thread copies for every tile.  Identical results.  Returns PF_OK.
+ *   makes pf_ens_diag return PF_ERR_TIMEOUT.  Updates the device run table on the
+ *   stream and synchronises; PF_ERR_ARG on NULL or polls < 0.
+ * pf_ens_set_tma: 1 (the default) stages the tiles of kinds 0 and 1 by TMA: the tiles
+ *   inside their run's grid in x, and in runs whose width is a multiple of 4 also the
+ *   tiles that wrap in x (the last tile column starts at nx - 56); every run's tensor
+ *   maps travel with the launch as a kernel parameter (ensembles of up to 80 runs; maps
+ *   encoded at pf_ens_init).  0: per-thread copies for every tile.  Identical results.
+ *   Returns PF_OK, or PF_ERR_ARG on NULL.
  * pf_ens_staging_mode: 1 if the current tile kind stages by TMA, 0 if not, -1 on NULL.
  * pf_ens_diag: pf_diag of run `run` (synchronises).
  */
