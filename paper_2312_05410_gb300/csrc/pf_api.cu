@@ -146,7 +146,7 @@ struct pf_handle {
     int mob;
     int tile;
     bool ring;              // large grids: the persistent tile loop (TILE_LARGE tiles, next tile staged ahead)
-    bool tma;               // interior tiles staged by TMA through maps[buffer]
+    bool tma;               // tiles staged by TMA through maps[buffer] (all but the wraps of widths not a multiple of 4)
     pf::StepMaps maps[2];   // tensor maps of u[0] and u[1]
     int spl;                // steps per launch: 1, or 2 (two steps per launch where the diagnostics allow)
     bool tma2;              // the two-step kernel's interior tiles staged by TMA through maps2[buffer]
@@ -390,7 +390,7 @@ int pf_init(const pf_params* p, int nx, int ny, int pitch, float* phi, float* c,
     h->mob = pf::mob_kind_of(*p);
     h->tile = pf::choose_tile(nx, ny);
     h->ring = false;  // the tile loop is opt-in: one CTA per tile measured faster on GB300
-    // interior tiles are staged by TMA whenever the grid holds a full staged window
+    // tiles are staged by TMA whenever the grid holds an interior tile's full staged window
     h->tma =
              pf::make_step_maps(h->u[0][0], h->u[0][1], h->u[0][2], nx, ny, pitch, h->tile, &h->maps[0]) &&
              pf::make_step_maps(h->u[1][0], h->u[1][1], h->u[1][2], nx, ny, pitch, h->tile, &h->maps[1]);

@@ -99,7 +99,7 @@ constexpr int ERR_BIT_TIMEOUT = 2;  // a bounded wait for a TMA copy ran out
 
 // Launch one fused step: (phi0, c0, rho0) -> (phi1, c1, rho1) with programmatic
 // dependent launch enabled (the kernel waits for the previous grid before reading).
-// maps (may be NULL) are the tensor maps of (phi0, c0, rho0): interior tiles are then
+// maps (may be NULL) are the tensor maps of (phi0, c0, rho0): tiles are then
 // staged by TMA; err receives ERR_BIT_TIMEOUT if a staging wait ran out.
 cudaError_t launch_step(const StepConst& k, int tile, int phi_mode, int mob,
                         const float* phi0, const float* c0, const float* rho0,

@@ -52,7 +52,8 @@
 #ifndef PF_MINB_LARGE
 #define PF_MINB_LARGE 4
 #endif
-// Single runs: TMA staging of the bottom and top tiles as well (1), or of interior tiles only (0).
+// Single runs: TMA staging of the bottom and top tiles and of the x-wrap tiles as well (1), or of
+// interior tiles only (0).
 #ifndef PF_SINGLE_TMA_EDGES
 #define PF_SINGLE_TMA_EDGES 1
 #endif
@@ -685,7 +686,7 @@ step_kernel(const StepConst k, const float* __restrict__ phi0, const float* __re
     step_tile<TY, S, PHI_MODE, MOB>(k, tile_x0(blockIdx.x, k.nx), blockIdx.y * TY, phi0, c0, rho0, phi1, c1, rho1);
 }
 
-// The same, with interior tiles staged through the tensor maps of the source state.
+// The same, with tiles staged by TMA through the tensor maps of the source state.
 template <int TY, int S, int PHI_MODE, int MOB>
 __global__ void __launch_bounds__(Geo<TY, S>::THREADS, Geo<TY, S>::MINB)
 step_kernel_tma(const StepConst k, const float* __restrict__ phi0, const float* __restrict__ c0,
