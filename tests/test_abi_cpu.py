@@ -32,6 +32,24 @@ def test_library_exports_every_declared_symbol(pf):
         assert hasattr(pf.lib, n), n
 
 
+def test_binding_declares_the_argument_types_of_every_entry_point(pf):
+    """ctypes passes undeclared arguments as C ints: a pointer, size_t, long or double argument would be
+    truncated or mis-passed.  Every entry point the header declares has its argument types set."""
+    import ctypes as C
+
+    missing = [s for s in declared_symbols() if getattr(pf.lib, s).argtypes is None]
+    assert not missing, missing
+    # entry points that return something other than an int declare it (return types read from the header)
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(B.INCLUDE, "pf.h")).read(), flags=re.S)
+    kinds = {"size_t": C.c_size_t, "long": C.c_long, "const char*": C.c_char_p}
+    wide = {}
+    for ret, name in re.findall(r"^(size_t|long|const char\*)\s+(pf_[a-z_0-9]+)\s*\(", text, flags=re.M):
+        wide[name] = kinds[ret]
+    assert len(wide) >= 10, wide
+    for name, rt in wide.items():
+        assert getattr(pf.lib, name).restype is rt, name
+
+
 def test_strerror(pf):
     assert pf.strerror(0) == "ok"
     assert "stability" in pf.strerror(pf.PF_ERR_UNSTABLE)
