@@ -50,6 +50,38 @@ def test_binding_declares_the_argument_types_of_every_entry_point(pf):
         assert getattr(pf.lib, name).restype is rt, name
 
 
+def test_ctypes_struct_mirrors_match_the_c_layout(pf, tmp_path):
+    """The binding's mirrors of pf_params, pf_hybrid_params and pf_hybrid_stats have the C structs' size and
+    field offsets: a small C program compiled against include/pf.h prints them."""
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"pf_params": pf.Params, "pf_hybrid_params": pf.HybridParams, "pf_hybrid_stats": pf.HybridStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pf.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", B.INCLUDE, "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    assert len(got) == sum(1 + len(py._fields_) for py in mirrors.values())
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
 def test_strerror(pf):
     assert pf.strerror(0) == "ok"
     assert "stability" in pf.strerror(pf.PF_ERR_UNSTABLE)
